@@ -1,0 +1,234 @@
+/*
+ * sssp.h -- C ABI of the GB300 library for Garg's bound-based single-source
+ * shortest paths (arXiv 1812.10499, "Removing Sequential Bottleneck of
+ * Dijkstra's Algorithm for the Shortest Path Problem").
+ *
+ * Problem (Sec. I and Sec. II): a directed graph with n vertices and m edges
+ * and strictly positive integer weights; find cost[x], the minimum weight of a
+ * path from the source v0 to every vertex x.  The library runs the
+ * data-parallel round of SP_3/SP_4 (Sec. V, Sec. VI): each round
+ *   (a) relaxes the out-edges of the vertices fixed in the previous round,
+ *       lowering the upper bounds D (SP_4 step 3, label-setting as in SP_3);
+ *   (b) raises the lower bounds C of the discovered, unfixed vertices with
+ *       Eq. (1) of Lemma 6 over their in-edges, clamped by
+ *       min(D, threshold) from Lemmas 7 and 8 (SP_4 steps 1 and 4);
+ *   (c) fixes every vertex whose C equals its D (SP_4 step 5) and makes the
+ *       newly fixed vertices the next round's frontier.
+ * All arithmetic is exact 64-bit integer; results are bit-identical to a
+ * sequential execution of the same rounds.
+ *
+ * Conventions for every entry point:
+ *   - Return value: SSSP_OK (0) on success, a negative SSSP_E_* code on
+ *     failure; sssp_strerror() names it.  On failure, outputs are unspecified
+ *     and no input is modified.
+ *   - Host pointers are caller-owned and only read during the call (inputs)
+ *     or written before the call returns (outputs); nothing is retained.
+ *   - Device pointers ("_dev", "_device") are CUDA global-memory addresses on
+ *     the handle's device; the caller owns them.
+ *   - A handle may be used by one host thread at a time.
+ *   - Unreachable vertices get distance SSSP_DIST_INF (UINT64_MAX).
+ */
+#ifndef SSSP_H
+#define SSSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SSSP_OK                 0
+#define SSSP_E_INVAL           (-1)  /* malformed argument (NULL, bad CSR, n = 0, ...)      */
+#define SSSP_E_ZERO_WEIGHT     (-2)  /* an edge weight is 0; Sec. I requires w > 0          */
+#define SSSP_E_SOURCE_RANGE    (-3)  /* source vertex >= n                                  */
+#define SSSP_E_OVERFLOW        (-4)  /* n * max weight does not fit the packed distance     */
+#define SSSP_E_NOMEM           (-5)  /* device allocation failed or budget exhausted        */
+#define SSSP_E_DEVICE_TIMEOUT  (-6)  /* a bounded device-side wait gave up                  */
+#define SSSP_E_CUDA            (-7)  /* a CUDA runtime call failed                          */
+#define SSSP_E_ROUND_LIMIT     (-8)  /* more rounds than vertices: internal invariant broken */
+#define SSSP_E_BUSY            (-9)  /* server has no free slot / budget for this query      */
+#define SSSP_E_NOT_FOUND      (-10)  /* unknown ticket                                      */
+#define SSSP_PENDING            1    /* sssp_serve_poll: query still running                 */
+
+#define SSSP_DIST_INF UINT64_MAX
+
+/* Lower-bound clamp used in step (b).
+ *   SSSP_RULE_THRESHOLD: C[y] >= min(D[y], threshold), the combination of
+ *     Lemma 7 (crule2) and Lemma 8 (Crauser et al. out-version); subsumes
+ *     SP_4 step 2's "fix D <= threshold".
+ *   SSSP_RULE_MIND: C[y] >= minD over the unfixed set (SP_4 step 4 as
+ *     printed) plus SP_4 step 2 (fix D <= threshold).  Same distances, the
+ *     round count may differ. */
+#define SSSP_RULE_THRESHOLD 0u
+#define SSSP_RULE_MIND      1u
+
+/* How the per-round kernels are sequenced. */
+#define SSSP_LOOP_GRAPH 0u  /* one CUDA graph with a device-side while loop (default) */
+#define SSSP_LOOP_HOST  1u  /* host launches rounds in groups and polls a status word  */
+
+typedef struct sssp_graph* sssp_handle;
+typedef struct sssp_server sssp_server;
+
+/* Device-memory allocator hook.  alloc returns a device pointer aligned to at
+ * least 256 bytes or NULL; free releases it.  Both are called only from
+ * sssp_create / sssp_destroy / sssp_serve_open / sssp_serve_close.  NULL
+ * hooks mean cudaMalloc / cudaFree. */
+typedef void* (*sssp_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*sssp_free_fn)(void* ptr, void* ctx);
+
+typedef struct sssp_options {
+    uint32_t rule;           /* SSSP_RULE_*                                                */
+    uint32_t loop_mode;      /* SSSP_LOOP_*                                                */
+    uint32_t hub_degree;     /* vertices of degree > hub_degree are split into chunks
+                                processed by many warps (0 = library default, 256)         */
+    uint32_t chunk_edges;    /* edges per hub chunk (0 = default 512, must be a multiple
+                                of 32)                                                     */
+    uint32_t block_threads;  /* threads per CTA of the round kernels (0 = 256)             */
+    uint32_t ctas_per_sm;    /* CTAs per SM of the round kernels (0 = from occupancy)      */
+    int32_t device;          /* CUDA device ordinal (-1 = the calling thread's current)    */
+    uint32_t reserved;
+    sssp_alloc_fn alloc;     /* NULL = cudaMalloc                                          */
+    sssp_free_fn free;       /* NULL = cudaFree                                            */
+    void* alloc_ctx;
+} sssp_options;
+
+/* Fills *opt with the defaults described above. */
+void sssp_options_default(sssp_options* opt);
+
+/* Builds a device-resident graph (Sec. II: out-edges for relaxation; Sec. IV:
+ * in-edges, needed by the lower-bound rule of Lemma 6).
+ *   n        number of vertices, 1 <= n < 2^32 - 1
+ *   m        number of edges (entries of col / w)
+ *   row_ptr  host u64[n+1], CSR offsets: out-edges of u are
+ *            col[row_ptr[u] .. row_ptr[u+1]); row_ptr[0] = 0, row_ptr[n] = m,
+ *            non-decreasing
+ *   col      host u32[m], edge targets (< n)
+ *   w        host u32[m], edge weights (> 0)
+ *   col_ptr, row, w_in: optional host CSC of the same edge multiset (in-edges
+ *            of v are row/w_in[col_ptr[v] .. col_ptr[v+1])); pass all three
+ *            NULL to have the library transpose on the device.
+ *   opt      NULL for defaults.
+ * Self-loops (u, u) are dropped (Sec. II assumes a loop-free graph; a loop
+ * never lies on a shortest path).  Multi-edges are kept.  Vertices without
+ * in-edges are allowed (they are unreachable unless they are the source).
+ * Errors: SSSP_E_INVAL, SSSP_E_ZERO_WEIGHT, SSSP_E_OVERFLOW (when
+ * n * max(w) >= 2^(64 - ceil(log2 n)) - 1: distance and parent share one
+ * 64-bit word), SSSP_E_NOMEM, SSSP_E_CUDA.  *out is set only on success. */
+int sssp_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t* col,
+                const uint32_t* w, const uint64_t* col_ptr, const uint32_t* row,
+                const uint32_t* w_in, const sssp_options* opt, sssp_handle* out);
+
+/* Single-source shortest paths from `source` (Sec. VI, rounds until no vertex
+ * is left to explore).  dist_out: host u64[n], written on success.
+ * rounds_out (nullable): number of rounds executed (relaxation steps,
+ * including the last one that finds nothing new).  Blocks until done.
+ * Errors: SSSP_E_INVAL, SSSP_E_SOURCE_RANGE, SSSP_E_ROUND_LIMIT, SSSP_E_CUDA. */
+int sssp_solve(sssp_handle h, uint32_t source, uint64_t* dist_out, uint32_t* rounds_out);
+
+/* Same as sssp_solve, but dist_dev is a device u64[n] and the work is
+ * enqueued on `cuda_stream` (a cudaStream_t; NULL = the legacy default
+ * stream).  If rounds_out is NULL the call returns without synchronising;
+ * otherwise it waits for the stream and reports the round count. */
+int sssp_solve_device(sssp_handle h, uint32_t source, uint64_t* dist_dev, uint32_t* rounds_out,
+                      void* cuda_stream);
+
+/* Optional outputs and counters of one solve (all output pointers nullable;
+ * "dev" selects device pointers instead of host pointers). */
+typedef struct sssp_solve_args {
+    uint64_t* dist;          /* u64[n]: cost[x] or SSSP_DIST_INF                           */
+    uint32_t* parent;        /* u32[n]: predecessor on a shortest path (source: itself;
+                                unreachable: UINT32_MAX); among equal distances the
+                                smallest predecessor id                                    */
+    int32_t* fixed_round;    /* i32[n]: round in which x was fixed (source 0, never: -1)   */
+    uint64_t* lower;         /* u64[n]: final lower bound C[x]                             */
+    uint32_t max_rounds;     /* stop after this many rounds (0 = run to completion); the
+                                outputs then hold the state after that round               */
+    uint32_t dev;            /* 1: output pointers are device pointers                     */
+    void* cuda_stream;       /* stream for the work (NULL = legacy default stream)         */
+} sssp_solve_args;
+
+typedef struct sssp_solve_info {
+    uint32_t rounds;         /* rounds executed                                            */
+    uint32_t finished;       /* 1 if no vertex was left to explore                          */
+    uint64_t reached;        /* vertices fixed (reachable, source included)                */
+    uint64_t out_scanned;    /* out-edges scanned by step (a)                              */
+    uint64_t in_scanned;     /* in-edges scanned by step (b)                               */
+    uint64_t active_visits;  /* sum over rounds of the discovered-unfixed set size         */
+    uint64_t front_visits;   /* sum over rounds of the frontier size                       */
+} sssp_solve_info;
+
+/* General form of sssp_solve.  Synchronises the stream before returning.
+ * info (nullable) receives the counters. */
+int sssp_solve_ex(sssp_handle h, uint32_t source, const sssp_solve_args* args,
+                  sssp_solve_info* info);
+
+/* k independent queries solved together in lock-step rounds by the same
+ * kernels: query i is (g[i], sources[i]); g[i] may repeat (many sources on
+ * one graph) or differ (many graphs).  Each query's rounds depend only on its
+ * own graph and source, so every result equals the one sssp_solve returns.
+ * All handles must live on the same device and be created with the same
+ * options.  dist_out[i]: host u64[n_i]; rounds_out: host u32[k] (nullable).
+ * Errors: as sssp_solve, plus SSSP_E_NOMEM for the batch workspace. */
+int sssp_solve_batch(const sssp_handle* g, const uint32_t* sources, uint32_t k,
+                     uint64_t* const* dist_out, uint32_t* rounds_out);
+
+/* Device-pointer form of sssp_solve_batch: dist_dev[i] is a device u64[n_i].
+ * Synchronises `cuda_stream` before returning. */
+int sssp_solve_batch_device(const sssp_handle* g, const uint32_t* sources, uint32_t k,
+                            uint64_t* const* dist_dev, uint32_t* rounds_out, void* cuda_stream);
+
+/* Continuous-batching query server.  Queries (graph handle, source) are
+ * admitted into free slots while earlier queries are in flight, as long as
+ * their state fits the device-memory budget; all admitted queries advance
+ * together, a few rounds per step, on one stream owned by the server.  A
+ * query's result does not depend on which other queries share its rounds. */
+typedef struct sssp_serve_cfg {
+    uint64_t budget_bytes;   /* device bytes for query state (0 = 32 GiB)                  */
+    uint32_t max_slots;      /* queries in flight at once (0 = 1024)                       */
+    uint32_t rounds_per_step;/* rounds per device step between admissions (0 = 8)          */
+    int32_t device;          /* -1 = current                                               */
+    uint32_t reserved;
+    sssp_alloc_fn alloc;     /* NULL = cudaMalloc (one allocation of budget_bytes)         */
+    sssp_free_fn free;
+    void* alloc_ctx;
+} sssp_serve_cfg;
+
+/* Opens a server.  The graphs passed to sssp_serve_submit must stay alive
+ * until their queries complete.  Errors: SSSP_E_INVAL, SSSP_E_NOMEM. */
+int sssp_serve_open(const sssp_serve_cfg* cfg, sssp_server** out);
+
+/* Queues a query.  dist_out: host u64[n] written when the query completes
+ * (owned by the caller, must stay valid until sssp_serve_poll reports it
+ * done).  *ticket identifies the query.  Does not block on the device.
+ * Errors: SSSP_E_INVAL, SSSP_E_SOURCE_RANGE, SSSP_E_BUSY (the query alone
+ * exceeds the budget). */
+int sssp_serve_submit(sssp_server* s, sssp_handle g, uint32_t source, uint64_t* dist_out,
+                      uint64_t* ticket);
+
+/* Advances the server by one step (admission, a few rounds, retirement) and
+ * reports on `ticket`: SSSP_OK when its dist_out is written (rounds_out set,
+ * nullable), SSSP_PENDING while it is queued or running, SSSP_E_NOT_FOUND
+ * for an unknown or already reported ticket. */
+int sssp_serve_poll(sssp_server* s, uint64_t ticket, uint32_t* rounds_out);
+
+/* Runs the server until every submitted query is complete. */
+int sssp_serve_drain(sssp_server* s);
+
+/* Closes the server; queries still in flight are abandoned. */
+void sssp_serve_close(sssp_server* s);
+
+/* Releases a graph and its device memory.  NULL is ignored. */
+void sssp_destroy(sssp_handle h);
+
+/* Static string naming an SSSP_* status code. */
+const char* sssp_strerror(int code);
+
+/* Number of vertices / edges (after self-loop removal) of a handle. */
+uint32_t sssp_num_vertices(sssp_handle h);
+uint64_t sssp_num_edges(sssp_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSSP_H */

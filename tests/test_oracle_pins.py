@@ -1,0 +1,340 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each check ties the oracle to a fact fixed by the paper or by mathematics:
+the worked example printed in Sec. III / Sec. IV, textbook shortest-path
+algorithms (Bellman-Ford, Floyd-Warshall, brute-force path enumeration,
+scipy's Dijkstra), closed forms (BFS depth on unit weights, Manhattan
+distance on a unit grid) and the invariants of Lemmas 6-8 (C <= cost <= D
+after every round).  test_oracle_mutants.py shows that plausible mistakes in
+oracle.c fail at least one of these checks.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from tests.golden.fixtures import worked_example
+
+INF = int(oracle.INF)
+
+
+# ----------------------------------------------------------------- helpers
+
+def edges_of(g):
+    src, col, w = g.edges()
+    return list(zip(src.tolist(), col.tolist(), w.tolist()))
+
+
+def brute_force_dist(g, s):
+    """Minimum over all simple paths by explicit enumeration (tiny graphs)."""
+    adj = {u: [] for u in range(g.n)}
+    for u, v, w in edges_of(g):
+        if u != v:
+            adj[u].append((v, w))
+    best = [INF] * g.n
+    best[s] = 0
+
+    def dfs(u, cost, seen):
+        for v, w in adj[u]:
+            if v in seen:
+                continue
+            c = cost + w
+            if c < best[v]:
+                best[v] = c
+            dfs(v, c, seen | {v})
+
+    dfs(s, 0, {s})
+    return np.array(best, dtype=np.uint64)
+
+
+def bfs_depth(g, s):
+    depth = np.full(g.n, -1, dtype=np.int64)
+    depth[s] = 0
+    frontier = [s]
+    while frontier:
+        nxt = []
+        for u in frontier:
+            for k in range(int(g.row_ptr[u]), int(g.row_ptr[u + 1])):
+                v = int(g.col[k])
+                if depth[v] < 0:
+                    depth[v] = depth[u] + 1
+                    nxt.append(v)
+        frontier = nxt
+    return depth
+
+
+def random_small(n, deg, wmax, seed):
+    return gg.random_graph(n, deg, 1, wmax, seed)
+
+
+SMALL_CASES = [(n, d, wmax, seed) for n, d, wmax in
+               [(2, 1, 3), (5, 2, 3), (8, 3, 5), (17, 2, 10), (33, 4, 100), (64, 6, 1000)]
+               for seed in range(3)]
+
+
+# ------------------------------------------------------- worked example pins
+
+@pytest.mark.parametrize("variant", ["A", "B"])
+def test_worked_example(variant):
+    ex = worked_example()[variant]
+    g = gg.from_edges(ex["n"], ex["edges"])
+    s = ex["source"]
+    assert oracle.dijkstra(g, s)[0].tolist() == ex["dist"]
+    d1, ops1 = oracle.sp1(g, s)
+    d2, ops2 = oracle.sp2(g, s)
+    assert d1.tolist() == ex["dist"] and d2.tolist() == ex["dist"]
+    assert ops1["inserts"] == ex["sp1_inserts"] and ops1["outer"] == ex["sp1_outer"]
+    assert ops2["inserts"] == ex["sp2_inserts"] and ops2["outer"] == ex["sp2_outer"]
+    r = oracle.round_r(g, s)
+    assert r.dist.tolist() == ex["dist"]
+    assert r.fixed_round.tolist() == ex["fixed_round"]
+    assert r.parent.tolist() == ex["parent"]
+    assert r.rounds == ex["rounds"]
+
+
+@pytest.mark.parametrize("variant", ["threshold", "jacobi", "inclamp"])
+def test_hand_derived_round_traces(variant):
+    """Round traces derived by hand from Lemma 8 and the Jacobi reading of
+    SP_4 step 4 (see the comments in tests/golden/worked_example.txt)."""
+    ex = worked_example()[variant]
+    g = gg.from_edges(ex["n"], ex["edges"])
+    r = oracle.round_r(g, ex["source"])
+    assert r.dist.tolist() == ex["dist"]
+    assert r.fixed_round.tolist() == ex["fixed_round"]
+    assert r.parent.tolist() == ex["parent"]
+    assert r.rounds == ex["rounds"]
+
+
+# ---------------------------------------- distances vs textbook algorithms
+
+def test_exhaustive_three_vertex_digraphs():
+    """Every digraph on 3 vertices with weights in {1,2,3} (4^6 graphs), every
+    source: Dijkstra = Bellman-Ford = Floyd-Warshall = enumeration = Round R."""
+    pairs = [(u, v) for u in range(3) for v in range(3) if u != v]
+    lib = oracle.load()
+    for choice in itertools.product(range(4), repeat=len(pairs)):
+        edges = [(u, v, c) for (u, v), c in zip(pairs, choice) if c]
+        g = gg.from_edges(3, edges)
+        for s in range(3):
+            ref = brute_force_dist(g, s)
+            assert np.array_equal(oracle.dijkstra(g, s, lib=lib)[0], ref)
+            assert np.array_equal(oracle.bellman_ford(g, s, lib=lib), ref)
+            assert np.array_equal(oracle.floyd_warshall(g, s, lib=lib), ref)
+            assert np.array_equal(oracle.round_r(g, s, lib=lib).dist, ref)
+
+
+@pytest.mark.parametrize("case", SMALL_CASES)
+def test_distances_agree(case):
+    n, d, wmax, seed = case
+    g = random_small(n, d, wmax, seed)
+    scipy_sp = pytest.importorskip("scipy.sparse.csgraph")
+    import scipy.sparse as sp
+    for s in range(min(n, 4)):
+        dj, _ = oracle.dijkstra(g, s)
+        assert np.array_equal(dj, oracle.bellman_ford(g, s))
+        assert np.array_equal(dj, oracle.floyd_warshall(g, s))
+        if n <= 8:
+            assert np.array_equal(dj, brute_force_dist(g, s))
+        # scipy's Dijkstra keeps the minimum of parallel edges when summing
+        # duplicates is avoided; build the matrix from the min weight per pair.
+        src, col, w = g.edges()
+        M = {}
+        for u, v, ww in zip(src.tolist(), col.tolist(), w.tolist()):
+            M[(u, v)] = min(M.get((u, v), ww), ww)
+        mat = sp.csr_matrix((np.array(list(M.values()), dtype=np.float64),
+                             ([k[0] for k in M], [k[1] for k in M])), shape=(n, n))
+        ref = scipy_sp.dijkstra(mat, directed=True, indices=s)
+        fin = ~np.isinf(ref)
+        assert np.array_equal(dj == INF, ~fin)
+        assert np.array_equal(dj[fin], ref[fin].astype(np.uint64))
+        for mode in (oracle.RULE_THR, oracle.RULE_MIND, oracle.LABEL_CORRECT,
+                     oracle.LABEL_CORRECT | oracle.RULE_MIND):
+            assert np.array_equal(oracle.round_r(g, s, mode=mode).dist, dj)
+        assert np.array_equal(oracle.sp1(g, s)[0], dj)
+        assert np.array_equal(oracle.sp2(g, s)[0], dj)
+
+
+def test_transpose_is_the_same_edge_multiset():
+    g = gg.random_var_graph(300, 1, 9, 1, 50, 7)
+    col_ptr, row, w_in = oracle.transpose(g)
+    fwd = sorted(edges_of(g))
+    bwd = sorted((int(row[k]), v, int(w_in[k]))
+                 for v in range(g.n) for k in range(int(col_ptr[v]), int(col_ptr[v + 1])))
+    assert fwd == bwd
+
+
+# ---------------------------------------------------- Round R invariants
+
+def check_round_invariants(g, s, mode=oracle.RULE_THR, lib=None):
+    cost, _ = oracle.dijkstra(g, s, lib=lib)
+    seen = []
+
+    def on_round(r, thr, minD, D, C, F):
+        fixed = F >= 0
+        # Lemmas 6-8: every C is a lower bound, every D an upper bound.
+        assert np.all(C <= cost), f"round {r}: C > cost"
+        assert np.all(D >= cost), f"round {r}: D < cost"
+        # Fixed vertices carry their final cost (Lemma 1(a) analogue).
+        assert np.all(D[fixed] == cost[fixed]) and np.all(C[fixed] == cost[fixed])
+        # Fixing is C = D (SP_4 step 5).
+        unf = ~fixed & (D != INF)
+        assert np.all(C[unf] < D[unf])
+        seen.append(int(np.count_nonzero(F == r)))
+
+    r = oracle.round_r(g, s, mode=mode, on_round=on_round, lib=lib)
+    reach = cost != INF
+    assert np.array_equal(r.dist, cost)
+    assert np.array_equal(r.fixed_round >= 0, reach)
+    # every round but the last fixes at least one vertex
+    assert all(c >= 1 for c in seen[:-1]) and seen[-1] == 0
+    assert r.rounds == len(seen) <= max(1, int(reach.sum()))
+    assert r.stats["reached"] == int(reach.sum())
+    # parent edges are tight and come from vertices fixed earlier
+    for v in np.flatnonzero(reach):
+        p = int(r.parent[v])
+        if v == s:
+            assert p == s
+            continue
+        ws = [int(g.w[k]) for k in range(int(g.row_ptr[p]), int(g.row_ptr[p + 1]))
+              if int(g.col[k]) == v]
+        assert ws and int(cost[p]) + min(ws) == int(cost[v])
+        assert r.fixed_round[p] < r.fixed_round[v]
+    return r
+
+
+@pytest.mark.parametrize("case", SMALL_CASES)
+@pytest.mark.parametrize("mode", [oracle.RULE_THR, oracle.RULE_MIND])
+def test_round_invariants(case, mode):
+    n, d, wmax, seed = case
+    g = random_small(n, d, wmax, seed)
+    for s in range(min(n, 3)):
+        check_round_invariants(g, s, mode)
+
+
+def test_round_invariants_skewed():
+    g = gg.rmat(10, 8, 1, 255, 3)
+    s = int(np.argmax(g.out_degree()))
+    check_round_invariants(g, s)
+
+
+def test_threshold_rule_fixes_at_least_as_fast_as_mind_rule():
+    """min(D, threshold) >= minD, so the THR clamp never fixes later."""
+    for seed in range(5):
+        g = random_small(200, 4, 100, seed)
+        a = oracle.round_r(g, 0, mode=oracle.RULE_THR)
+        b = oracle.round_r(g, 0, mode=oracle.RULE_MIND)
+        ok = (a.fixed_round >= 0)
+        assert np.all(a.fixed_round[ok] <= b.fixed_round[ok])
+
+
+# ------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("seed", range(4))
+def test_unit_weights_is_bfs(seed):
+    """Unit weights: the vertex at BFS depth k is fixed in round k and the
+    number of rounds is the eccentricity plus one (the last round relaxes the
+    deepest layer and finds nothing)."""
+    g = gg.random_graph(500, 3, 1, 1, seed)
+    for s in (0, 7):
+        depth = bfs_depth(g, s)
+        r = oracle.round_r(g, s)
+        reach = depth >= 0
+        assert np.array_equal(r.dist[reach], depth[reach].astype(np.uint64))
+        assert np.array_equal(r.fixed_round[reach], depth[reach])
+        assert r.rounds == int(depth.max()) + 1
+
+
+@pytest.mark.parametrize("rows,cols", [(1, 1), (1, 9), (7, 5), (16, 16), (33, 20)])
+def test_unit_grid_closed_form(rows, cols):
+    g = gg.grid(rows, cols, 1, 1, 0)
+    r = oracle.round_r(g, 0)
+    i, j = np.divmod(np.arange(rows * cols), cols)
+    assert np.array_equal(r.dist, (i + j).astype(np.uint64))
+    assert r.rounds == (rows - 1) + (cols - 1) + 1
+
+
+def test_weighted_grid_distances():
+    g = gg.grid(20, 30, 1, 10000, 5)
+    dj, _ = oracle.dijkstra(g, 0)
+    assert np.array_equal(oracle.bellman_ford(g, 0), dj)
+    check_round_invariants(g, 0)
+
+
+# -------------------------------------------------- SP_1 / SP_2 heap claims
+
+@pytest.mark.parametrize("seed", range(4))
+def test_sp1_dag_needs_no_heap_operation(seed):
+    """Theorem 2: on a DAG in which only the source lacks in-edges (after the
+    Sec. III pruning), SP_1 inserts only the source and never adjusts."""
+    g = gg.dag(30, 40, 4, 4, 1, 1000, seed)
+    dist, ops = oracle.sp1(g, 0, prune_first=True)
+    assert np.array_equal(dist, oracle.dijkstra(g, 0)[0])
+    assert ops["inserts"] + ops["adjusts"] == 1
+    d2, ops2 = oracle.sp2(g, 0, prune_first=True)
+    assert np.array_equal(d2, dist) and ops2["inserts"] + ops2["adjusts"] == 1
+
+
+def test_prune_removes_exactly_the_vertices_without_paths_from_in_degree_zero():
+    g = gg.from_edges(6, [(0, 1, 1), (2, 3, 1), (3, 4, 1), (4, 1, 1), (5, 5, 1)])
+    removed = oracle.prune(g, 0)
+    # 2 has no in-edge -> removed, then 3, then 4; 5 only has a self-loop
+    # (stripped, Sec. II) -> removed; 1 keeps the edge from 0.
+    assert removed.tolist() == [0, 0, 1, 1, 1, 1]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_sp1_sp2_use_no_more_heap_operations_than_dijkstra(seed):
+    """Sec. I / Sec. III: SP_1 and SP_2 never perform more heap inserts and
+    adjusts than Dijkstra's algorithm."""
+    g = gg.random_graph(300, 3, 1, 20, seed)
+    _, dj = oracle.dijkstra(g, 0)
+    _, o1 = oracle.sp1(g, 0)
+    _, o2 = oracle.sp2(g, 0)
+    base = dj["inserts"] + dj["adjusts"]
+    assert o1["inserts"] + o1["adjusts"] <= base
+    assert o2["inserts"] + o2["adjusts"] <= base
+
+
+def test_sp2_unweighted_counterexample():
+    """Theorem 3 claims SP_2 is O(e) (no heap use) on unweighted graphs.  With
+    d read as the key of the last removeMin, unit weights s->a->b->x->b force
+    a heap insert: when b is discovered, D[b] = 2 > d + inWeight[b] = 0 + 1."""
+    g = gg.from_edges(4, [(0, 1, 1), (1, 2, 1), (2, 3, 1), (3, 2, 1)])
+    dist, ops = oracle.sp2(g, 0)
+    assert dist.tolist() == [0, 1, 2, 3]
+    assert ops["inserts"] >= 2
+
+
+def test_reduction_after_relaxation_reading():
+    """SP_4 as printed computes threshold before relaxing; if the vertices
+    fixed in the previous step are not yet explored this fixes b with
+    D[b] = 5 > cost 2.  The oracle takes the minima after the relaxation."""
+    g = gg.from_edges(5, [(0, 1, 1), (0, 2, 5), (1, 2, 1), (2, 3, 1), (3, 4, 100)])
+    for mode in (oracle.RULE_THR, oracle.RULE_MIND, oracle.LABEL_CORRECT):
+        assert oracle.round_r(g, 0, mode=mode).dist.tolist() == [0, 1, 2, 3, 103]
+
+
+def test_termination_reading():
+    """SP_4's printed loop test (some discovered vertex unfixed) would stop
+    after s->a if a is fixed at once; the oracle runs while a frontier is
+    left, so b is still reached."""
+    g = gg.from_edges(3, [(0, 1, 1), (1, 2, 1)])
+    r = oracle.round_r(g, 0)
+    assert r.dist.tolist() == [0, 1, 2] and r.rounds == 3
+
+
+def test_unreachable_and_isolated():
+    g = gg.from_edges(4, [(1, 2, 3), (2, 1, 3)])
+    r = oracle.round_r(g, 0)
+    assert r.dist.tolist() == [0, INF, INF, INF]
+    assert r.fixed_round.tolist() == [0, -1, -1, -1]
+    assert r.rounds == 1
+
+
+def test_multi_edges_and_self_loops():
+    g = gg.from_edges(3, [(0, 1, 5), (0, 1, 2), (1, 1, 1), (1, 2, 4), (1, 2, 9)])
+    assert oracle.round_r(g, 0).dist.tolist() == [0, 2, 6]
+    with pytest.raises(ValueError):
+        oracle.round_r(gg.from_edges(2, [(0, 1, 0)]), 0)
