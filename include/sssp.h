@@ -49,6 +49,7 @@ extern "C" {
 #define SSSP_E_ROUND_LIMIT     (-8)  /* more rounds than vertices: internal invariant broken */
 #define SSSP_E_BUSY            (-9)  /* server has no free slot / budget for this query      */
 #define SSSP_E_NOT_FOUND      (-10)  /* unknown ticket                                      */
+#define SSSP_E_INTERNAL       (-11)  /* a device-side consistency guard tripped (library bug) */
 #define SSSP_PENDING            1    /* sssp_serve_poll: query still running                 */
 
 #define SSSP_DIST_INF UINT64_MAX

@@ -1,0 +1,326 @@
+"""Python binding of libsssp.so, the GB300 library for Garg's bound-based
+single-source shortest paths (arXiv 1812.10499).
+
+Argument marshalling only: every function has the name of the C entry point
+it calls (include/sssp.h) and every step of the computation runs in the CUDA
+kernels of the library.  There is no CPU fallback: if the library has not
+been built, load() raises.
+
+PyTorch is used only as plumbing: optional device memory through its caching
+allocator (torch_allocator_options) and streams / device tensors for the
+_device entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsssp.so")
+
+SSSP_OK = 0
+SSSP_PENDING = 1
+SSSP_RULE_THRESHOLD = 0
+SSSP_RULE_MIND = 1
+SSSP_LOOP_GRAPH = 0
+SSSP_LOOP_HOST = 1
+SSSP_DIST_INF = 0xFFFFFFFFFFFFFFFF
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class sssp_options(ctypes.Structure):
+    _fields_ = [("rule", ctypes.c_uint32), ("loop_mode", ctypes.c_uint32),
+                ("hub_degree", ctypes.c_uint32), ("chunk_edges", ctypes.c_uint32),
+                ("block_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("device", ctypes.c_int32), ("reserved", ctypes.c_uint32),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class sssp_solve_args(ctypes.Structure):
+    _fields_ = [("dist", ctypes.c_void_p), ("parent", ctypes.c_void_p),
+                ("fixed_round", ctypes.c_void_p), ("lower", ctypes.c_void_p),
+                ("max_rounds", ctypes.c_uint32), ("dev", ctypes.c_uint32),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class sssp_solve_info(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_uint32), ("finished", ctypes.c_uint32),
+                ("reached", ctypes.c_uint64), ("out_scanned", ctypes.c_uint64),
+                ("in_scanned", ctypes.c_uint64), ("active_visits", ctypes.c_uint64),
+                ("front_visits", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class sssp_serve_cfg(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_uint32),
+                ("rounds_per_step", ctypes.c_uint32), ("device", ctypes.c_int32),
+                ("reserved", ctypes.c_uint32), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", ctypes.c_void_p)]
+
+
+class SsspError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {sssp_strerror(code)} ({code})")
+
+
+_lib = None
+# ctypes callbacks must outlive the handles that use them.
+_keepalive: dict = {}
+
+
+def load(path: str = LIB_PATH):
+    """Loads libsssp.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(the CUDA library is required; there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    vp, u32, u64, i32, c_int = (ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                                ctypes.c_int32, ctypes.c_int)
+    sig = {
+        "sssp_options_default": (None, [ctypes.POINTER(sssp_options)]),
+        "sssp_create": (c_int, [u32, u64, vp, vp, vp, vp, vp, vp,
+                                ctypes.POINTER(sssp_options), ctypes.POINTER(vp)]),
+        "sssp_solve": (c_int, [vp, u32, vp, ctypes.POINTER(u32)]),
+        "sssp_solve_device": (c_int, [vp, u32, vp, ctypes.POINTER(u32), vp]),
+        "sssp_solve_ex": (c_int, [vp, u32, ctypes.POINTER(sssp_solve_args),
+                                  ctypes.POINTER(sssp_solve_info)]),
+        "sssp_solve_batch": (c_int, [vp, vp, u32, vp, vp]),
+        "sssp_solve_batch_device": (c_int, [vp, vp, u32, vp, vp, vp]),
+        "sssp_serve_open": (c_int, [ctypes.POINTER(sssp_serve_cfg), ctypes.POINTER(vp)]),
+        "sssp_serve_submit": (c_int, [vp, vp, u32, vp, ctypes.POINTER(u64)]),
+        "sssp_serve_poll": (c_int, [vp, u64, ctypes.POINTER(u32)]),
+        "sssp_serve_drain": (c_int, [vp]),
+        "sssp_serve_close": (None, [vp]),
+        "sssp_destroy": (None, [vp]),
+        "sssp_strerror": (ctypes.c_char_p, [c_int]),
+        "sssp_num_vertices": (u32, [vp]),
+        "sssp_num_edges": (u64, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str):
+    if rc != SSSP_OK:
+        raise SsspError(rc, what)
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def sssp_strerror(code: int) -> str:
+    return load().sssp_strerror(code).decode()
+
+
+def sssp_options_default() -> sssp_options:
+    o = sssp_options()
+    load().sssp_options_default(ctypes.byref(o))
+    return o
+
+
+def torch_allocator_options(opt: sssp_options | None = None, device: int | None = None):
+    """Options whose allocator hooks take device memory from PyTorch's CUDA
+    caching allocator."""
+    import torch
+
+    opt = opt or sssp_options_default()
+    dev = torch.cuda.current_device() if device is None else device
+
+    def _alloc(nbytes, _ctx):
+        return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev)
+
+    def _free(ptr, _ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    opt.alloc = ALLOC_FN(_alloc)
+    opt.free = FREE_FN(_free)
+    opt.device = dev
+    _keepalive[id(opt)] = (opt.alloc, opt.free)
+    return opt
+
+
+def _contig(a, dtype):
+    if a is None:
+        return None
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def sssp_create(n: int, row_ptr, col, w, col_ptr=None, row=None, w_in=None,
+                options: sssp_options | None = None) -> int:
+    """Device-resident graph from a host CSR (and optional CSC); returns the handle."""
+    lib = load()
+    row_ptr = _contig(row_ptr, np.uint64)
+    col, w = _contig(col, np.uint32), _contig(w, np.uint32)
+    col_ptr, row, w_in = _contig(col_ptr, np.uint64), _contig(row, np.uint32), _contig(w_in, np.uint32)
+    m = int(row_ptr[-1]) if row_ptr is not None and len(row_ptr) else 0
+    if row_ptr is None or len(row_ptr) != n + 1 or len(col) != m or len(w) != m:
+        raise SsspError(-1, "sssp_create")
+    h = ctypes.c_void_p()
+    rc = lib.sssp_create(n, m, _ptr(row_ptr), _ptr(col) if m else None, _ptr(w) if m else None,
+                         _ptr(col_ptr), _ptr(row) if row is not None and m else None,
+                         _ptr(w_in) if w_in is not None and m else None,
+                         ctypes.byref(options) if options is not None else None, ctypes.byref(h))
+    _check(rc, "sssp_create")
+    if options is not None and id(options) in _keepalive:
+        _keepalive[h.value] = _keepalive[id(options)]
+    return h.value
+
+
+def sssp_destroy(h: int):
+    if h:
+        load().sssp_destroy(h)
+        _keepalive.pop(h, None)
+
+
+def sssp_num_vertices(h: int) -> int:
+    return load().sssp_num_vertices(h)
+
+
+def sssp_num_edges(h: int) -> int:
+    return load().sssp_num_edges(h)
+
+
+def sssp_solve(h: int, source: int):
+    """Returns (dist u64[n], rounds)."""
+    lib = load()
+    dist = np.empty(lib.sssp_num_vertices(h), dtype=np.uint64)
+    rounds = ctypes.c_uint32(0)
+    _check(lib.sssp_solve(h, source, _ptr(dist), ctypes.byref(rounds)), "sssp_solve")
+    return dist, int(rounds.value)
+
+
+def sssp_solve_device(h: int, source: int, dist_dev, stream=None, want_rounds: bool = False):
+    """dist_dev: a CUDA tensor (u64/int64, n entries).  Enqueues on `stream`
+    (a torch.cuda.Stream or raw handle); returns the round count only if
+    want_rounds (which synchronises)."""
+    lib = load()
+    rounds = ctypes.c_uint32(0)
+    rc = lib.sssp_solve_device(h, source, _ptr(dist_dev),
+                               ctypes.byref(rounds) if want_rounds else None, _stream_ptr(stream))
+    _check(rc, "sssp_solve_device")
+    return int(rounds.value) if want_rounds else None
+
+
+def sssp_solve_ex(h: int, source: int, *, dist=True, parent=False, fixed_round=False,
+                  lower=False, max_rounds: int = 0, stream=None) -> dict:
+    """Host outputs chosen by flag, plus the solve counters."""
+    lib = load()
+    n = lib.sssp_num_vertices(h)
+    out = {}
+    a = sssp_solve_args()
+    if dist:
+        out["dist"] = np.empty(n, dtype=np.uint64)
+        a.dist = out["dist"].ctypes.data
+    if parent:
+        out["parent"] = np.empty(n, dtype=np.uint32)
+        a.parent = out["parent"].ctypes.data
+    if fixed_round:
+        out["fixed_round"] = np.empty(n, dtype=np.int32)
+        a.fixed_round = out["fixed_round"].ctypes.data
+    if lower:
+        out["lower"] = np.empty(n, dtype=np.uint64)
+        a.lower = out["lower"].ctypes.data
+    a.max_rounds = max_rounds
+    a.dev = 0
+    a.cuda_stream = _stream_ptr(stream)
+    info = sssp_solve_info()
+    _check(lib.sssp_solve_ex(h, source, ctypes.byref(a), ctypes.byref(info)), "sssp_solve_ex")
+    out["info"] = info.as_dict()
+    return out
+
+
+def _handle_array(handles):
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    return arr
+
+
+def sssp_solve_batch(handles, sources):
+    """k queries in one lock-step launch; returns (list of dist arrays, rounds u32[k])."""
+    lib = load()
+    k = len(handles)
+    src = np.ascontiguousarray(sources, dtype=np.uint32)
+    dists = [np.empty(lib.sssp_num_vertices(h), dtype=np.uint64) for h in handles]
+    ptrs = (ctypes.c_void_p * k)(*[d.ctypes.data for d in dists])
+    rounds = np.zeros(k, dtype=np.uint32)
+    _check(lib.sssp_solve_batch(_handle_array(handles), src.ctypes.data, k, ptrs,
+                                rounds.ctypes.data), "sssp_solve_batch")
+    return dists, rounds
+
+
+def sssp_solve_batch_device(handles, sources, dist_devs, stream=None):
+    """Device-output form; dist_devs are CUDA tensors.  Returns rounds u32[k]."""
+    lib = load()
+    k = len(handles)
+    src = np.ascontiguousarray(sources, dtype=np.uint32)
+    ptrs = (ctypes.c_void_p * k)(*[_ptr(d) for d in dist_devs])
+    rounds = np.zeros(k, dtype=np.uint32)
+    _check(lib.sssp_solve_batch_device(_handle_array(handles), src.ctypes.data, k, ptrs,
+                                       rounds.ctypes.data, _stream_ptr(stream)),
+           "sssp_solve_batch_device")
+    return rounds
+
+
+def sssp_serve_open(budget_bytes: int = 0, max_slots: int = 0, rounds_per_step: int = 0,
+                    device: int = -1) -> int:
+    cfg = sssp_serve_cfg()
+    cfg.budget_bytes = budget_bytes
+    cfg.max_slots = max_slots
+    cfg.rounds_per_step = rounds_per_step
+    cfg.device = device
+    s = ctypes.c_void_p()
+    _check(load().sssp_serve_open(ctypes.byref(cfg), ctypes.byref(s)), "sssp_serve_open")
+    return s.value
+
+
+def sssp_serve_submit(server: int, h: int, source: int, dist_out: np.ndarray) -> int:
+    """Queues a query; dist_out (u64[n], host) is written when it completes."""
+    t = ctypes.c_uint64(0)
+    _check(load().sssp_serve_submit(server, h, source, dist_out.ctypes.data, ctypes.byref(t)),
+           "sssp_serve_submit")
+    return int(t.value)
+
+
+def sssp_serve_poll(server: int, ticket: int):
+    """Returns (status, rounds): status SSSP_OK when done, SSSP_PENDING otherwise."""
+    r = ctypes.c_uint32(0)
+    rc = load().sssp_serve_poll(server, ticket, ctypes.byref(r))
+    if rc not in (SSSP_OK, SSSP_PENDING):
+        raise SsspError(rc, "sssp_serve_poll")
+    return rc, int(r.value)
+
+
+def sssp_serve_drain(server: int):
+    _check(load().sssp_serve_drain(server), "sssp_serve_drain")
+
+
+def sssp_serve_close(server: int):
+    if server:
+        load().sssp_serve_close(server)

@@ -1,0 +1,720 @@
+// sssp_api.cu -- host engine and C ABI (include/sssp.h) of the GB300
+// bound-based SSSP library (Garg, arXiv 1812.10499).
+//
+// A handle owns the device-resident graph (CSR out-edges, CSC in-edges,
+// outWeight) and a single-query solve context.  Solving launches three setup
+// kernels, the round loop, and one output kernel; the loop is a CUDA graph
+// with a device-side while node whose condition the last CTA of each round
+// sets, so a solve costs one graph launch whatever its round count.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "sssp_engine.h"
+
+using namespace sssp;
+using namespace sssp::engine;
+
+namespace sssp {
+namespace engine {
+
+int occupancy_grid(int device, const sssp_options& o) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    int per = (int)o.ctas_per_sm;
+    if (per <= 0) per = std::max(1, round_blocks_per_sm(kThreads));
+    return std::max(1, sms) * per;
+}
+
+int scan_excl(u64* in, u64 cnt, u64* out, u64* tmp, cudaStream_t st) {
+    const u32 tiles = (u32)((cnt + kScanTile - 1) / kScanTile);
+    k_scan_tiles<<<tiles, kThreads, 0, st>>>(in, cnt, tmp);
+    k_scan_sums<<<1, kThreads, 0, st>>>(tmp, tiles);
+    k_scan_apply<<<tiles, kThreads, 0, st>>>(in, cnt, tmp, out);
+    CK(cudaGetLastError());
+    return SSSP_OK;
+}
+
+// Builds the device-side while loop: body = relax -> cupdate.
+int build_loop(Context& c) {
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        CK(e);
+    }
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    e = cudaGraphAddNode(&cnode, g, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        CK(e);
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    RoundParams P = c.P;
+    P.cond = h;
+    void* args[] = {&P};
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void*>(relax_fn(c.multi));
+    kp.gridDim = dim3(c.grid);
+    kp.blockDim = dim3(kThreads);
+    kp.kernelParams = args;
+    cudaGraphNode_t n1, n2;
+    e = cudaGraphAddKernelNode(&n1, body, nullptr, 0, &kp);
+    if (e == cudaSuccess) {
+        kp.func = const_cast<void*>(cupdate_fn(c.multi));
+        e = cudaGraphAddKernelNode(&n2, body, &n1, 1, &kp);
+    }
+    cudaGraphExec_t x = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        CK(e);
+    }
+    c.graph = g;
+    c.exec = x;
+    return SSSP_OK;
+}
+
+// Runs rounds until the device loop stops (all queries done, stop round hit,
+// or an error).
+int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
+    if (loop_mode == SSSP_LOOP_GRAPH) {
+        if (!c.exec) RC(build_loop(c));
+        CK(cudaGraphLaunch(c.exec, st));
+        return SSSP_OK;
+    }
+    const void* fr = relax_fn(c.multi);
+    const void* fc = cupdate_fn(c.multi);
+    RoundParams P = c.P;
+    P.cond = 0;
+    void* args[] = {&P};
+    for (;;) {
+        for (int i = 0; i < 16; ++i) {
+            CK(cudaLaunchKernel(fr, dim3(c.grid), dim3(kThreads), args, 0, st));
+            CK(cudaLaunchKernel(fc, dim3(c.grid), dim3(kThreads), args, 0, st));
+        }
+        CK(cudaMemcpyAsync(c.h_ctl, c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (c.h_ctl->status != kRunning || c.h_ctl->round > c.h_ctl->stop_round) break;
+    }
+    return SSSP_OK;
+}
+
+int alloc_lists(Context& c, u64 capS, u64 capH) {
+    capH = std::max<u64>(capH, 1);
+    for (int i = 0; i < 2; ++i) {
+        RC(c.pool.get(&c.P.L.FS[i], capS));
+        RC(c.pool.get(&c.P.L.AS[i], capS));
+        RC(c.pool.get(&c.P.L.FH[i], capH));
+        RC(c.pool.get(&c.P.L.AH[i], capH));
+    }
+    RC(c.pool.get(&c.P.L.hubmin, capH));
+    RC(c.pool.get(&c.P.L.hubcnt, capH));
+    c.P.L.capS = (u32)std::min<u64>(capS, 0xFFFFFFFFull);
+    c.P.L.capH = (u32)std::min<u64>(capH, 0xFFFFFFFFull);
+    c.capH = c.P.L.capH;
+    return SSSP_OK;
+}
+
+int alloc_pinned(Context& c, u32 slots) {
+    CK(cudaHostAlloc((void**)&c.h_ctl, sizeof(Ctl), cudaHostAllocDefault));
+    CK(cudaHostAlloc((void**)&c.h_ivar, sizeof(InstVar) * slots, cudaHostAllocDefault));
+    return SSSP_OK;
+}
+
+int init_single_context(sssp_graph* h) {
+    Context& c = h->single;
+    c.pool.al = Allocator{h->opt.alloc, h->opt.free, h->opt.alloc_ctx};
+    c.multi = false;
+    c.nrec = h->n;
+    c.nslots = 1;
+    c.grid = h->grid;
+    RoundParams& P = c.P;
+    P.g.out_off = h->out_off;
+    P.g.out_adj = h->out_adj;
+    P.g.in_off = h->in_off;
+    P.g.in_adj = h->in_adj;
+    P.g.outw = h->outw;
+    P.g.base = 0;
+    P.g.n = h->n;
+    P.g.source = 0;
+    RC(c.pool.get(&P.rec, h->n));
+    RC(c.pool.get(&P.ctl, 1));
+    RC(c.pool.get(&P.ivar, 1));
+    RC(c.pool.get(&c.stage, h->n));
+    RC(alloc_lists(c, h->n, std::max(h->hubs_in, h->hubs_out)));
+    P.dinf = h->dinf;
+    P.vbits = h->vbits;
+    P.hub = h->opt.hub_degree;
+    P.chunk = h->opt.chunk_edges;
+    P.rule = h->opt.rule;
+    P.page_shift = kPageShift;
+    RC(alloc_pinned(c, 1));
+    CK(cudaMemsetAsync(P.L.hubmin, 0xFF, sizeof(u64) * c.capH, h->stream));
+    CK(cudaMemsetAsync(P.L.hubcnt, 0, sizeof(u32) * c.capH, h->stream));
+    return SSSP_OK;
+}
+
+int validate_csr(u32 n, u64 m, const u64* off, const u32* idx, const u32* w, u32* wmax) {
+    if (!off || (m && (!idx || !w))) return SSSP_E_INVAL;
+    if (off[0] != 0 || off[n] != m) return SSSP_E_INVAL;
+    u32 mx = 0;
+    for (u32 u = 0; u < n; ++u)
+        if (off[u + 1] < off[u]) return SSSP_E_INVAL;
+    for (u64 k = 0; k < m; ++k) {
+        if (idx[k] >= n) return SSSP_E_INVAL;
+        if (w[k] == 0) return SSSP_E_ZERO_WEIGHT;
+        mx = std::max(mx, w[k]);
+    }
+    *wmax = mx;
+    return SSSP_OK;
+}
+
+// Copies a CSR without its self-loops (Sec. II: the graph is loop-free).
+// `src_of_row` is true for CSR (row = source), false for CSC (row = target);
+// the loop test is the same either way.
+void strip_loops(u32 n, const u64* off, const u32* idx, const u32* w, std::vector<u64>& o2,
+                 std::vector<u32>& i2, std::vector<u32>& w2) {
+    o2.assign((size_t)n + 1, 0);
+    i2.clear();
+    w2.clear();
+    i2.reserve(off[n]);
+    w2.reserve(off[n]);
+    for (u32 u = 0; u < n; ++u) {
+        o2[u] = i2.size();
+        for (u64 k = off[u]; k < off[u + 1]; ++k) {
+            if (idx[k] == u) continue;
+            i2.push_back(idx[k]);
+            w2.push_back(w[k]);
+        }
+    }
+    o2[n] = i2.size();
+}
+
+bool has_loop(u32 n, const u64* off, const u32* idx) {
+    for (u32 u = 0; u < n; ++u)
+        for (u64 k = off[u]; k < off[u + 1]; ++k)
+            if (idx[k] == u) return true;
+    return false;
+}
+
+int upload_adj(sssp_graph* h, const u32* idx, const u32* w, u64 m, uint2* adj) {
+    if (m == 0) return SSSP_OK;
+    Pool tmp;
+    tmp.al = h->gpool.al;
+    u32 *d_i = nullptr, *d_w = nullptr;
+    int rc = tmp.get(&d_i, m);
+    if (rc == SSSP_OK) rc = tmp.get(&d_w, m);
+    if (rc == SSSP_OK) {
+        cudaError_t e = cudaMemcpyAsync(d_i, idx, sizeof(u32) * m, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_w, w, sizeof(u32) * m, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) {
+            k_interleave<<<h->grid, kThreads, 0, h->stream>>>(d_i, d_w, m, adj);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            rc = SSSP_E_CUDA;
+        }
+    }
+    tmp.release();
+    return rc;
+}
+
+int create_impl(sssp_graph* h, u32 n, u64 m, const u64* row_ptr, const u32* col, const u32* w,
+                const u64* col_ptr, const u32* row, const u32* w_in) {
+    u32 wmax = 0;
+    RC(validate_csr(n, m, row_ptr, col, w, &wmax));
+    const bool csc_given = col_ptr || row || w_in;
+    if (csc_given) {
+        if (!(col_ptr && (m == 0 || (row && w_in)))) return SSSP_E_INVAL;
+        u32 wmax2 = 0;
+        RC(validate_csr(n, m, col_ptr, row, w_in, &wmax2));
+        if (wmax2 != wmax) return SSSP_E_INVAL;
+    }
+    h->vbits = std::max<u32>(1, bits_for((u64)n - 1));
+    h->dinf = (~0ull) >> h->vbits;
+    // Every finite quantity of a round (D, C, lb + w, D + outWeight) stays
+    // below n * wmax; it must stay below the infinity of the packed word.
+    if (wmax && (unsigned __int128)n * wmax >= (unsigned __int128)h->dinf) return SSSP_E_OVERFLOW;
+    h->wmax = wmax;
+
+    std::vector<u64> o2, c2;
+    std::vector<u32> i2, w2, r2, wi2;
+    if (has_loop(n, row_ptr, col)) {
+        strip_loops(n, row_ptr, col, w, o2, i2, w2);
+        row_ptr = o2.data();
+        col = i2.data();
+        w = w2.data();
+        m = o2[n];
+        if (csc_given) {
+            strip_loops(n, col_ptr, row, w_in, c2, r2, wi2);
+            col_ptr = c2.data();
+            row = r2.data();
+            w_in = wi2.data();
+            if (c2[n] != m) return SSSP_E_INVAL;
+        }
+    }
+    h->n = n;
+    h->m = m;
+
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->grid = occupancy_grid(h->device, h->opt);
+    Pool& gp = h->gpool;
+    RC(gp.get(&h->out_off, (size_t)n + 1));
+    RC(gp.get(&h->in_off, (size_t)n + 1));
+    RC(gp.get(&h->out_adj, std::max<u64>(m, 1)));
+    RC(gp.get(&h->in_adj, std::max<u64>(m, 1)));
+    RC(gp.get(&h->outw, n));
+    CK(cudaMemcpyAsync(h->out_off, row_ptr, sizeof(u64) * ((size_t)n + 1), cudaMemcpyHostToDevice,
+                       h->stream));
+    RC(upload_adj(h, col, w, m, h->out_adj));
+    if (csc_given) {
+        CK(cudaMemcpyAsync(h->in_off, col_ptr, sizeof(u64) * ((size_t)n + 1),
+                           cudaMemcpyHostToDevice, h->stream));
+        RC(upload_adj(h, row, w_in, m, h->in_adj));
+    } else {
+        // K0: transpose on the device (histogram, exclusive scan, scatter).
+        Pool tmp;
+        tmp.al = gp.al;
+        u64 *cnt = nullptr, *cursor = nullptr, *sums = nullptr;
+        const u64 cntn = (u64)n + 1;
+        int rc = tmp.get(&cnt, cntn);
+        if (rc == SSSP_OK) rc = tmp.get(&cursor, cntn);
+        if (rc == SSSP_OK) rc = tmp.get(&sums, (cntn + kScanTile - 1) / kScanTile + 1);
+        cudaError_t e = cudaSuccess;
+        if (rc == SSSP_OK) {
+            e = cudaMemsetAsync(cnt, 0, sizeof(u64) * cntn, h->stream);
+            if (e == cudaSuccess && m) {
+                k_count_in<<<h->grid, kThreads, 0, h->stream>>>(h->out_adj, m, cnt);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) rc = scan_excl(cnt, cntn, h->in_off, sums, h->stream);
+            if (rc == SSSP_OK && e == cudaSuccess)
+                e = cudaMemcpyAsync(cursor, h->in_off, sizeof(u64) * cntn, cudaMemcpyDeviceToDevice,
+                                    h->stream);
+            if (rc == SSSP_OK && e == cudaSuccess && m) {
+                k_scatter_in<<<h->grid, kThreads, 0, h->stream>>>(h->out_off, h->out_adj, n, cursor,
+                                                                  h->in_adj);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        }
+        tmp.release();
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return SSSP_E_CUDA;
+        }
+        RC(rc);
+    }
+    k_outw<<<h->grid, kThreads, 0, h->stream>>>(h->out_off, h->out_adj, n, h->outw);
+    CK(cudaGetLastError());
+    {
+        Pool tmp;
+        tmp.al = gp.al;
+        u32* cnt = nullptr;
+        RC(tmp.get(&cnt, 2));
+        u32 hc[2] = {0, 0};
+        cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(u32) * 2, h->stream);
+        if (e == cudaSuccess) {
+            k_count_hubs<<<h->grid, kThreads, 0, h->stream>>>(h->out_off, h->in_off, n,
+                                                              h->opt.hub_degree, cnt);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        tmp.release();
+        CK(e);
+        h->hubs_out = hc[0];
+        h->hubs_in = hc[1];
+    }
+    RC(init_single_context(h));
+    CK(cudaStreamSynchronize(h->stream));
+    return SSSP_OK;
+}
+
+void destroy_impl(sssp_graph* h) {
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->single.destroy();
+    if (h->batch) {
+        h->batch->destroy();
+        delete h->batch;
+        h->batch = nullptr;
+    }
+    h->gpool.release();
+    if (h->stream) cudaStreamDestroy(h->stream);
+    h->stream = nullptr;
+}
+
+int read_status(Context& c, cudaStream_t st, u32 ninst) {
+    CK(cudaMemcpyAsync(c.h_ctl, c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c.h_ivar, c.P.ivar, sizeof(InstVar) * ninst, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (c.h_ctl->error) return SSSP_E_INTERNAL;
+    if (c.h_ctl->status == kErrRounds) return SSSP_E_ROUND_LIMIT;
+    return SSSP_OK;
+}
+
+// Enqueues one single-query solve on `st` (no synchronisation).
+int enqueue_single(sssp_graph* h, u32 source, u32 max_rounds, cudaStream_t st, u64* dist_dev,
+                   u32* parent_dev, int* fround_dev, u64* lower_dev) {
+    Context& c = h->single;
+    RoundParams P = c.P;
+    P.g.source = source;
+    c.P.g.source = source;
+    k_init_records<<<c.grid, kThreads, 0, st>>>(P.rec, h->outw, h->n);
+    k_reset_ctl<<<1, 32, 0, st>>>(P.ctl, 1, h->n + 2);
+    CK(launch_start(false, P, 0, 1, max_rounds, st));
+    RC(run_loop(c, h->opt.loop_mode, st));
+    k_finalize<<<c.grid, kThreads, 0, st>>>(P.rec, 0, h->n, h->vbits, P.ivar, dist_dev, parent_dev,
+                                            fround_dev, lower_dev);
+    CK(cudaGetLastError());
+    return SSSP_OK;
+}
+
+// ----------------------------------------------------------- multi-query
+
+int ensure_batch(sssp_graph* h0, u64 nrec, u32 nslots, u32 npages, u64 capH) {
+    Context* c = h0->batch;
+    if (c && c->nrec >= nrec && c->nslots >= nslots && c->npages >= npages && c->capH >= capH)
+        return SSSP_OK;
+    if (c) {
+        c->destroy();
+        delete c;
+        h0->batch = nullptr;
+    }
+    c = new (std::nothrow) Context();
+    if (!c) return SSSP_E_NOMEM;
+    h0->batch = c;
+    c->pool.al = Allocator{h0->opt.alloc, h0->opt.free, h0->opt.alloc_ctx};
+    c->multi = true;
+    c->nrec = nrec;
+    c->nslots = nslots;
+    c->npages = npages;
+    c->grid = h0->grid;
+    RoundParams& P = c->P;
+    RC(c->pool.get(&P.rec, nrec));
+    RC(c->pool.get(&P.ctl, 1));
+    RC(c->pool.get(&P.ivar, nslots));
+    InstDesc* idesc = nullptr;
+    u32* pages = nullptr;
+    RC(c->pool.get(&idesc, nslots));
+    RC(c->pool.get(&pages, npages));
+    P.idesc = idesc;
+    P.page_owner = pages;
+    RC(c->pool.get(&c->stage, nrec));
+    RC(alloc_lists(*c, nrec, capH));
+    P.page_shift = kPageShift;
+    P.hub = h0->opt.hub_degree;
+    P.chunk = h0->opt.chunk_edges;
+    P.rule = h0->opt.rule;
+    RC(alloc_pinned(*c, nslots));
+    CK(cudaHostAlloc((void**)&c->h_desc, sizeof(InstDesc) * nslots, cudaHostAllocDefault));
+    CK(cudaHostAlloc((void**)&c->h_pages, sizeof(u32) * npages, cudaHostAllocDefault));
+    CK(cudaMemsetAsync(P.L.hubmin, 0xFF, sizeof(u64) * c->capH, h0->stream));
+    CK(cudaMemsetAsync(P.L.hubcnt, 0, sizeof(u32) * c->capH, h0->stream));
+    CK(cudaStreamSynchronize(h0->stream));
+    return SSSP_OK;
+}
+
+int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist, bool dev,
+               u32* rounds_out, cudaStream_t st_user, bool use_user_stream) {
+    if (!g || !sources || !dist || k == 0) return SSSP_E_INVAL;
+    sssp_graph* h0 = g[0];
+    if (!h0) return SSSP_E_INVAL;
+    u32 vbits = 1;
+    u64 npages = 0, capH = 0;
+    for (u32 i = 0; i < k; ++i) {
+        if (!g[i] || !dist[i]) return SSSP_E_INVAL;
+        if (g[i]->device != h0->device || g[i]->opt.hub_degree != h0->opt.hub_degree ||
+            g[i]->opt.chunk_edges != h0->opt.chunk_edges || g[i]->opt.rule != h0->opt.rule)
+            return SSSP_E_INVAL;
+        if (sources[i] >= g[i]->n) return SSSP_E_SOURCE_RANGE;
+        vbits = std::max(vbits, g[i]->vbits);
+        npages += ((u64)g[i]->n + (1u << kPageShift) - 1) >> kPageShift;
+        capH += std::max(g[i]->hubs_in, g[i]->hubs_out);
+    }
+    const u64 nrec = npages << kPageShift;
+    if (nrec >= 0xFFFFFFFFull) return SSSP_E_NOMEM;   // list entries are 32-bit record ids
+    const u64 dinf = (~0ull) >> vbits;
+    for (u32 i = 0; i < k; ++i)
+        if (g[i]->wmax && (unsigned __int128)g[i]->n * g[i]->wmax >= (unsigned __int128)dinf)
+            return SSSP_E_OVERFLOW;
+    DeviceGuard dg(h0->device);
+    std::lock_guard<std::mutex> lk(h0->mu);
+    RC(ensure_batch(h0, nrec, k, (u32)npages, capH));
+    Context& c = *h0->batch;
+    cudaStream_t st = use_user_stream ? st_user : h0->stream;
+    RoundParams& P = c.P;
+    // The loop graph bakes the params in; rebuild it when they change.
+    if (c.exec && P.vbits != vbits) {
+        cudaGraphExecDestroy(c.exec);
+        cudaGraphDestroy(c.graph);
+        c.exec = nullptr;
+        c.graph = nullptr;
+    }
+    P.vbits = vbits;
+    P.dinf = dinf;
+    P.g = InstDesc{g[0]->out_off, g[0]->out_adj, g[0]->in_off, g[0]->in_adj, g[0]->outw, 0,
+                   g[0]->n, sources[0]};
+    u64 page = 0;
+    for (u32 i = 0; i < k; ++i) {
+        const sssp_graph* gi = g[i];
+        c.h_desc[i] = InstDesc{gi->out_off, gi->out_adj, gi->in_off, gi->in_adj, gi->outw,
+                               page << kPageShift, gi->n, sources[i]};
+        const u64 np = ((u64)gi->n + (1u << kPageShift) - 1) >> kPageShift;
+        for (u64 p = 0; p < np; ++p) c.h_pages[page + p] = i;
+        page += np;
+    }
+    CK(cudaMemcpyAsync((void*)P.idesc, c.h_desc, sizeof(InstDesc) * k, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync((void*)P.page_owner, c.h_pages, sizeof(u32) * npages, cudaMemcpyHostToDevice,
+                       st));
+    u32 max_n = 0;
+    for (u32 i = 0; i < k; ++i) max_n = std::max(max_n, g[i]->n);
+    k_init_records_multi<<<c.grid, kThreads, 0, st>>>(P, nrec, 0, (u32)npages);
+    k_reset_ctl<<<1, 32, 0, st>>>(P.ctl, k, max_n + 2);
+    CK(launch_start(true, P, 0, k, 0, st));
+    RC(run_loop(c, h0->opt.loop_mode, st));
+    k_finalize_multi<<<c.grid, kThreads, 0, st>>>(P, nrec, c.stage);
+    CK(cudaGetLastError());
+    for (u32 i = 0; i < k; ++i) {
+        const u64 base = c.h_desc[i].base;
+        if (dev) {
+            CK(cudaMemcpyAsync(dist[i], c.stage + base, sizeof(u64) * g[i]->n,
+                               cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    if (!dev) {
+        if (c.h_stage_n < nrec) {
+            if (c.h_stage) cudaFreeHost(c.h_stage);
+            c.h_stage = nullptr;
+            c.h_stage_n = 0;
+            CK(cudaHostAlloc((void**)&c.h_stage, sizeof(u64) * nrec, cudaHostAllocDefault));
+            c.h_stage_n = nrec;
+        }
+        CK(cudaMemcpyAsync(c.h_stage, c.stage, sizeof(u64) * nrec, cudaMemcpyDeviceToHost, st));
+    }
+    RC(read_status(c, st, k));
+    for (u32 i = 0; i < k; ++i) {
+        if (c.h_ivar[i].status != kDone) return SSSP_E_ROUND_LIMIT;
+        if (rounds_out) rounds_out[i] = c.h_ivar[i].rounds;
+        if (!dev) memcpy(dist[i], c.h_stage + c.h_desc[i].base, sizeof(u64) * g[i]->n);
+    }
+    return SSSP_OK;
+}
+
+}  // namespace engine
+}  // namespace sssp
+
+// ================================================================= C ABI
+
+extern "C" {
+
+void sssp_options_default(sssp_options* opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->rule = SSSP_RULE_THRESHOLD;
+    opt->loop_mode = SSSP_LOOP_GRAPH;
+    opt->hub_degree = kDefaultHub;
+    opt->chunk_edges = kDefaultChunk;
+    opt->block_threads = kThreads;
+    opt->ctas_per_sm = 0;
+    opt->device = -1;
+}
+
+int sssp_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t* col,
+                const uint32_t* w, const uint64_t* col_ptr, const uint32_t* row,
+                const uint32_t* w_in, const sssp_options* opt, sssp_handle* out) {
+    if (!out || n == 0 || n == 0xFFFFFFFFu || !row_ptr) return SSSP_E_INVAL;
+    sssp_options o;
+    sssp_options_default(&o);
+    if (opt) o = *opt;
+    if (o.hub_degree == 0) o.hub_degree = kDefaultHub;
+    if (o.chunk_edges == 0) o.chunk_edges = kDefaultChunk;
+    if (o.block_threads == 0) o.block_threads = kThreads;
+    if (o.rule > SSSP_RULE_MIND || o.loop_mode > SSSP_LOOP_HOST || o.chunk_edges % 32 != 0 ||
+        o.hub_degree > (1u << 20) || o.chunk_edges > (1u << 20) ||
+        o.block_threads != kThreads || (o.alloc == nullptr) != (o.free == nullptr))
+        return SSSP_E_INVAL;
+    {
+        // Host-side checks first: no device is touched for a malformed graph.
+        u32 wmax = 0, wmax2 = 0;
+        RC(validate_csr(n, m, reinterpret_cast<const u64*>(row_ptr), col, w, &wmax));
+        if (col_ptr || row || w_in) {
+            if (!(col_ptr && (m == 0 || (row && w_in)))) return SSSP_E_INVAL;
+            RC(validate_csr(n, m, reinterpret_cast<const u64*>(col_ptr), row, w_in, &wmax2));
+            if (wmax2 != wmax) return SSSP_E_INVAL;
+        }
+        const u32 vb = std::max<u32>(1, bits_for((u64)n - 1));
+        if (wmax && (unsigned __int128)n * wmax >= (unsigned __int128)((~0ull) >> vb))
+            return SSSP_E_OVERFLOW;
+    }
+    int dev = o.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return SSSP_E_CUDA;
+    }
+    sssp_graph* h = new (std::nothrow) sssp_graph();
+    if (!h) return SSSP_E_NOMEM;
+    h->device = dev;
+    h->opt = o;
+    h->opt.device = dev;
+    h->gpool.al = Allocator{o.alloc, o.free, o.alloc_ctx};
+    int rc;
+    {
+        DeviceGuard dg(dev);
+        rc = create_impl(h, n, m, reinterpret_cast<const u64*>(row_ptr), col, w,
+                         reinterpret_cast<const u64*>(col_ptr), row, w_in);
+        if (rc != SSSP_OK) destroy_impl(h);
+    }
+    if (rc != SSSP_OK) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return SSSP_OK;
+}
+
+void sssp_destroy(sssp_handle h) {
+    if (!h) return;
+    {
+        DeviceGuard dg(h->device);
+        destroy_impl(h);
+    }
+    delete h;
+}
+
+uint32_t sssp_num_vertices(sssp_handle h) { return h ? h->n : 0; }
+uint64_t sssp_num_edges(sssp_handle h) { return h ? h->m : 0; }
+
+int sssp_solve_ex(sssp_handle h, uint32_t source, const sssp_solve_args* args,
+                  sssp_solve_info* info) {
+    if (!h) return SSSP_E_INVAL;
+    if (source >= h->n) return SSSP_E_SOURCE_RANGE;
+    sssp_solve_args a{};
+    if (args) a = *args;
+    DeviceGuard dg(h->device);
+    std::lock_guard<std::mutex> lk(h->mu);
+    cudaStream_t st = a.cuda_stream ? (cudaStream_t)a.cuda_stream : h->stream;
+    Context& c = h->single;
+    u64* const a_dist = reinterpret_cast<u64*>(a.dist);
+    u64* const a_lower = reinterpret_cast<u64*>(a.lower);
+    u64* dist_dev = a.dev ? a_dist : (a_dist ? c.stage : nullptr);
+    // Host outputs other than dist go through device scratch in the lists
+    // (free after the solve): parent / fround use FS, lower uses AS.
+    u32* parent_dev = a.parent ? (a.dev ? a.parent : c.P.L.FS[0]) : nullptr;
+    int* fround_dev = a.fixed_round ? (a.dev ? a.fixed_round : (int*)c.P.L.FS[1]) : nullptr;
+    u64* lower_dev = (a_lower && a.dev) ? a_lower : nullptr;
+    Pool tmp;
+    tmp.al = c.pool.al;
+    if (a.lower && !a.dev) RC(tmp.get(&lower_dev, h->n));
+    int rc = enqueue_single(h, source, a.max_rounds, st, dist_dev, parent_dev, fround_dev, lower_dev);
+    if (rc == SSSP_OK) rc = read_status(c, st, 1);
+    if (rc == SSSP_OK && !a.dev) {
+        cudaError_t e = cudaSuccess;
+        if (a.dist)
+            e = cudaMemcpyAsync(a.dist, dist_dev, sizeof(u64) * h->n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && a.parent)
+            e = cudaMemcpyAsync(a.parent, parent_dev, sizeof(u32) * h->n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && a.fixed_round)
+            e = cudaMemcpyAsync(a.fixed_round, fround_dev, sizeof(int) * h->n,
+                                cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && a.lower)
+            e = cudaMemcpyAsync(a.lower, lower_dev, sizeof(u64) * h->n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            rc = SSSP_E_CUDA;
+        }
+    }
+    tmp.release();
+    if (rc != SSSP_OK) return rc;
+    const InstVar& v = c.h_ivar[0];
+    if (v.status != kDone && v.status != kStopped) return SSSP_E_ROUND_LIMIT;
+    if (info) {
+        info->rounds = v.rounds;
+        info->finished = v.status == kDone;
+        info->out_scanned = c.h_ctl->stats[0];
+        info->in_scanned = c.h_ctl->stats[1];
+        info->active_visits = c.h_ctl->stats[2];
+        info->front_visits = c.h_ctl->stats[3];
+        info->reached = c.h_ctl->stats[3];
+    }
+    return SSSP_OK;
+}
+
+int sssp_solve(sssp_handle h, uint32_t source, uint64_t* dist_out, uint32_t* rounds_out) {
+    if (!h || !dist_out) return SSSP_E_INVAL;
+    sssp_solve_args a{};
+    a.dist = dist_out;
+    sssp_solve_info info{};
+    RC(sssp_solve_ex(h, source, &a, &info));
+    if (rounds_out) *rounds_out = info.rounds;
+    return SSSP_OK;
+}
+
+int sssp_solve_device(sssp_handle h, uint32_t source, uint64_t* dist_dev, uint32_t* rounds_out,
+                      void* cuda_stream) {
+    if (!h || !dist_dev) return SSSP_E_INVAL;
+    if (source >= h->n) return SSSP_E_SOURCE_RANGE;
+    DeviceGuard dg(h->device);
+    std::lock_guard<std::mutex> lk(h->mu);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    RC(enqueue_single(h, source, 0, st, reinterpret_cast<u64*>(dist_dev), nullptr, nullptr,
+                      nullptr));
+    if (rounds_out) {
+        RC(read_status(h->single, st, 1));
+        if (h->single.h_ivar[0].status != kDone) return SSSP_E_ROUND_LIMIT;
+        *rounds_out = h->single.h_ivar[0].rounds;
+    }
+    return SSSP_OK;
+}
+
+int sssp_solve_batch(const sssp_handle* g, const uint32_t* sources, uint32_t k,
+                     uint64_t* const* dist_out, uint32_t* rounds_out) {
+    return batch_impl(g, sources, k, reinterpret_cast<u64* const*>(dist_out), false, rounds_out,
+                      nullptr, false);
+}
+
+int sssp_solve_batch_device(const sssp_handle* g, const uint32_t* sources, uint32_t k,
+                            uint64_t* const* dist_dev, uint32_t* rounds_out, void* cuda_stream) {
+    return batch_impl(g, sources, k, reinterpret_cast<u64* const*>(dist_dev), true, rounds_out,
+                      (cudaStream_t)cuda_stream, true);
+}
+
+const char* sssp_strerror(int code) {
+    switch (code) {
+        case SSSP_OK: return "ok";
+        case SSSP_PENDING: return "pending";
+        case SSSP_E_INVAL: return "invalid argument";
+        case SSSP_E_ZERO_WEIGHT: return "edge weight must be strictly positive";
+        case SSSP_E_SOURCE_RANGE: return "source vertex out of range";
+        case SSSP_E_OVERFLOW: return "n * max weight does not fit the packed distance word";
+        case SSSP_E_NOMEM: return "out of device memory or budget";
+        case SSSP_E_DEVICE_TIMEOUT: return "device-side wait timed out";
+        case SSSP_E_CUDA: return "CUDA runtime error";
+        case SSSP_E_ROUND_LIMIT: return "round limit exceeded";
+        case SSSP_E_BUSY: return "server busy";
+        case SSSP_E_NOT_FOUND: return "unknown ticket";
+        case SSSP_E_INTERNAL: return "internal consistency guard tripped";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

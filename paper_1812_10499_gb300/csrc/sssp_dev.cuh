@@ -1,0 +1,112 @@
+// sssp_dev.cuh -- device-side data layout shared by the round kernels and the
+// host engine of the GB300 bound-based SSSP library (Garg, arXiv 1812.10499).
+//
+// Per-query state lives in one 32-byte record per vertex (VRec), so the two
+// random accesses of a round -- the relaxation of an out-edge (Sec. VI, SP_4
+// step 3) and the lower-bound gather over an in-edge (Eq. 1) -- touch exactly
+// one 32-byte DRAM sector each.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sssp {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+// Packed upper bound: D word = (dist << vbits) | parent.  Equal distances keep
+// the smaller parent id (64-bit atomicMin).  All ones = infinity.
+constexpr u64 kInf64 = ~0ull;
+// Lower-bound words carry the "fixed" flag in bit 63 (C < 2^63 always).
+constexpr u64 kFixed = 1ull << 63;
+constexpr u64 kCMask = kFixed - 1;
+constexpr u32 kNoOutW = 0xFFFFFFFFu;   // vertex without out-edges
+
+// One vertex of one query.  cf[] is double-buffered by round parity: round r
+// reads cf[r & 1] (the lower bounds before the round: Jacobi update, SP_4
+// step 4 "in parallel") and writes cf[(r & 1) ^ 1].
+struct __align__(32) VRec {
+    u64 dp;        // packed upper bound D (atomicMin target)
+    u64 cf[2];     // lower bound C | kFixed
+    u32 outw;      // outWeight (Fig. SP_3 / SP_4 declarations), kNoOutW if none
+    int fround;    // round in which the vertex was fixed, -1 if not fixed
+};
+static_assert(sizeof(VRec) == 32, "VRec must be one 32-byte sector");
+
+// Read-only description of one query's graph.
+struct InstDesc {
+    const u64* out_off;     // CSR offsets, n + 1
+    const uint2* out_adj;   // {target, weight}
+    const u64* in_off;      // CSC offsets, n + 1
+    const uint2* in_adj;    // {source, weight}
+    const u32* outw;        // min out-weight per vertex
+    u64 base;               // global record index of local vertex 0
+    u32 n;
+    u32 source;
+};
+
+enum : u32 { kIdle = 0, kRunning = 1, kDone = 2, kStopped = 3, kErrRounds = 4 };
+
+// Mutable per-query scalars; slot [r & 1] belongs to round r.
+struct __align__(16) InstVar {
+    u64 thr[2];         // threshold = min over unfixed discovered of D + outWeight (Lemma 8)
+    u64 minD[2];        // min over unfixed discovered of D (Lemma 7)
+    u32 nfix[2];        // vertices fixed in the round
+    u32 start_round;    // engine round in which the query's round 1 runs
+    u32 rounds;         // rounds executed (set when the query stops)
+    u32 status;         // kIdle / kRunning / kDone / kStopped
+    u32 max_rounds;     // stop after this many rounds (0 = unlimited)
+};
+
+// Engine control block (one per solve context).
+struct __align__(16) Ctl {
+    u32 round;          // next engine round to execute
+    u32 status;         // kRunning while any query runs, kDone otherwise, kErrRounds
+    u32 running;        // queries still running after the last round
+    u32 stop_round;     // device loop stops after this round (serving steps)
+    u32 round_limit;    // hard cap; exceeding it is an internal error
+    u32 error;          // nonzero: a list capacity was exceeded (bug guard)
+    u32 nFS[2];         // frontier, small-degree entries
+    u32 nAS[2];         // active, small-degree entries
+    u64 FHpk[2];        // frontier hubs: (entries << 32) | chunks
+    u64 AHpk[2];        // active hubs: (entries << 32) | chunks
+    u32 work[2];        // dynamic work counters of the two round kernels
+    u32 done_ctas;      // arrival counter for the end-of-round epilogue
+    u32 ninst;          // number of query slots
+    u32 loop_iters;     // loop bodies started (watchdog against a stuck loop)
+    u32 pad1;
+    u64 stats[4];       // out-edges scanned, in-edges scanned, active visits, frontier visits
+};
+
+// Work lists.  Small-degree vertices are processed 32 per warp with a
+// warp-local load balance; vertices above the hub degree are split into
+// chunks of `chunk` edges handled by many warps.
+struct Lists {
+    u32* FS[2];
+    uint2* FH[2];   // {record index, first chunk}
+    u32* AS[2];
+    uint2* AH[2];
+    u64* hubmin;    // per active-hub entry: running min of Eq. (1) terms
+    u32* hubcnt;    // per active-hub entry: chunks finished
+    u32 capS, capH; // capacities of the small and hub lists
+};
+
+struct RoundParams {
+    InstDesc g;                 // the graph when a single query runs
+    const InstDesc* idesc;      // per-slot graphs (multi-query)
+    InstVar* ivar;              // per-slot scalars
+    const u32* page_owner;      // record page -> slot (multi-query)
+    VRec* rec;
+    Ctl* ctl;
+    Lists L;
+    u64 dinf;                   // distance infinity = 2^(64 - vbits) - 1
+    u32 vbits;                  // parent bits of the packed D word
+    u32 hub;                    // hub degree threshold
+    u32 chunk;                  // edges per hub chunk
+    u32 rule;                   // 0: min(D, threshold) clamp; 1: minD clamp
+    u32 page_shift;
+    u32 pad;
+    unsigned long long cond;    // cudaGraphConditionalHandle of the device loop, 0 = none
+};
+
+}  // namespace sssp

@@ -1,0 +1,195 @@
+// sssp_engine.h -- host-side structures shared by the engine translation
+// units (sssp_api.cu: graphs, single and batched solves; sssp_serve.cu:
+// continuous-batching server).  Internal; not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "sssp.h"
+#include "sssp_dev.cuh"
+
+namespace sssp {
+const void* relax_fn(bool multi);
+const void* cupdate_fn(bool multi);
+cudaError_t launch_start(bool multi, const RoundParams& P, u32 first, u32 count, u32 max_rounds,
+                         cudaStream_t st);
+int round_blocks_per_sm(int threads);
+__global__ void k_init_records(VRec* rec, const u32* outw, u32 n);
+__global__ void k_init_records_multi(RoundParams P, u64 nrec, u32 first_page, u32 npages);
+__global__ void k_reset_ctl(Ctl* ctl, u32 ninst, u32 round_limit);
+__global__ void k_finalize(const VRec* rec, u64 base, u32 n, u32 vbits, const InstVar* iv,
+                           u64* dist, u32* parent, int* fround, u64* lower);
+__global__ void k_finalize_multi(RoundParams P, u64 nrec, u64* dist);
+__global__ void k_interleave(const u32* col, const u32* w, u64 m, uint2* adj);
+__global__ void k_count_in(const uint2* adj, u64 m, u64* cnt);
+__global__ void k_scatter_in(const u64* out_off, const uint2* out_adj, u32 n, u64* cursor,
+                             uint2* in_adj);
+__global__ void k_outw(const u64* out_off, const uint2* out_adj, u32 n, u32* outw);
+__global__ void k_count_hubs(const u64* out_off, const u64* in_off, u32 n, u32 hub, u32* cnt);
+__global__ void k_scan_tiles(const u64* in, u64 cnt, u64* tile_sums);
+__global__ void k_scan_sums(u64* tile_sums, u32 ntiles);
+__global__ void k_scan_apply(const u64* in, u64 cnt, const u64* tile_sums, u64* out);
+constexpr u32 kScanTile = 2048;
+}  // namespace sssp
+
+namespace sssp {
+namespace engine {
+
+constexpr u32 kThreads = 256;
+constexpr u32 kPageShift = 10;
+constexpr u32 kDefaultHub = 256;
+constexpr u32 kDefaultChunk = 512;
+
+#define CK(call)                                       \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) {                       \
+            (void)cudaGetLastError();                  \
+            return SSSP_E_CUDA;                        \
+        }                                              \
+    } while (0)
+
+#define RC(call)                      \
+    do {                              \
+        int r_ = (call);              \
+        if (r_ != SSSP_OK) return r_; \
+    } while (0)
+
+struct Allocator {
+    sssp_alloc_fn fa = nullptr;
+    sssp_free_fn ff = nullptr;
+    void* ctx = nullptr;
+    void* get(size_t bytes) {
+        if (bytes == 0) bytes = 256;
+        if (fa) return fa(bytes, ctx);
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        return p;
+    }
+    void put(void* p) {
+        if (!p) return;
+        if (ff) ff(p, ctx);
+        else cudaFree(p);
+    }
+};
+
+// Device allocations of one owner, released together.
+struct Pool {
+    Allocator al;
+    std::vector<void*> ptrs;
+    template <class T>
+    int get(T** out, size_t count) {
+        void* p = al.get(count * sizeof(T));
+        if (!p) return SSSP_E_NOMEM;
+        ptrs.push_back(p);
+        *out = static_cast<T*>(p);
+        return SSSP_OK;
+    }
+    void release() {
+        for (void* p : ptrs) al.put(p);
+        ptrs.clear();
+    }
+};
+
+class DeviceGuard {
+   public:
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev_);
+        if (dev != prev_) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() { cudaSetDevice(prev_); }
+
+   private:
+    int prev_ = 0;
+};
+
+inline u32 bits_for(u64 x) {
+    u32 b = 0;
+    while (b < 64 && (x >> b)) ++b;
+    return b;
+}
+
+// Solve context: records, work lists, control block, per-query scalars and
+// the instantiated round loop.
+struct Context {
+    Pool pool;
+    bool multi = false;
+    u64 nrec = 0;            // records
+    u32 nslots = 0;          // query slots
+    u32 npages = 0;
+    u32 capH = 0;
+    RoundParams P{};
+    u64* stage = nullptr;    // device staging (distances)
+    Ctl* h_ctl = nullptr;    // pinned
+    InstVar* h_ivar = nullptr;
+    InstDesc* h_desc = nullptr;
+    u32* h_pages = nullptr;
+    u64* h_stage = nullptr;  // pinned staging for multi-query host outputs
+    u64 h_stage_n = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int grid = 0;
+
+    void destroy() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        if (h_ctl) cudaFreeHost(h_ctl);
+        if (h_ivar) cudaFreeHost(h_ivar);
+        if (h_desc) cudaFreeHost(h_desc);
+        if (h_pages) cudaFreeHost(h_pages);
+        if (h_stage) cudaFreeHost(h_stage);
+        h_ctl = nullptr;
+        h_ivar = nullptr;
+        h_desc = nullptr;
+        h_pages = nullptr;
+        h_stage = nullptr;
+        pool.release();
+    }
+};
+
+}  // namespace engine
+}  // namespace sssp
+
+struct sssp_graph {
+    typedef sssp::u32 u32;
+    typedef sssp::u64 u64;
+    int device = 0;
+    u32 n = 0;
+    u64 m = 0;
+    u32 vbits = 1;
+    u64 dinf = 0;
+    u32 wmax = 0;
+    u32 hubs_out = 0, hubs_in = 0;
+    sssp_options opt{};
+    sssp::engine::Pool gpool;        // graph arrays
+    u64* out_off = nullptr;
+    uint2* out_adj = nullptr;
+    u64* in_off = nullptr;
+    uint2* in_adj = nullptr;
+    u32* outw = nullptr;
+    cudaStream_t stream = nullptr;   // internal stream for setup and host-pointer solves
+    int grid = 0;
+    sssp::engine::Context single;    // single-query context
+    sssp::engine::Context* batch = nullptr;  // multi-query context (grown on demand)
+    std::mutex mu;
+};
+
+
+namespace sssp {
+namespace engine {
+int build_loop(Context& c);
+int run_loop(Context& c, u32 loop_mode, cudaStream_t st);
+int alloc_lists(Context& c, u64 capS, u64 capH);
+int alloc_pinned(Context& c, u32 slots);
+}  // namespace engine
+}  // namespace sssp

@@ -1,0 +1,131 @@
+"""Batched and served queries give, query by query, exactly the distances and
+round counts of the oracle (and of a solve on its own)."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def batch_graphs(count, seed, nmin=200, nmax=20000):
+    """Independent graphs of uneven size: n log-uniform, out-degree U{4..16}."""
+    u = gg.unit(seed, 1, count)
+    ns = np.round(np.exp(np.log(nmin) + u * (np.log(nmax) - np.log(nmin)))).astype(int)
+    graphs = [gg.random_var_graph(int(n), 4, 16, 1, 1000, seed * 1000 + i)
+              for i, n in enumerate(ns)]
+    srcs = [int(gg.uniform(seed, 2 + i, 1, 0, g.n - 1)[0]) for i, g in enumerate(graphs)]
+    return graphs, srcs
+
+
+def test_batch_independent_graphs(sssp_lib):
+    P = sssp_lib
+    graphs, srcs = batch_graphs(24, 3)
+    hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w) for g in graphs]
+    try:
+        dists, rounds = P.sssp_solve_batch(hs, srcs)
+        for g, s, d, r in zip(graphs, srcs, dists, rounds):
+            ref = oracle.round_r(g, s)
+            assert np.array_equal(d, ref.dist)
+            assert int(r) == ref.rounds
+        # Same again (the cached workspace is reused) and in another order.
+        perm = list(reversed(range(len(hs))))
+        dists2, rounds2 = P.sssp_solve_batch([hs[i] for i in perm], [srcs[i] for i in perm])
+        for j, i in enumerate(perm):
+            assert np.array_equal(dists2[j], dists[i]) and rounds2[j] == rounds[i]
+    finally:
+        for h in hs:
+            P.sssp_destroy(h)
+
+
+def test_batch_many_sources_one_graph(sssp_lib):
+    P = sssp_lib
+    g = gg.rmat(13, 16, 1, 255, 4)
+    cand = np.flatnonzero(g.out_degree() > 0)
+    srcs = [int(cand[int(i)]) for i in gg.uniform(4, 9, 16, 0, len(cand) - 1)]
+    h = P.sssp_create(g.n, g.row_ptr, g.col, g.w)
+    try:
+        dists, rounds = P.sssp_solve_batch([h] * len(srcs), srcs)
+        for s, d, r in zip(srcs, dists, rounds):
+            ref = oracle.round_r(g, s)
+            assert np.array_equal(d, ref.dist) and int(r) == ref.rounds
+    finally:
+        P.sssp_destroy(h)
+
+
+def test_batch_with_hubs(sssp_lib):
+    P = sssp_lib
+    o = P.sssp_options_default()
+    o.hub_degree = 8
+    o.chunk_edges = 32
+    graphs = [gg.rmat(11, 8, 1, 255, 20 + i) for i in range(5)]
+    srcs = [int(np.argmax(g.out_degree())) for g in graphs]
+    hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w, options=o) for g in graphs]
+    try:
+        dists, rounds = P.sssp_solve_batch(hs, srcs)
+        for g, s, d, r in zip(graphs, srcs, dists, rounds):
+            ref = oracle.round_r(g, s)
+            assert np.array_equal(d, ref.dist) and int(r) == ref.rounds
+    finally:
+        for h in hs:
+            P.sssp_destroy(h)
+
+
+def test_batch_device(sssp_lib):
+    torch = pytest.importorskip("torch")
+    P = sssp_lib
+    graphs, srcs = batch_graphs(6, 7)
+    hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w) for g in graphs]
+    try:
+        outs = [torch.empty(g.n, dtype=torch.int64, device="cuda") for g in graphs]
+        st = torch.cuda.Stream()
+        rounds = P.sssp_solve_batch_device(hs, srcs, outs, stream=st)
+        for g, s, d, r in zip(graphs, srcs, outs, rounds):
+            ref = oracle.round_r(g, s)
+            assert np.array_equal(d.cpu().numpy().view(np.uint64), ref.dist)
+            assert int(r) == ref.rounds
+    finally:
+        for h in hs:
+            P.sssp_destroy(h)
+
+
+def test_serve_alone_and_in_the_mix(sssp_lib):
+    """Queries submitted while others run are admitted as slots free up; each
+    result equals the oracle's and the query's solve on its own."""
+    P = sssp_lib
+    graphs, srcs = batch_graphs(16, 11, nmin=500, nmax=30000)
+    hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w) for g in graphs]
+    refs = [oracle.round_r(g, s) for g, s in zip(graphs, srcs)]
+    server = P.sssp_serve_open(budget_bytes=64 << 20, max_slots=4, rounds_per_step=3)
+    try:
+        outs, tickets = {}, {}
+        order = [int(i) for i in np.argsort(gg.uniform(11, 50, len(hs), 0, 1 << 30))]
+        done = {}
+        for step, i in enumerate(order):
+            outs[i] = np.zeros(graphs[i].n, dtype=np.uint64)
+            tickets[i] = P.sssp_serve_submit(server, hs[i], srcs[i], outs[i])
+            # poll a few outstanding tickets between submissions
+            for j in list(tickets):
+                if j in done:
+                    continue
+                st, r = P.sssp_serve_poll(server, tickets[j])
+                if st == P.SSSP_OK:
+                    done[j] = r
+                if step % 2 == 0:
+                    break
+        P.sssp_serve_drain(server)
+        for j in tickets:
+            if j not in done:
+                st, r = P.sssp_serve_poll(server, tickets[j])
+                assert st == P.SSSP_OK
+                done[j] = r
+        for i in range(len(hs)):
+            assert np.array_equal(outs[i], refs[i].dist), f"query {i}"
+            assert done[i] == refs[i].rounds
+            alone, r_alone = P.sssp_solve(hs[i], srcs[i])
+            assert np.array_equal(alone, outs[i]) and r_alone == done[i]
+    finally:
+        P.sssp_serve_close(server)
+        for h in hs:
+            P.sssp_destroy(h)

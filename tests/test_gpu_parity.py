@@ -1,0 +1,234 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Everything here is integer work, so the bar is bit-exact equality: distances,
+parents (smaller id among equal distances), the round in which every vertex
+was fixed, the final lower bounds C, the round count and the work counters.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from tests.golden.fixtures import worked_example
+
+pytestmark = pytest.mark.gpu
+
+INF = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def make_opts(P, **kw):
+    o = P.sssp_options_default()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def gpu_solve(P, g, s, max_rounds=0, **opt):
+    h = P.sssp_create(g.n, g.row_ptr, g.col, g.w, options=make_opts(P, **opt) if opt else None)
+    try:
+        return P.sssp_solve_ex(h, s, parent=True, fixed_round=True, lower=True,
+                               max_rounds=max_rounds)
+    finally:
+        P.sssp_destroy(h)
+
+
+def assert_parity(P, g, s, mode=oracle.RULE_THR, **opt):
+    if mode == oracle.RULE_MIND:
+        opt.setdefault("rule", P.SSSP_RULE_MIND)
+    ref = oracle.round_r(g, s, mode=mode)
+    out = gpu_solve(P, g, s, **opt)
+    assert np.array_equal(out["dist"], ref.dist)
+    assert np.array_equal(out["parent"], ref.parent)
+    assert np.array_equal(out["fixed_round"], ref.fixed_round)
+    assert np.array_equal(out["lower"], ref.C)
+    info = out["info"]
+    assert info["rounds"] == ref.rounds and info["finished"] == 1
+    assert info["out_scanned"] == ref.stats["out_scanned"]
+    assert info["in_scanned"] == ref.stats["in_scanned"]
+    assert info["active_visits"] == ref.stats["active_visits"]
+    assert info["front_visits"] == ref.stats["front_visits"]
+    assert info["reached"] == ref.stats["reached"]
+    return out, ref
+
+
+# ------------------------------------------------------------- fixtures
+
+@pytest.mark.parametrize("variant", ["A", "B", "threshold", "jacobi", "inclamp"])
+def test_worked_examples(sssp_lib, variant):
+    ex = worked_example()[variant]
+    g = gg.from_edges(ex["n"], ex["edges"])
+    out, _ = assert_parity(sssp_lib, g, ex["source"])
+    assert out["dist"].tolist() == ex["dist"]
+    assert out["fixed_round"].tolist() == ex["fixed_round"]
+    assert out["info"]["rounds"] == ex["rounds"]
+
+
+def test_random_4096_config(sssp_lib):
+    """Random directed graph n = 4096, 8 distinct out-edges, w in [1, 100], s = 0."""
+    g = gg.random_graph(4096, 8, 1, 100, 1812_10499)
+    assert_parity(sssp_lib, g, 0)
+    assert_parity(sssp_lib, g, 0, mode=oracle.RULE_MIND)
+    assert_parity(sssp_lib, g, 0, loop_mode=sssp_lib.SSSP_LOOP_HOST)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_graphs_many_tiles(sssp_lib, seed):
+    n = [37, 300, 1000, 5000, 20000, 70001][seed]
+    g = gg.random_var_graph(n, 1, 12, 1, [3, 100, 1000, 10, 255, 10000][seed], seed)
+    s = int(gg.uniform(seed, 0, 1, 0, n - 1)[0])
+    assert_parity(sssp_lib, g, s)
+
+
+@pytest.mark.parametrize("hub,chunk", [(4, 32), (8, 64), (31, 32), (32, 96)])
+def test_hub_paths(sssp_lib, hub, chunk):
+    """Small hub thresholds push many vertices through the chunked paths."""
+    g = gg.rmat(13, 8, 1, 255, hub)
+    s = int(np.argmax(g.out_degree()))
+    assert_parity(sssp_lib, g, s, hub_degree=hub, chunk_edges=chunk)
+    assert_parity(sssp_lib, g, s, mode=oracle.RULE_MIND, hub_degree=hub, chunk_edges=chunk)
+
+
+def test_degree_boundaries(sssp_lib):
+    """Degrees around the hub threshold (8) and chunk size (32)."""
+    edges = []
+    n = 400
+    k = 1
+    for deg in (7, 8, 9, 31, 32, 33, 64, 65, 100):
+        hubv = k
+        k += 1
+        edges.append((0, hubv, deg))
+        for j in range(deg):
+            leaf = k
+            k += 1
+            edges.append((hubv, leaf, 1 + (j % 5)))
+            edges.append((leaf, n - 1, 1 + (j % 7)))     # in-degree of n-1 grows large
+    for j in range(1, k):
+        edges.append((j, (j * 7) % k, 3))
+    g = gg.from_edges(n, [e for e in edges if e[0] != e[1]])
+    assert_parity(sssp_lib, g, 0, hub_degree=8, chunk_edges=32)
+    assert_parity(sssp_lib, g, 0)
+
+
+def test_star_hub_in_and_out(sssp_lib):
+    """Source with 100000 out-edges; a sink with in-degree 100000."""
+    n = 100_002
+    leaves = np.arange(1, n - 1, dtype=np.uint32)
+    w1 = (gg.uniform(1, 1, len(leaves), 1, 1000)).astype(np.uint32)
+    w2 = (gg.uniform(1, 2, len(leaves), 1, 1000)).astype(np.uint32)
+    src = np.concatenate([np.zeros(len(leaves), np.uint32), leaves])
+    dst = np.concatenate([leaves, np.full(len(leaves), n - 1, np.uint32)])
+    w = np.concatenate([w1, w2])
+    order = np.lexsort((dst, src))
+    row_ptr = np.zeros(n + 1, dtype=np.uint64)
+    np.add.at(row_ptr, src.astype(np.int64) + 1, 1)
+    g = gg.Graph(n, np.cumsum(row_ptr, dtype=np.uint64), dst[order], w[order])
+    assert_parity(sssp_lib, g, 0)
+
+
+def test_edge_cases(sssp_lib):
+    P = sssp_lib
+    # n = 1, no edges
+    assert_parity(P, gg.from_edges(1, []), 0)
+    # isolated vertices, source in the middle
+    assert_parity(P, gg.from_edges(5, []), 2)
+    # source without out-edges
+    assert_parity(P, gg.from_edges(4, [(1, 2, 3), (2, 3, 1)]), 0)
+    # two components
+    assert_parity(P, gg.from_edges(6, [(0, 1, 2), (1, 2, 2), (3, 4, 1), (4, 5, 1), (5, 3, 1)]), 0)
+    # multi-edges and self-loops (stripped, Sec. II)
+    g = gg.from_edges(4, [(0, 1, 5), (0, 1, 2), (1, 1, 1), (1, 2, 4), (1, 2, 9), (2, 3, 1),
+                          (3, 3, 7), (3, 0, 1)])
+    out, _ = assert_parity(P, g, 0)
+    assert out["dist"].tolist() == [0, 2, 6, 7]
+
+
+def test_per_round_state(sssp_lib):
+    """After every round r the device state equals the oracle's: D, C and the
+    rounds in which vertices were fixed (the state read with max_rounds = r)."""
+    g = gg.random_var_graph(700, 1, 6, 1, 50, 11)
+    snaps = []
+    oracle.round_r(g, 0, on_round=lambda r, thr, mD, D, C, F: snaps.append(
+        (D.copy(), C.copy(), F.copy())))
+    for r, (D, C, F) in enumerate(snaps, start=1):
+        out = gpu_solve(sssp_lib, g, 0, max_rounds=r)
+        assert out["info"]["rounds"] == r
+        assert np.array_equal(out["dist"], D), f"D after round {r}"
+        assert np.array_equal(out["lower"], C), f"C after round {r}"
+        assert np.array_equal(out["fixed_round"], F), f"fixed after round {r}"
+
+
+def test_unit_grid_closed_form(sssp_lib):
+    """Unit weights: BFS; a 300 x 200 grid from a corner needs 498 + 1 rounds."""
+    g = gg.grid(300, 200, 1, 1, 0)
+    out = gpu_solve(sssp_lib, g, 0)
+    i, j = np.divmod(np.arange(g.n), 200)
+    assert np.array_equal(out["dist"], (i + j).astype(np.uint64))
+    assert np.array_equal(out["fixed_round"], (i + j).astype(np.int32))
+    assert out["info"]["rounds"] == 299 + 199 + 1
+
+
+def test_weighted_grid_and_dag(sssp_lib):
+    assert_parity(sssp_lib, gg.grid(200, 150, 1, 10000, 3), 0)
+    assert_parity(sssp_lib, gg.dag(64, 512, 8, 4, 1, 1000, 2), 0)
+
+
+def test_solve_and_solve_device(sssp_lib):
+    torch = pytest.importorskip("torch")
+    P = sssp_lib
+    g = gg.rmat(14, 16, 1, 255, 9)
+    s = int(np.argmax(g.out_degree()))
+    ref = oracle.round_r(g, s)
+    h = P.sssp_create(g.n, g.row_ptr, g.col, g.w)
+    try:
+        d, r = P.sssp_solve(h, s)
+        assert np.array_equal(d, ref.dist) and r == ref.rounds
+        st = torch.cuda.Stream()
+        dd = torch.empty(g.n, dtype=torch.int64, device="cuda")
+        with torch.cuda.stream(st):
+            P.sssp_solve_device(h, s, dd, stream=st)
+        st.synchronize()
+        assert np.array_equal(dd.cpu().numpy().view(np.uint64), ref.dist)
+        assert P.sssp_solve_device(h, s, dd, stream=st, want_rounds=True) == ref.rounds
+    finally:
+        P.sssp_destroy(h)
+
+
+def test_given_csc_and_torch_allocator(sssp_lib):
+    torch = pytest.importorskip("torch")
+    P = sssp_lib
+    g = gg.random_var_graph(3000, 2, 9, 1, 77, 5)
+    col_ptr, row, w_in = oracle.transpose(g)
+    ref = oracle.round_r(g, 3)
+    before = torch.cuda.memory_allocated()
+    opt = P.torch_allocator_options()
+    h = P.sssp_create(g.n, g.row_ptr, g.col, g.w, col_ptr, row, w_in, options=opt)
+    try:
+        assert torch.cuda.memory_allocated() > before   # device memory came from torch
+        out = P.sssp_solve_ex(h, 3, fixed_round=True)
+        assert np.array_equal(out["dist"], ref.dist)
+        assert np.array_equal(out["fixed_round"], ref.fixed_round)
+    finally:
+        P.sssp_destroy(h)
+
+
+def test_source_range(sssp_lib):
+    P = sssp_lib
+    g = gg.random_graph(16, 2, 1, 5, 1)
+    h = P.sssp_create(g.n, g.row_ptr, g.col, g.w)
+    try:
+        with pytest.raises(P.SsspError) as e:
+            P.sssp_solve(h, 16)
+        assert e.value.code == -3
+    finally:
+        P.sssp_destroy(h)
+
+
+@pytest.mark.slow
+def test_rmat22_full_size(sssp_lib):
+    """R-MAT scale 22, edge factor 16, w in [1, 255], one source of the
+    benchmark's eight: bit-exact distances, fixing rounds and counters."""
+    g = gg.rmat(22, 16, 1, 255, 1812_10499 + 1)
+    outdeg = g.out_degree()
+    cand = np.flatnonzero(outdeg > 0)
+    s = int(cand[int(gg.uniform(1812_10499 + 1, 7, 1, 0, len(cand) - 1)[0])])
+    assert_parity(sssp_lib, g, s)
