@@ -219,6 +219,29 @@ int sssp_serve_drain(sssp_server* s);
 /* Closes the server; queries still in flight are abandoned. */
 void sssp_serve_close(sssp_server* s);
 
+/* Per-kernel timing of the round kernels (tracing; the paper has no
+ * counterpart).  While enabled on a handle, its single-query solves launch
+ * the rounds from the host and bracket every k_relax / k_cupdate launch with
+ * CUDA events on the solve stream; launches after the last round are not
+ * counted.  Results are bit-identical to the default device loop. */
+typedef struct sssp_kernel_profile {
+    uint64_t relax_launches;
+    uint64_t cupdate_launches;
+    double relax_ms;         /* summed event time of k_relax launches    */
+    double cupdate_ms;       /* summed event time of k_cupdate launches  */
+} sssp_kernel_profile;
+
+/* enable: 1 = on, 0 = off.  out (nullable) receives the totals gathered
+ * since the last call, which are then reset.  Errors: SSSP_E_INVAL. */
+int sssp_profile(sssp_handle h, int enable, sssp_kernel_profile* out);
+
+/* Per-round event times of the most recent profiled solve: round i's
+ * k_relax / k_cupdate milliseconds go to relax_ms[i] / cupdate_ms[i] for
+ * i < cap; *count receives the number of rounds recorded.
+ * Errors: SSSP_E_INVAL. */
+int sssp_profile_rounds(sssp_handle h, float* relax_ms, float* cupdate_ms, uint32_t cap,
+                        uint32_t* count);
+
 /* Releases a graph and its device memory.  NULL is ignored. */
 void sssp_destroy(sssp_handle h);
 

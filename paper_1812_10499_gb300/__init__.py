@@ -57,6 +57,14 @@ class sssp_solve_info(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class sssp_kernel_profile(ctypes.Structure):
+    _fields_ = [("relax_launches", ctypes.c_uint64), ("cupdate_launches", ctypes.c_uint64),
+                ("relax_ms", ctypes.c_double), ("cupdate_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class sssp_serve_cfg(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_uint32),
                 ("rounds_per_step", ctypes.c_uint32), ("device", ctypes.c_int32),
@@ -101,6 +109,8 @@ def load(path: str = LIB_PATH):
         "sssp_serve_poll": (c_int, [vp, u64, ctypes.POINTER(u32)]),
         "sssp_serve_drain": (c_int, [vp]),
         "sssp_serve_close": (None, [vp]),
+        "sssp_profile": (c_int, [vp, c_int, ctypes.POINTER(sssp_kernel_profile)]),
+        "sssp_profile_rounds": (c_int, [vp, vp, vp, u32, ctypes.POINTER(u32)]),
         "sssp_destroy": (None, [vp]),
         "sssp_strerror": (ctypes.c_char_p, [c_int]),
         "sssp_num_vertices": (u32, [vp]),
@@ -198,6 +208,26 @@ def sssp_destroy(h: int):
     if h:
         load().sssp_destroy(h)
         _keepalive.pop(h, None)
+
+
+def sssp_profile(h: int, enable: bool) -> dict:
+    """Switches per-kernel CUDA-event timing on or off; returns (and resets)
+    the totals gathered so far."""
+    p = sssp_kernel_profile()
+    _check(load().sssp_profile(h, int(bool(enable)), ctypes.byref(p)), "sssp_profile")
+    return p.as_dict()
+
+
+def sssp_profile_rounds(h: int):
+    """Per-round (relax_ms, cupdate_ms) arrays of the last profiled solve."""
+    lib = load()
+    cnt = ctypes.c_uint32(0)
+    _check(lib.sssp_profile_rounds(h, None, None, 0, ctypes.byref(cnt)), "sssp_profile_rounds")
+    r = np.zeros(cnt.value, dtype=np.float32)
+    c = np.zeros(cnt.value, dtype=np.float32)
+    _check(lib.sssp_profile_rounds(h, r.ctypes.data, c.ctypes.data, cnt.value,
+                                   ctypes.byref(cnt)), "sssp_profile_rounds")
+    return r, c
 
 
 def sssp_num_vertices(h: int) -> int:

@@ -91,23 +91,56 @@ int build_loop(Context& c) {
 // Runs rounds until the device loop stops (all queries done, stop round hit,
 // or an error).
 int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
-    if (loop_mode == SSSP_LOOP_GRAPH) {
+    if (loop_mode == SSSP_LOOP_GRAPH && !c.prof) {
         if (!c.exec) RC(build_loop(c));
         CK(cudaGraphLaunch(c.exec, st));
         return SSSP_OK;
     }
+    // Host-launched rounds, 16 per group, then a status check.  With
+    // profiling, events bracket every launch: ev[3i] | relax | ev[3i+1] |
+    // cupdate | ev[3i+2].
+    constexpr int kGroup = 16;
     const void* fr = relax_fn(c.multi);
     const void* fc = cupdate_fn(c.multi);
     RoundParams P = c.P;
     P.cond = 0;
     void* args[] = {&P};
+    if (c.prof && c.ev.empty()) {
+        c.ev.resize(3 * kGroup);
+        for (auto& e : c.ev) CK(cudaEventCreate(&e));
+    }
+    CK(cudaMemcpyAsync(c.h_ctl, c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    u32 round_before = c.h_ctl->round;
+    if (c.prof) {
+        c.prof_round_relax.clear();
+        c.prof_round_cup.clear();
+    }
     for (;;) {
-        for (int i = 0; i < 16; ++i) {
+        for (int i = 0; i < kGroup; ++i) {
+            if (c.prof) CK(cudaEventRecord(c.ev[3 * i], st));
             CK(cudaLaunchKernel(fr, dim3(c.grid), dim3(kThreads), args, 0, st));
+            if (c.prof) CK(cudaEventRecord(c.ev[3 * i + 1], st));
             CK(cudaLaunchKernel(fc, dim3(c.grid), dim3(kThreads), args, 0, st));
+            if (c.prof) CK(cudaEventRecord(c.ev[3 * i + 2], st));
         }
         CK(cudaMemcpyAsync(c.h_ctl, c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        if (c.prof) {
+            const u32 ran = std::min<u32>(kGroup, c.h_ctl->round - round_before);
+            for (u32 i = 0; i < ran; ++i) {
+                float a = 0, b = 0;
+                CK(cudaEventElapsedTime(&a, c.ev[3 * i], c.ev[3 * i + 1]));
+                CK(cudaEventElapsedTime(&b, c.ev[3 * i + 1], c.ev[3 * i + 2]));
+                c.prof_relax_ms += a;
+                c.prof_cup_ms += b;
+                c.prof_round_relax.push_back(a);
+                c.prof_round_cup.push_back(b);
+            }
+            c.prof_relax_n += ran;
+            c.prof_cup_n += ran;
+        }
+        round_before = c.h_ctl->round;
         if (c.h_ctl->status != kRunning || c.h_ctl->round > c.h_ctl->stop_round) break;
     }
     return SSSP_OK;
@@ -696,6 +729,36 @@ int sssp_solve_batch_device(const sssp_handle* g, const uint32_t* sources, uint3
                             uint64_t* const* dist_dev, uint32_t* rounds_out, void* cuda_stream) {
     return batch_impl(g, sources, k, reinterpret_cast<u64* const*>(dist_dev), true, rounds_out,
                       (cudaStream_t)cuda_stream, true);
+}
+
+int sssp_profile(sssp_handle h, int enable, sssp_kernel_profile* out) {
+    if (!h || (enable != 0 && enable != 1)) return SSSP_E_INVAL;
+    std::lock_guard<std::mutex> lk(h->mu);
+    Context& c = h->single;
+    if (out) {
+        out->relax_launches = c.prof_relax_n;
+        out->cupdate_launches = c.prof_cup_n;
+        out->relax_ms = c.prof_relax_ms;
+        out->cupdate_ms = c.prof_cup_ms;
+    }
+    c.prof_relax_n = c.prof_cup_n = 0;
+    c.prof_relax_ms = c.prof_cup_ms = 0;
+    c.prof = enable != 0;
+    return SSSP_OK;
+}
+
+int sssp_profile_rounds(sssp_handle h, float* relax_ms, float* cupdate_ms, uint32_t cap,
+                        uint32_t* count) {
+    if (!h || !count || (cap && (!relax_ms || !cupdate_ms))) return SSSP_E_INVAL;
+    std::lock_guard<std::mutex> lk(h->mu);
+    const Context& c = h->single;
+    const u32 n = (u32)c.prof_round_cup.size();
+    for (u32 i = 0; i < n && i < cap; ++i) {
+        relax_ms[i] = c.prof_round_relax[i];
+        cupdate_ms[i] = c.prof_round_cup[i];
+    }
+    *count = n;
+    return SSSP_OK;
 }
 
 const char* sssp_strerror(int code) {

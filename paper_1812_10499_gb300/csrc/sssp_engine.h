@@ -137,6 +137,12 @@ struct Context {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int grid = 0;
+    // Per-kernel event timing (sssp_profile).
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    u64 prof_relax_n = 0, prof_cup_n = 0;
+    double prof_relax_ms = 0, prof_cup_ms = 0;
+    std::vector<float> prof_round_relax, prof_round_cup;   // last profiled solve
 
     void destroy() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -153,6 +159,8 @@ struct Context {
         h_desc = nullptr;
         h_pages = nullptr;
         h_stage = nullptr;
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        ev.clear();
         pool.release();
     }
 };

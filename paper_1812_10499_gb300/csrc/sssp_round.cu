@@ -1,5 +1,5 @@
 // sssp_round.cu -- sm_103a kernels of the SP_3/SP_4 round (Garg, arXiv
-// 1812.10499, Sec. V-VI) and the per-graph setup kernels.
+// 1812.10499, Sec. V-VI).
 //
 // One round r is two kernels:
 //   k_relax   : SP_4 step 3, label-setting (as SP_3 explores only fixed
@@ -19,17 +19,43 @@
 //               minima.  The last CTA to finish closes the round.
 // Both kernels pull work dynamically: 32 list entries per warp with a
 // warp-local load balance over their edges, or one chunk of a hub vertex.
+// Every lane keeps kUnroll edges in flight (independent adjacency loads,
+// then independent 32-byte state gathers); the adjacency is streamed with
+// an evict-first policy so the state records stay in L2; list appends go
+// through warp-private buffers flushed 32 entries per atomic.
 #include "sssp_dev.cuh"
 
 namespace sssp {
 
 constexpr u32 kFull = 0xFFFFFFFFu;
+constexpr u32 kUnroll = 4;     // edges per lane in flight
+constexpr u32 kWarps = 8;      // warps per CTA (256 threads)
+constexpr u32 kQCap = 64;      // entries of a warp append buffer
 
 // ------------------------------------------------------------------ helpers
 
 __device__ __forceinline__ ulonglong4_32a ld_rec(const VRec* p) {
     return *reinterpret_cast<const ulonglong4_32a*>(p);
 }
+// The two words a round reads from a neighbour: packed D and the lower-bound
+// word of round parity `cur` (both in the record's 32-byte sector).
+struct DC {
+    u64 d, c;
+};
+__device__ __forceinline__ DC ld_dc(const VRec* p, u32 cur) {
+    DC r;
+    if (cur == 0) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(p);
+        r.d = v.x;
+        r.c = v.y;
+    } else {
+        r.d = p->dp;
+        r.c = p->cf[1];
+    }
+    return r;
+}
+// Adjacency entries are read once per visit: stream them (evict first).
+__device__ __forceinline__ uint2 ld_stream(const uint2* p) { return __ldcs(p); }
 __device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
 __device__ __forceinline__ u64 umax64(u64 a, u64 b) { return a > b ? a : b; }
 __device__ __forceinline__ u32 ld_volatile(const u32* p) { return *(volatile const u32*)p; }
@@ -66,17 +92,6 @@ __device__ __forceinline__ u64 warp_sum64(u64 v) {
     return v;
 }
 
-// Warp-aggregated append: one atomicAdd per warp.  Call with all lanes.
-__device__ __forceinline__ u32 warp_append(u32* counter, bool pred, u32 lane) {
-    u32 mask = __ballot_sync(kFull, pred);
-    if (mask == 0) return 0;
-    u32 leader = __ffs(mask) - 1;
-    u32 base = 0;
-    if (lane == leader) base = atomicAdd(counter, __popc(mask));
-    base = __shfl_sync(kFull, base, leader);
-    return base + __popc(mask & ((1u << lane) - 1u));
-}
-
 __device__ __forceinline__ void put_small(const RoundParams& P, u32* list, u32 idx, u32 g) {
     if (idx < P.L.capS) list[idx] = g;
     else atomicOr(&P.ctl->error, 1u);
@@ -90,10 +105,50 @@ __device__ __forceinline__ void put_hub(const RoundParams& P, u64* pk, uint2* li
     else atomicOr(&P.ctl->error, 2u);
 }
 
+// Warp-private append buffer of one small list (in shared memory); the
+// count is warp-uniform.  32 entries leave per global atomicAdd.
+struct WarpQueue {
+    u32* buf;
+    u32 cnt;
+};
+
+__device__ __forceinline__ void wq_push(const RoundParams& P, WarpQueue& q, u32* counter,
+                                        u32* list, bool pred, u32 g, u32 lane) {
+    const u32 mask = __ballot_sync(kFull, pred);
+    if (mask == 0) return;
+    if (pred) q.buf[q.cnt + __popc(mask & ((1u << lane) - 1u))] = g;
+    q.cnt += __popc(mask);
+    __syncwarp();
+    if (q.cnt >= 32) {
+        u32 base = 0;
+        if (lane == 0) base = atomicAdd(counter, 32u);
+        base = __shfl_sync(kFull, base, 0);
+        put_small(P, list, base + lane, q.buf[lane]);
+        const u32 rest = q.cnt - 32;
+        const u32 v = (lane < rest) ? q.buf[32 + lane] : 0u;
+        __syncwarp();
+        if (lane < rest) q.buf[lane] = v;
+        __syncwarp();
+        q.cnt = rest;
+    }
+}
+
+__device__ __forceinline__ void wq_flush(const RoundParams& P, WarpQueue& q, u32* counter,
+                                         u32* list, u32 lane) {
+    if (q.cnt == 0) return;
+    u32 base = 0;
+    if (lane == 0) base = atomicAdd(counter, q.cnt);
+    base = __shfl_sync(kFull, base, 0);
+    if (lane < q.cnt) put_small(P, list, base + lane, q.buf[lane]);
+    __syncwarp();
+    q.cnt = 0;
+}
+
 // Accumulators a thread carries through one kernel.
 struct Acc {
     u64 fmin_d, fmin_t;     // folds of minD / threshold (single-query mode)
     u64 edges, visits;
+    u32 nfix;               // vertices fixed (single-query mode)
 };
 
 __device__ __forceinline__ void atomic_min_checked(u64* p, u64 v) {
@@ -117,12 +172,14 @@ __device__ __forceinline__ void fold(const RoundParams& P, u32 inst, u32 slot, u
 template <bool MULTI>
 __device__ __forceinline__ void flush(const RoundParams& P, u32 slot, Acc& a, u32 lane,
                                       int stat_edges, int stat_visits) {
-    u64 e = warp_sum64(a.edges), v = warp_sum64(a.visits);
+    const u64 e = warp_sum64(a.edges), v = warp_sum64(a.visits);
+    const u64 nf = warp_sum64(a.nfix);
     if (!MULTI) {
-        u64 d = warp_min64(a.fmin_d), t = warp_min64(a.fmin_t);
+        const u64 d = warp_min64(a.fmin_d), t = warp_min64(a.fmin_t);
         if (lane == 0) {
             if (d != kInf64) atomic_min_checked(&P.ivar[0].minD[slot], d);
             if (t != kInf64) atomic_min_checked(&P.ivar[0].thr[slot], t);
+            if (nf) atomicAdd(&P.ivar[0].nfix[slot], (u32)nf);
         }
     }
     if (lane == 0) {
@@ -144,43 +201,51 @@ __device__ __forceinline__ const InstDesc& desc_of(const RoundParams& P, u32 g, 
 
 // ---------------------------------------------------------------- k_relax
 
-// Relaxes one out-edge (x -> y, w) of a fixed x (SP_4 step 3) and appends a
-// newly discovered y to the active lists.  Call with all lanes of the warp.
+// Relaxes kUnroll out-edges per lane (SP_4 step 3) and queues newly
+// discovered targets.  Call with all lanes of the warp.
 template <bool MULTI>
-__device__ __forceinline__ void relax_edge(const RoundParams& P, u32 cur, bool ev,
-                                           const uint2* ep, u64 dx, u32 xloc, u64 gbase,
-                                           const u64* in_off, u32 inst, Acc& a, u32 lane) {
-    bool fresh = false;
-    u32 gy = 0;
-    u64 indeg = 0;
-    if (ev) {
-        uint2 e = *ep;                        // {y, w}
-        u64 d = dx + e.y;
-        u64 cand = (d << P.vbits) | xloc;
-        gy = (u32)(gbase + e.x);
-        VRec* ry = P.rec + gy;
-        ulonglong4_32a v = ld_rec(ry);
-        u64 cf = cur ? v.z : v.y;
-        if (!(cf & kFixed) && cand < v.x) {
-            u64 old = atomicMin(&ry->dp, cand);
-            if (cand < old) {
-                u32 ow = (u32)v.w;
-                fold<MULTI>(P, inst, cur, d, ow == kNoOutW ? P.dinf : d + ow, a);
-                if (old == kInf64) {
-                    fresh = true;
-                    indeg = in_off[e.x + 1] - in_off[e.x];
-                }
-            }
+__device__ __forceinline__ void relax_edges(const RoundParams& P, u32 cur, const bool* ev,
+                                            const uint2* e, const u64* dx, const u32* xloc,
+                                            const u64* gbase, const u64* const* in_off,
+                                            const u32* inst, Acc& a, WarpQueue& q, u32 lane) {
+    DC v[kUnroll];
+    u32 gy[kUnroll];
+#pragma unroll
+    for (u32 u = 0; u < kUnroll; ++u) {
+        gy[u] = (u32)(gbase[u] + e[u].x);
+        if (ev[u]) v[u] = ld_dc(P.rec + gy[u], cur);
+    }
+    bool fresh[kUnroll];
+    u64 indeg[kUnroll];
+#pragma unroll
+    for (u32 u = 0; u < kUnroll; ++u) {
+        fresh[u] = false;
+        indeg[u] = 0;
+        if (!ev[u]) continue;
+        const u64 dd = dx[u] + e[u].y;
+        const u64 cand = (dd << P.vbits) | xloc[u];
+        if ((v[u].c & kFixed) || cand >= v[u].d) continue;
+        const u64 old = atomicMin(&P.rec[gy[u]].dp, cand);
+        if (cand < old) {
+            const u32 ow = P.rec[gy[u]].outw;
+            fold<MULTI>(P, inst[u], cur, dd, ow == kNoOutW ? P.dinf : dd + ow, a);
+            fresh[u] = (old == kInf64);
         }
     }
-    bool sm = fresh && indeg <= P.hub;
-    u32 idx = warp_append(&P.ctl->nAS[cur], sm, lane);
-    if (sm) put_small(P, P.L.AS[cur], idx, gy);
-    if (fresh && !sm) put_hub(P, &P.ctl->AHpk[cur], P.L.AH[cur], gy, indeg);
+#pragma unroll
+    for (u32 u = 0; u < kUnroll; ++u)
+        if (fresh[u]) indeg[u] = in_off[u][e[u].x + 1] - in_off[u][e[u].x];
+#pragma unroll
+    for (u32 u = 0; u < kUnroll; ++u) {
+        const bool sm = fresh[u] && indeg[u] <= P.hub;
+        wq_push(P, q, &P.ctl->nAS[cur], P.L.AS[cur], sm, gy[u], lane);
+        if (fresh[u] && !sm) put_hub(P, &P.ctl->AHpk[cur], P.L.AH[cur], gy[u], indeg[u]);
+    }
 }
 
 template <bool MULTI>
-__device__ void relax_small(const RoundParams& P, u32 t, u32 nfs, u32 cur, u32 lane, Acc& a) {
+__device__ void relax_small(const RoundParams& P, u32 t, u32 nfs, u32 cur, u32 lane, Acc& a,
+                            WarpQueue& q) {
     const u32 idx = t * 32 + lane;
     const bool valid = idx < nfs;
     u32 g = 0, xloc = 0, inst = 0, deg = 0;
@@ -197,7 +262,7 @@ __device__ void relax_small(const RoundParams& P, u32 t, u32 nfs, u32 cur, u32 l
         b = d.out_off[xloc];
         deg = (u32)(d.out_off[xloc + 1] - b);
         VRec* rx = P.rec + g;
-        u64 cfx = rx->cf[cur];
+        const u64 cfx = rx->cf[cur];
         rx->cf[cur ^ 1] = cfx;       // keep both copies "fixed" from now on
         dx = cfx & kCMask;           // C = D for a fixed vertex
         a.visits++;
@@ -206,29 +271,44 @@ __device__ void relax_small(const RoundParams& P, u32 t, u32 nfs, u32 cur, u32 l
     const u32 total = __shfl_sync(kFull, incl, 31);
     const u32 excl = incl - deg;
     const u64 eaddr = (u64)(adj + b);
-    for (u32 j0 = 0; j0 < total; j0 += 32) {
-        const u32 j = j0 + lane;
-        const bool ev = j < total;
-        const u32 own = find_owner(excl, j);
-        const u32 k = j - __shfl_sync(kFull, excl, own);
-        const uint2* ep = reinterpret_cast<const uint2*>(__shfl_sync(kFull, eaddr, own)) + k;
-        const u64 odx = __shfl_sync(kFull, dx, own);
-        const u32 ox = __shfl_sync(kFull, xloc, own);
-        u64 ob = 0;
-        const u64* oin = in_off;
-        u32 oinst = 0;
-        if (MULTI) {
-            ob = __shfl_sync(kFull, gbase, own);
-            oin = reinterpret_cast<const u64*>(__shfl_sync(kFull, (u64)in_off, own));
-            oinst = __shfl_sync(kFull, inst, own);
+    for (u32 j0 = 0; j0 < total; j0 += 32 * kUnroll) {
+        bool ev[kUnroll];
+        uint2 e[kUnroll];
+        u64 odx[kUnroll], ob[kUnroll];
+        u32 ox[kUnroll], oinst[kUnroll];
+        const u64* oin[kUnroll];
+#pragma unroll
+        for (u32 u = 0; u < kUnroll; ++u) {
+            ev[u] = false;
+            e[u] = make_uint2(0, 0);
+            odx[u] = 0;
+            ox[u] = 0;
+            ob[u] = 0;
+            oinst[u] = 0;
+            oin[u] = in_off;
+            if (j0 + 32 * u >= total) continue;    // warp-uniform
+            const u32 j = j0 + 32 * u + lane;
+            ev[u] = j < total;
+            const u32 own = find_owner(excl, j);
+            const u32 k = j - __shfl_sync(kFull, excl, own);
+            const uint2* ep = reinterpret_cast<const uint2*>(__shfl_sync(kFull, eaddr, own)) + k;
+            odx[u] = __shfl_sync(kFull, dx, own);
+            ox[u] = __shfl_sync(kFull, xloc, own);
+            if (MULTI) {
+                ob[u] = __shfl_sync(kFull, gbase, own);
+                oin[u] = reinterpret_cast<const u64*>(__shfl_sync(kFull, (u64)in_off, own));
+                oinst[u] = __shfl_sync(kFull, inst, own);
+            }
+            if (ev[u]) e[u] = ld_stream(ep);
+            a.edges += ev[u];
         }
-        relax_edge<MULTI>(P, cur, ev, ep, odx, ox, ob, oin, oinst, a, lane);
-        a.edges += ev;
+        relax_edges<MULTI>(P, cur, ev, e, odx, ox, ob, oin, oinst, a, q, lane);
     }
 }
 
 template <bool MULTI>
-__device__ void relax_hub(const RoundParams& P, u32 c, u32 nfh, u32 cur, u32 lane, Acc& a) {
+__device__ void relax_hub(const RoundParams& P, u32 c, u32 nfh, u32 cur, u32 lane, Acc& a,
+                          WarpQueue& q) {
     const uint2* FH = P.L.FH[cur];
     u32 lo = 0, hi = nfh;
     while (hi - lo > 1) {
@@ -240,31 +320,48 @@ __device__ void relax_hub(const RoundParams& P, u32 c, u32 nfh, u32 cur, u32 lan
     u32 inst;
     const InstDesc& d = desc_of<MULTI>(P, g, inst);
     const u32 xloc = g - (u32)d.base;
-    const u64 b = d.out_off[xloc], e = d.out_off[xloc + 1];
+    const u64 b = d.out_off[xloc], e_end = d.out_off[xloc + 1];
     const u64 cb = b + (u64)k * P.chunk;
-    const u64 ce = umin64(cb + P.chunk, e);
+    const u64 ce = umin64(cb + P.chunk, e_end);
     VRec* rx = P.rec + g;
     const u64 cfx = rx->cf[cur];
-    const u64 dx = cfx & kCMask;
     if (k == 0 && lane == 0) {
         rx->cf[cur ^ 1] = cfx;
         a.visits++;
     }
-    for (u64 e0 = cb; e0 < ce; e0 += 32) {
-        const u64 ei = e0 + lane;
-        const bool ev = ei < ce;
-        relax_edge<MULTI>(P, cur, ev, d.out_adj + ei, dx, xloc, d.base, d.in_off, inst, a, lane);
-        a.edges += ev;
+    bool ev[kUnroll];
+    uint2 e[kUnroll];
+    u64 odx[kUnroll], ob[kUnroll];
+    u32 ox[kUnroll], oinst[kUnroll];
+    const u64* oin[kUnroll];
+#pragma unroll
+    for (u32 u = 0; u < kUnroll; ++u) {
+        odx[u] = cfx & kCMask;
+        ox[u] = xloc;
+        ob[u] = d.base;
+        oinst[u] = inst;
+        oin[u] = d.in_off;
+    }
+    for (u64 e0 = cb; e0 < ce; e0 += 32 * kUnroll) {
+#pragma unroll
+        for (u32 u = 0; u < kUnroll; ++u) {
+            const u64 ei = e0 + 32 * u + lane;
+            ev[u] = ei < ce;
+            e[u] = ev[u] ? ld_stream(d.out_adj + ei) : make_uint2(0, 0);
+            a.edges += ev[u];
+        }
+        relax_edges<MULTI>(P, cur, ev, e, odx, ox, ob, oin, oinst, a, q, lane);
     }
 }
 
 template <bool MULTI>
-__global__ void __launch_bounds__(256) k_relax(RoundParams P) {
+__global__ void __launch_bounds__(256, 2) k_relax(RoundParams P) {
+    __shared__ u32 s_q[kWarps][kQCap];
     Ctl* ctl = P.ctl;
     if (ld_volatile(&ctl->status) != kRunning) return;
     const u32 r = ctl->round;
     const u32 cur = r & 1u, nxt = cur ^ 1u;
-    const u32 lane = threadIdx.x & 31u;
+    const u32 lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
 
     if (blockIdx.x == 0) {
         // Open the slots of round r + 1 (last read in round r - 1).
@@ -294,15 +391,17 @@ __global__ void __launch_bounds__(256) k_relax(RoundParams P) {
     const u32 tiles = (nfs + 31) >> 5;
     const u32 total = tiles + fh_chunks;
 
-    Acc a = {kInf64, kInf64, 0, 0};
+    Acc a = {kInf64, kInf64, 0, 0, 0};
+    WarpQueue q = {s_q[wib], 0};
     for (;;) {
         u32 item = 0;
         if (lane == 0) item = atomicAdd(&ctl->work[0], 1u);
         item = __shfl_sync(kFull, item, 0);
         if (item >= total) break;
-        if (item < tiles) relax_small<MULTI>(P, item, nfs, cur, lane, a);
-        else relax_hub<MULTI>(P, item - tiles, nfh, cur, lane, a);
+        if (item < tiles) relax_small<MULTI>(P, item, nfs, cur, lane, a, q);
+        else relax_hub<MULTI>(P, item - tiles, nfh, cur, lane, a, q);
     }
+    wq_flush(P, q, &ctl->nAS[cur], P.L.AS[cur], lane);
     flush<MULTI>(P, cur, a, lane, 0, 3);
 }
 
@@ -310,10 +409,9 @@ __global__ void __launch_bounds__(256) k_relax(RoundParams P) {
 
 // lb(x): the lower bound an in-neighbour contributes (Lemmas 7 and 8); with
 // rule 1 the printed SP_4 step 4 clamp (minD for unfixed vertices).
-__device__ __forceinline__ u64 lb_of(const RoundParams& P, u32 cur, u32 gx, u64 thr, u64 minD) {
-    const ulonglong4_32a v = ld_rec(P.rec + gx);
-    const u64 dx = v.x >> P.vbits;            // infinity maps to dinf
-    const u64 cfx = cur ? v.z : v.y;
+__device__ __forceinline__ u64 lb_of(const RoundParams& P, const DC& v, u64 thr, u64 minD) {
+    const u64 dx = v.d >> P.vbits;            // infinity maps to dinf
+    const u64 cfx = v.c;
     const u64 cx = cfx & kCMask;
     if (P.rule == 0) return umax64(cx, umin64(dx, thr));
     return (cfx & kFixed) ? cx : umax64(cx, minD);
@@ -330,7 +428,8 @@ __device__ __forceinline__ u64 decide(const RoundParams& P, u64 dy, u64 cy, u64 
 
 template <bool MULTI>
 __device__ void cup_small(const RoundParams& P, u32 t, u32 nas, u32 r, u32 cur, u32 lane,
-                          u64* smin, u64 thr0, u64 minD0, Acc& a, Acc& an) {
+                          u64* smin, u64 thr0, u64 minD0, Acc& a, Acc& an, WarpQueue& qf,
+                          WarpQueue& qa) {
     const u32 nxt = cur ^ 1u;
     const u32 idx = t * 32 + lane;
     const bool valid = idx < nas;
@@ -362,42 +461,60 @@ __device__ void cup_small(const RoundParams& P, u32 t, u32 nas, u32 r, u32 cur, 
     const u32 total = __shfl_sync(kFull, incl, 31);
     const u32 excl = incl - deg;
     const u64 eaddr = (u64)(in_adj + ib);
-    for (u32 j0 = 0; j0 < total; j0 += 32) {
-        const u32 j = j0 + lane;
-        const bool ev = j < total;
-        const u32 own = find_owner(excl, j);
-        const u32 k = j - __shfl_sync(kFull, excl, own);
-        const uint2* ep = reinterpret_cast<const uint2*>(__shfl_sync(kFull, eaddr, own)) + k;
-        u64 othr = thr, omin = minD, ob = 0;
-        if (MULTI) {
-            othr = __shfl_sync(kFull, thr, own);
-            omin = __shfl_sync(kFull, minD, own);
-            ob = __shfl_sync(kFull, gbase, own);
-        }
-        u64 val = kInf64;
-        if (ev) {
-            const uint2 e = *ep;                     // {x, w}
-            const u64 lb = lb_of(P, cur, (u32)(ob + e.x), othr, omin);
-            val = umin64(lb + e.y, P.dinf);
-        }
-        // Segmented min over lanes sharing an owner (contiguous by construction).
-        const u32 key = ev ? own : 32u + lane;
+    for (u32 j0 = 0; j0 < total; j0 += 32 * kUnroll) {
+        bool ev[kUnroll];
+        uint2 e[kUnroll];
+        u32 own[kUnroll];
+        u64 othr[kUnroll], omin[kUnroll], ob[kUnroll];
 #pragma unroll
-        for (u32 dd = 1; dd < 32; dd <<= 1) {
-            const u64 ov = __shfl_up_sync(kFull, val, dd);
-            const u32 ok = __shfl_up_sync(kFull, key, dd);
-            if (lane >= dd && ok == key) val = umin64(val, ov);
+        for (u32 u = 0; u < kUnroll; ++u) {
+            ev[u] = false;
+            own[u] = 0;
+            e[u] = make_uint2(0, 0);
+            othr[u] = thr;
+            omin[u] = minD;
+            ob[u] = 0;
+            if (j0 + 32 * u >= total) continue;    // warp-uniform
+            const u32 j = j0 + 32 * u + lane;
+            ev[u] = j < total;
+            own[u] = find_owner(excl, j);
+            const u32 k = j - __shfl_sync(kFull, excl, own[u]);
+            const uint2* ep =
+                reinterpret_cast<const uint2*>(__shfl_sync(kFull, eaddr, own[u])) + k;
+            if (MULTI) {
+                othr[u] = __shfl_sync(kFull, thr, own[u]);
+                omin[u] = __shfl_sync(kFull, minD, own[u]);
+                ob[u] = __shfl_sync(kFull, gbase, own[u]);
+            }
+            if (ev[u]) e[u] = ld_stream(ep);
         }
-        const u32 nk = __shfl_down_sync(kFull, key, 1);
-        if (ev && (lane == 31 || nk != key)) smin[own] = umin64(smin[own], val);
-        __syncwarp();
+        DC v[kUnroll];
+#pragma unroll
+        for (u32 u = 0; u < kUnroll; ++u)
+            if (ev[u]) v[u] = ld_dc(P.rec + (u32)(ob[u] + e[u].x), cur);
+#pragma unroll
+        for (u32 u = 0; u < kUnroll; ++u) {
+            if (j0 + 32 * u >= total) continue;    // warp-uniform
+            u64 val = kInf64;
+            if (ev[u]) val = umin64(lb_of(P, v[u], othr[u], omin[u]) + e[u].y, P.dinf);
+            // Segmented min over lanes sharing an owner (contiguous by construction).
+            const u32 key = ev[u] ? own[u] : 32u + lane;
+#pragma unroll
+            for (u32 dd = 1; dd < 32; dd <<= 1) {
+                const u64 ov = __shfl_up_sync(kFull, val, dd);
+                const u32 ok = __shfl_up_sync(kFull, key, dd);
+                if (lane >= dd && ok == key) val = umin64(val, ov);
+            }
+            const u32 nk = __shfl_down_sync(kFull, key, 1);
+            if (ev[u] && (lane == 31 || nk != key)) smin[own[u]] = umin64(smin[own[u]], val);
+            __syncwarp();
+        }
     }
     a.edges += (lane == 0) ? total : 0;
 
     bool fix = false;
-    u64 cn = 0;
     if (valid) {
-        cn = decide(P, dy, cy, smin[lane], thr, minD, fix);
+        const u64 cn = decide(P, dy, cy, smin[lane], thr, minD, fix);
         VRec* ry = P.rec + g;
         ry->cf[nxt] = cn | (fix ? kFixed : 0ull);
         if (fix) ry->fround = (int)r;
@@ -408,16 +525,13 @@ __device__ void cup_small(const RoundParams& P, u32 t, u32 nas, u32 r, u32 cur, 
     u64 odeg = 0;
     if (fx) odeg = out_off[yloc + 1] - out_off[yloc];
     const bool fs = fx && odeg <= P.hub;
-    u32 pos = warp_append(&P.ctl->nFS[nxt], fs, lane);
-    if (fs) put_small(P, P.L.FS[nxt], pos, g);
+    wq_push(P, qf, &P.ctl->nFS[nxt], P.L.FS[nxt], fs, g, lane);
     if (fx && !fs) put_hub(P, &P.ctl->FHpk[nxt], P.L.FH[nxt], g, odeg);
-    pos = warp_append(&P.ctl->nAS[nxt], sv, lane);
-    if (sv) put_small(P, P.L.AS[nxt], pos, g);
+    wq_push(P, qa, &P.ctl->nAS[nxt], P.L.AS[nxt], sv, g, lane);
     if (MULTI) {
         if (fx) atomicAdd(&P.ivar[inst].nfix[nxt], 1u);
     } else {
-        const u32 c = __popc(__ballot_sync(kFull, fx));
-        if (lane == 0 && c) atomicAdd(&P.ivar[0].nfix[nxt], c);
+        an.nfix += fx;
     }
     if (sv) fold<MULTI>(P, inst, nxt, dy, outw == kNoOutW ? P.dinf : dy + outw, an);
 }
@@ -447,10 +561,21 @@ __device__ void cup_hub(const RoundParams& P, u32 c, u32 nah, u32 ah_chunks, u32
     const u64 cb = ib + (u64)k * P.chunk;
     const u64 ce = umin64(cb + P.chunk, ie);
     u64 val = kInf64;
-    for (u64 e0 = cb + lane; e0 < ce; e0 += 32) {
-        const uint2 e = d.in_adj[e0];
-        const u64 lb = lb_of(P, cur, (u32)(d.base + e.x), thr, minD);
-        val = umin64(val, umin64(lb + e.y, P.dinf));
+    for (u64 e0 = cb + lane; e0 < ce; e0 += 32 * kUnroll) {
+        uint2 e[kUnroll];
+        bool ev[kUnroll];
+#pragma unroll
+        for (u32 u = 0; u < kUnroll; ++u) {
+            ev[u] = e0 + 32 * u < ce;
+            e[u] = ev[u] ? ld_stream(d.in_adj + e0 + 32 * u) : make_uint2(0, 0);
+        }
+        DC v[kUnroll];
+#pragma unroll
+        for (u32 u = 0; u < kUnroll; ++u)
+            if (ev[u]) v[u] = ld_dc(P.rec + (u32)(d.base + e[u].x), cur);
+#pragma unroll
+        for (u32 u = 0; u < kUnroll; ++u)
+            if (ev[u]) val = umin64(val, umin64(lb_of(P, v[u], thr, minD) + e[u].y, P.dinf));
     }
     val = warp_min64(val);
     if (lane != 0) return;
@@ -476,7 +601,8 @@ __device__ void cup_hub(const RoundParams& P, u32 c, u32 nah, u32 ah_chunks, u32
         const u64 odeg = d.out_off[yloc + 1] - d.out_off[yloc];
         if (odeg <= P.hub) put_small(P, P.L.FS[nxt], atomicAdd(&P.ctl->nFS[nxt], 1u), g);
         else put_hub(P, &P.ctl->FHpk[nxt], P.L.FH[nxt], g, odeg);
-        atomicAdd(&P.ivar[inst].nfix[nxt], 1u);
+        if (MULTI) atomicAdd(&P.ivar[inst].nfix[nxt], 1u);
+        else an.nfix++;
     } else {
         put_hub(P, &P.ctl->AHpk[nxt], P.L.AH[nxt], g, ie - ib);
         fold<MULTI>(P, inst, nxt, dy, outw == kNoOutW ? P.dinf : dy + outw, an);
@@ -523,8 +649,10 @@ __device__ void round_epilogue(const RoundParams& P, u32 r) {
 }
 
 template <bool MULTI>
-__global__ void __launch_bounds__(256) k_cupdate(RoundParams P) {
-    __shared__ u64 s_min[8][32];
+__global__ void __launch_bounds__(256, 2) k_cupdate(RoundParams P) {
+    __shared__ u64 s_min[kWarps][32];
+    __shared__ u32 s_qf[kWarps][kQCap];
+    __shared__ u32 s_qa[kWarps][kQCap];
     __shared__ u32 s_last;
     Ctl* ctl = P.ctl;
     if (ld_volatile(&ctl->status) != kRunning) {
@@ -548,19 +676,25 @@ __global__ void __launch_bounds__(256) k_cupdate(RoundParams P) {
         minD = P.ivar[0].minD[cur];
     }
 
-    Acc a = {kInf64, kInf64, 0, 0};
-    Acc an = {kInf64, kInf64, 0, 0};
+    Acc a = {kInf64, kInf64, 0, 0, 0};
+    Acc an = {kInf64, kInf64, 0, 0, 0};
+    WarpQueue qf = {s_qf[wib], 0}, qa = {s_qa[wib], 0};
     for (;;) {
         u32 item = 0;
         if (lane == 0) item = atomicAdd(&ctl->work[1], 1u);
         item = __shfl_sync(kFull, item, 0);
         if (item >= total) break;
-        if (item < tiles) cup_small<MULTI>(P, item, nas, r, cur, lane, s_min[wib], thr, minD, a, an);
-        else cup_hub<MULTI>(P, item - tiles, nah, ah_chunks, r, cur, lane, thr, minD, a, an);
+        if (item < tiles)
+            cup_small<MULTI>(P, item, nas, r, cur, lane, s_min[wib], thr, minD, a, an, qf, qa);
+        else
+            cup_hub<MULTI>(P, item - tiles, nah, ah_chunks, r, cur, lane, thr, minD, a, an);
         __syncwarp();
     }
+    wq_flush(P, qf, &ctl->nFS[nxt], P.L.FS[nxt], lane);
+    wq_flush(P, qa, &ctl->nAS[nxt], P.L.AS[nxt], lane);
     a.fmin_d = an.fmin_d;
     a.fmin_t = an.fmin_t;
+    a.nfix = an.nfix;
     flush<MULTI>(P, nxt, a, lane, 1, 2);
 
     __syncthreads();
@@ -573,56 +707,6 @@ __global__ void __launch_bounds__(256) k_cupdate(RoundParams P) {
         __threadfence();
         round_epilogue(P, r);
     }
-}
-
-// ------------------------------------------------------- start / finalize
-
-// Every record of a single query: D = inf, C = 0 (Fig. SP_4 declarations).
-__global__ void k_init_records(VRec* rec, const u32* outw, u32 n) {
-    for (u64 v = blockIdx.x * (u64)blockDim.x + threadIdx.x; v < n;
-         v += (u64)gridDim.x * blockDim.x) {
-        VRec r;
-        r.dp = kInf64;
-        r.cf[0] = 0;
-        r.cf[1] = 0;
-        r.outw = outw[v];
-        r.fround = -1;
-        rec[v] = r;
-    }
-}
-
-// Records of all multi-query slots (pages not owned by a slot are skipped).
-__global__ void k_init_records_multi(RoundParams P, u64 nrec, u32 first_page, u32 npages) {
-    const u64 lo = (u64)first_page << P.page_shift;
-    const u64 hi = umin64(nrec, (u64)(first_page + npages) << P.page_shift);
-    for (u64 g = lo + blockIdx.x * (u64)blockDim.x + threadIdx.x; g < hi;
-         g += (u64)gridDim.x * blockDim.x) {
-        const u32 inst = P.page_owner[g >> P.page_shift];
-        if (inst == kFull) continue;
-        const InstDesc& d = P.idesc[inst];
-        const u64 v = g - d.base;
-        if (v >= d.n) continue;
-        VRec r;
-        r.dp = kInf64;
-        r.cf[0] = 0;
-        r.cf[1] = 0;
-        r.outw = d.outw[v];
-        r.fround = -1;
-        P.rec[g] = r;
-    }
-}
-
-// Resets the control block for a fresh solve context.
-__global__ void k_reset_ctl(Ctl* ctl, u32 ninst, u32 round_limit) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    Ctl c;
-    memset(&c, 0, sizeof(c));
-    c.round = 1;
-    c.status = kDone;
-    c.stop_round = 0xFFFFFFFFu;
-    c.round_limit = round_limit;
-    c.ninst = ninst;
-    *ctl = c;
 }
 
 // Starts the queries in slots [first, first + count) at the control block's
@@ -664,166 +748,6 @@ __global__ void k_start(RoundParams P, u32 first, u32 count, u32 max_rounds) {
     }
 }
 
-// Output of one query (Sec. I: cost[x]; parents as in Sec. I's remark on
-// backward parent pointers).
-// The lower bounds after the query's last round r sit in cf[(r + 1) & 1].
-__global__ void k_finalize(const VRec* rec, u64 base, u32 n, u32 vbits, const InstVar* iv,
-                           u64* dist, u32* parent, int* fround, u64* lower) {
-    const u64 vmask = (vbits >= 64) ? ~0ull : ((1ull << vbits) - 1);
-    const u32 cslot = (iv->start_round + iv->rounds) & 1u;
-    for (u64 v = blockIdx.x * (u64)blockDim.x + threadIdx.x; v < n;
-         v += (u64)gridDim.x * blockDim.x) {
-        const VRec r = rec[base + v];
-        const bool reach = r.dp != kInf64;
-        if (dist) dist[v] = reach ? (r.dp >> vbits) : kInf64;
-        if (parent) parent[v] = reach ? (u32)(r.dp & vmask) : kFull;
-        if (fround) fround[v] = r.fround;
-        if (lower) lower[v] = r.cf[cslot] & kCMask;
-    }
-}
-
-// Distances of every query of a multi-query context into one staging array
-// laid out like the records (entry g = record g).
-__global__ void k_finalize_multi(RoundParams P, u64 nrec, u64* dist) {
-    for (u64 g = blockIdx.x * (u64)blockDim.x + threadIdx.x; g < nrec;
-         g += (u64)gridDim.x * blockDim.x) {
-        const u32 inst = P.page_owner[g >> P.page_shift];
-        if (inst == kFull) continue;
-        const u64 dp = P.rec[g].dp;
-        dist[g] = (dp == kInf64) ? kInf64 : (dp >> P.vbits);
-    }
-}
-
-// ----------------------------------------------------------- graph setup
-
-__global__ void k_interleave(const u32* col, const u32* w, u64 m, uint2* adj) {
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < m;
-         i += (u64)gridDim.x * blockDim.x)
-        adj[i] = make_uint2(col[i], w[i]);
-}
-
-__global__ void k_count_in(const uint2* adj, u64 m, u64* cnt) {
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < m;
-         i += (u64)gridDim.x * blockDim.x)
-        atomicAdd(&cnt[adj[i].x], 1ull);
-}
-
-// One warp per source vertex scatters its out-edges into the in-lists.
-__global__ void k_scatter_in(const u64* out_off, const uint2* out_adj, u32 n, u64* cursor,
-                             uint2* in_adj) {
-    const u32 lane = threadIdx.x & 31u;
-    for (u64 u = (blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5; u < n;
-         u += ((u64)gridDim.x * blockDim.x) >> 5) {
-        for (u64 k = out_off[u] + lane; k < out_off[u + 1]; k += 32) {
-            const uint2 e = out_adj[k];
-            const u64 pos = atomicAdd(&cursor[e.x], 1ull);
-            in_adj[pos] = make_uint2((u32)u, e.y);
-        }
-    }
-}
-
-// outWeight[u] = min out-edge weight (computed once per graph, Sec. V).
-__global__ void k_outw(const u64* out_off, const uint2* out_adj, u32 n, u32* outw) {
-    const u32 lane = threadIdx.x & 31u;
-    for (u64 u = (blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5; u < n;
-         u += ((u64)gridDim.x * blockDim.x) >> 5) {
-        u32 m = kNoOutW;
-        for (u64 k = out_off[u] + lane; k < out_off[u + 1]; k += 32) m = min(m, out_adj[k].y);
-#pragma unroll
-        for (u32 d = 16; d >= 1; d >>= 1) m = min(m, __shfl_xor_sync(kFull, m, d));
-        if (lane == 0) outw[u] = m;
-    }
-}
-
-// Vertices above the hub degree, by direction (list capacities).
-__global__ void k_count_hubs(const u64* out_off, const u64* in_off, u32 n, u32 hub, u32* cnt) {
-    u32 a = 0, b = 0;
-    for (u64 v = blockIdx.x * (u64)blockDim.x + threadIdx.x; v < n;
-         v += (u64)gridDim.x * blockDim.x) {
-        a += (out_off[v + 1] - out_off[v]) > hub;
-        b += (in_off[v + 1] - in_off[v]) > hub;
-    }
-    for (u32 d = 16; d >= 1; d >>= 1) {
-        a += __shfl_xor_sync(kFull, a, d);
-        b += __shfl_xor_sync(kFull, b, d);
-    }
-    if ((threadIdx.x & 31u) == 0) {
-        if (a) atomicAdd(&cnt[0], a);
-        if (b) atomicAdd(&cnt[1], b);
-    }
-}
-
-// Exclusive scan of u64 counts, three passes (setup only).
-constexpr u32 kScanThreads = 256, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
-
-__device__ u64 block_excl_scan(u64 x, u64* total) {
-    __shared__ u64 s_warp[kScanThreads / 32];
-    const u32 lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-    u64 incl = x;
-#pragma unroll
-    for (u32 d = 1; d < 32; d <<= 1) {
-        u64 y = __shfl_up_sync(kFull, incl, d);
-        if (lane >= d) incl += y;
-    }
-    if (lane == 31) s_warp[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        u64 s = (lane < kScanThreads / 32) ? s_warp[lane] : 0;
-        u64 si = s;
-#pragma unroll
-        for (u32 d = 1; d < 32; d <<= 1) {
-            u64 y = __shfl_up_sync(kFull, si, d);
-            if (lane >= d) si += y;
-        }
-        if (lane < kScanThreads / 32) s_warp[lane] = si - s;
-        if (lane == kScanThreads / 32 - 1) *total = si;
-    }
-    __syncthreads();
-    const u64 res = s_warp[wid] + incl - x;
-    __syncthreads();
-    return res;
-}
-
-__global__ void k_scan_tiles(const u64* in, u64 cnt, u64* tile_sums) {
-    __shared__ u64 s_tot;
-    const u64 base = (u64)blockIdx.x * kScanTile + (u64)threadIdx.x * kScanItems;
-    u64 s = 0;
-    for (u32 i = 0; i < kScanItems; ++i)
-        if (base + i < cnt) s += in[base + i];
-    block_excl_scan(s, &s_tot);
-    if (threadIdx.x == 0) tile_sums[blockIdx.x] = s_tot;
-}
-
-__global__ void k_scan_sums(u64* tile_sums, u32 ntiles) {
-    __shared__ u64 s_tot;
-    u64 carry = 0;
-    for (u32 base = 0; base < ntiles; base += kScanThreads) {
-        const u32 i = base + threadIdx.x;
-        const u64 x = (i < ntiles) ? tile_sums[i] : 0;
-        const u64 ex = block_excl_scan(x, &s_tot);
-        if (i < ntiles) tile_sums[i] = carry + ex;
-        carry += s_tot;
-        __syncthreads();
-    }
-}
-
-__global__ void k_scan_apply(const u64* in, u64 cnt, const u64* tile_sums, u64* out) {
-    __shared__ u64 s_tot;
-    const u64 base = (u64)blockIdx.x * kScanTile + (u64)threadIdx.x * kScanItems;
-    u64 v[kScanItems];
-    u64 s = 0;
-    for (u32 i = 0; i < kScanItems; ++i) {
-        v[i] = (base + i < cnt) ? in[base + i] : 0;
-        s += v[i];
-    }
-    u64 run = tile_sums[blockIdx.x] + block_excl_scan(s, &s_tot);
-    for (u32 i = 0; i < kScanItems; ++i) {
-        if (base + i < cnt) out[base + i] = run;
-        run += v[i];
-    }
-}
-
-// Explicit instantiations used by the host engine.
 template __global__ void k_relax<false>(RoundParams);
 template __global__ void k_relax<true>(RoundParams);
 template __global__ void k_cupdate<false>(RoundParams);
@@ -831,11 +755,7 @@ template __global__ void k_cupdate<true>(RoundParams);
 template __global__ void k_start<false>(RoundParams, u32, u32, u32);
 template __global__ void k_start<true>(RoundParams, u32, u32, u32);
 
-}  // namespace sssp
-
 // --------------------------------------------- host access for the engine
-
-namespace sssp {
 
 const void* relax_fn(bool multi) {
     return multi ? (const void*)k_relax<true> : (const void*)k_relax<false>;
