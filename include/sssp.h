@@ -64,9 +64,14 @@ extern "C" {
 #define SSSP_RULE_THRESHOLD 0u
 #define SSSP_RULE_MIND      1u
 
-/* How the per-round kernels are sequenced. */
-#define SSSP_LOOP_GRAPH 0u  /* one CUDA graph with a device-side while loop (default) */
-#define SSSP_LOOP_HOST  1u  /* host launches rounds in groups and polls a status word  */
+/* How the rounds are sequenced.  All modes give identical results. */
+#define SSSP_LOOP_GRAPH      0u  /* two kernels per round in a CUDA graph with a device-side
+                                    while loop (default)                                  */
+#define SSSP_LOOP_HOST       1u  /* host launches the two kernels in groups of rounds and
+                                    polls a status word                                   */
+#define SSSP_LOOP_PERSISTENT 2u  /* one cooperative launch runs every round, phases
+                                    separated by grid barriers whose waits time out
+                                    (SSSP_E_DEVICE_TIMEOUT) instead of hanging            */
 
 typedef struct sssp_graph* sssp_handle;
 typedef struct sssp_server sssp_server;

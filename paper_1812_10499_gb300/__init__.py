@@ -26,6 +26,7 @@ SSSP_RULE_THRESHOLD = 0
 SSSP_RULE_MIND = 1
 SSSP_LOOP_GRAPH = 0
 SSSP_LOOP_HOST = 1
+SSSP_LOOP_PERSISTENT = 2
 SSSP_DIST_INF = 0xFFFFFFFFFFFFFFFF
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)

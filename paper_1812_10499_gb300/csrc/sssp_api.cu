@@ -70,11 +70,13 @@ int build_loop(Context& c) {
     kp.func = const_cast<void*>(relax_fn(c.multi));
     kp.gridDim = dim3(c.grid);
     kp.blockDim = dim3(kThreads);
+    kp.sharedMemBytes = (unsigned)relax_smem_bytes();
     kp.kernelParams = args;
     cudaGraphNode_t n1, n2;
     e = cudaGraphAddKernelNode(&n1, body, nullptr, 0, &kp);
     if (e == cudaSuccess) {
         kp.func = const_cast<void*>(cupdate_fn(c.multi));
+        kp.sharedMemBytes = (unsigned)cupdate_smem_bytes();
         e = cudaGraphAddKernelNode(&n2, body, &n1, 1, &kp);
     }
     cudaGraphExec_t x = nullptr;
@@ -91,6 +93,45 @@ int build_loop(Context& c) {
 // Runs rounds until the device loop stops (all queries done, stop round hit,
 // or an error).
 int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
+    if (loop_mode == SSSP_LOOP_PERSISTENT) {
+        RoundParams P = c.P;
+        P.cond = 0;
+        if (c.prof) {
+            // Device trace: globaltimer at launch and at the end of every phase.
+            if (!c.trace) {
+                c.trace_cap = 2 * 65536 + 1;
+                RC(c.pool.get(&c.trace, c.trace_cap));
+            }
+            CK(cudaMemcpyAsync(c.h_ctl, c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            P.trace = c.trace;
+            P.trace_cap = c.trace_cap;
+            P.trace_base = c.h_ctl->round;
+        }
+        void* args[] = {&P};
+        CK(cudaLaunchCooperativeKernel(solve_fn(c.multi), dim3(c.grid_solve), dim3(kThreads), args,
+                                       solve_smem_bytes(), st));
+        if (c.prof) {
+            CK(cudaMemcpyAsync(c.h_ctl, c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            const u32 rounds = std::min<u32>(c.h_ctl->round - P.trace_base, (c.trace_cap - 1) / 2);
+            std::vector<u64> t(2 * rounds + 1);
+            CK(cudaMemcpy(t.data(), c.trace, sizeof(u64) * t.size(), cudaMemcpyDeviceToHost));
+            c.prof_round_relax.clear();
+            c.prof_round_cup.clear();
+            for (u32 i = 0; i < rounds; ++i) {
+                const float a = (float)((t[2 * i + 1] - t[2 * i]) * 1e-6);
+                const float b = (float)((t[2 * i + 2] - t[2 * i + 1]) * 1e-6);
+                c.prof_round_relax.push_back(a);
+                c.prof_round_cup.push_back(b);
+                c.prof_relax_ms += a;
+                c.prof_cup_ms += b;
+            }
+            c.prof_relax_n += rounds;
+            c.prof_cup_n += rounds;
+        }
+        return SSSP_OK;
+    }
     if (loop_mode == SSSP_LOOP_GRAPH && !c.prof) {
         if (!c.exec) RC(build_loop(c));
         CK(cudaGraphLaunch(c.exec, st));
@@ -119,9 +160,9 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
     for (;;) {
         for (int i = 0; i < kGroup; ++i) {
             if (c.prof) CK(cudaEventRecord(c.ev[3 * i], st));
-            CK(cudaLaunchKernel(fr, dim3(c.grid), dim3(kThreads), args, 0, st));
+            CK(cudaLaunchKernel(fr, dim3(c.grid), dim3(kThreads), args, relax_smem_bytes(), st));
             if (c.prof) CK(cudaEventRecord(c.ev[3 * i + 1], st));
-            CK(cudaLaunchKernel(fc, dim3(c.grid), dim3(kThreads), args, 0, st));
+            CK(cudaLaunchKernel(fc, dim3(c.grid), dim3(kThreads), args, cupdate_smem_bytes(), st));
             if (c.prof) CK(cudaEventRecord(c.ev[3 * i + 2], st));
         }
         CK(cudaMemcpyAsync(c.h_ctl, c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -175,6 +216,7 @@ int init_single_context(sssp_graph* h) {
     c.nrec = h->n;
     c.nslots = 1;
     c.grid = h->grid;
+    c.grid_solve = h->grid_solve;
     RoundParams& P = c.P;
     P.g.out_off = h->out_off;
     P.g.out_adj = h->out_adj;
@@ -185,6 +227,7 @@ int init_single_context(sssp_graph* h) {
     P.g.n = h->n;
     P.g.source = 0;
     RC(c.pool.get(&P.rec, h->n));
+    RC(c.pool.get(&P.fround, h->n));
     RC(c.pool.get(&P.ctl, 1));
     RC(c.pool.get(&P.ivar, 1));
     RC(c.pool.get(&c.stage, h->n));
@@ -308,6 +351,11 @@ int create_impl(sssp_graph* h, u32 n, u64 m, const u64* row_ptr, const u32* col,
 
     CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     h->grid = occupancy_grid(h->device, h->opt);
+    {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+        h->grid_solve = std::max(1, sms) * std::max(1, solve_blocks_per_sm(kThreads));
+    }
     Pool& gp = h->gpool;
     RC(gp.get(&h->out_off, (size_t)n + 1));
     RC(gp.get(&h->in_off, (size_t)n + 1));
@@ -399,6 +447,7 @@ int read_status(Context& c, cudaStream_t st, u32 ninst) {
     CK(cudaMemcpyAsync(c.h_ctl, c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(c.h_ivar, c.P.ivar, sizeof(InstVar) * ninst, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (c.h_ctl->error & 4u) return SSSP_E_DEVICE_TIMEOUT;
     if (c.h_ctl->error) return SSSP_E_INTERNAL;
     if (c.h_ctl->status == kErrRounds) return SSSP_E_ROUND_LIMIT;
     return SSSP_OK;
@@ -411,12 +460,12 @@ int enqueue_single(sssp_graph* h, u32 source, u32 max_rounds, cudaStream_t st, u
     RoundParams P = c.P;
     P.g.source = source;
     c.P.g.source = source;
-    k_init_records<<<c.grid, kThreads, 0, st>>>(P.rec, h->outw, h->n);
+    k_init_records<<<c.grid, kThreads, 0, st>>>(P.rec, P.fround, h->outw, h->in_off, h->n);
     k_reset_ctl<<<1, 32, 0, st>>>(P.ctl, 1, h->n + 2);
     CK(launch_start(false, P, 0, 1, max_rounds, st));
     RC(run_loop(c, h->opt.loop_mode, st));
-    k_finalize<<<c.grid, kThreads, 0, st>>>(P.rec, 0, h->n, h->vbits, P.ivar, dist_dev, parent_dev,
-                                            fround_dev, lower_dev);
+    k_finalize<<<c.grid, kThreads, 0, st>>>(P.rec, P.fround, 0, h->n, h->vbits, P.ivar, dist_dev,
+                                            parent_dev, fround_dev, lower_dev);
     CK(cudaGetLastError());
     return SSSP_OK;
 }
@@ -441,8 +490,10 @@ int ensure_batch(sssp_graph* h0, u64 nrec, u32 nslots, u32 npages, u64 capH) {
     c->nslots = nslots;
     c->npages = npages;
     c->grid = h0->grid;
+    c->grid_solve = h0->grid_solve;
     RoundParams& P = c->P;
     RC(c->pool.get(&P.rec, nrec));
+    RC(c->pool.get(&P.fround, nrec));
     RC(c->pool.get(&P.ctl, 1));
     RC(c->pool.get(&P.ivar, nslots));
     InstDesc* idesc = nullptr;
@@ -581,7 +632,7 @@ int sssp_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t*
     if (o.hub_degree == 0) o.hub_degree = kDefaultHub;
     if (o.chunk_edges == 0) o.chunk_edges = kDefaultChunk;
     if (o.block_threads == 0) o.block_threads = kThreads;
-    if (o.rule > SSSP_RULE_MIND || o.loop_mode > SSSP_LOOP_HOST || o.chunk_edges % 32 != 0 ||
+    if (o.rule > SSSP_RULE_MIND || o.loop_mode > SSSP_LOOP_PERSISTENT || o.chunk_edges % 32 != 0 ||
         o.hub_degree > (1u << 20) || o.chunk_edges > (1u << 20) ||
         o.block_threads != kThreads || (o.alloc == nullptr) != (o.free == nullptr))
         return SSSP_E_INVAL;

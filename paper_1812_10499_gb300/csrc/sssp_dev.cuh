@@ -29,7 +29,7 @@ struct __align__(32) VRec {
     u64 dp;        // packed upper bound D (atomicMin target)
     u64 cf[2];     // lower bound C | kFixed
     u32 outw;      // outWeight (Fig. SP_3 / SP_4 declarations), kNoOutW if none
-    int fround;    // round in which the vertex was fixed, -1 if not fixed
+    u32 indeg;     // in-degree (decides the work list of a newly discovered vertex)
 };
 static_assert(sizeof(VRec) == 32, "VRec must be one 32-byte sector");
 
@@ -74,6 +74,8 @@ struct __align__(16) Ctl {
     u32 done_ctas;      // arrival counter for the end-of-round epilogue
     u32 ninst;          // number of query slots
     u32 loop_iters;     // loop bodies started (watchdog against a stuck loop)
+    u32 bar_count;      // grid barrier of the persistent kernel: arrivals
+    u32 bar_gen;        // grid barrier generation (bumped on release)
     u32 pad1;
     u64 stats[4];       // out-edges scanned, in-edges scanned, active visits, frontier visits
 };
@@ -97,6 +99,7 @@ struct RoundParams {
     InstVar* ivar;              // per-slot scalars
     const u32* page_owner;      // record page -> slot (multi-query)
     VRec* rec;
+    int* fround;                // per record: round in which it was fixed, -1 if never
     Ctl* ctl;
     Lists L;
     u64 dinf;                   // distance infinity = 2^(64 - vbits) - 1
@@ -105,8 +108,12 @@ struct RoundParams {
     u32 chunk;                  // edges per hub chunk
     u32 rule;                   // 0: min(D, threshold) clamp; 1: minD clamp
     u32 page_shift;
-    u32 pad;
+    u32 trace_cap;              // entries of `trace`
+    u32 trace_base;             // round number of the first traced round
+    u32 pad2;
     unsigned long long cond;    // cudaGraphConditionalHandle of the device loop, 0 = none
+    u64* trace;                 // persistent kernel: globaltimer at launch, then at the end of
+                                // every phase (2 per round); nullable
 };
 
 }  // namespace sssp

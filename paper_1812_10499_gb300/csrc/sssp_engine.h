@@ -16,14 +16,20 @@
 namespace sssp {
 const void* relax_fn(bool multi);
 const void* cupdate_fn(bool multi);
+const void* solve_fn(bool multi);
+size_t solve_smem_bytes();
+int solve_blocks_per_sm(int threads);
+size_t relax_smem_bytes();
+size_t cupdate_smem_bytes();
+cudaError_t round_kernels_init();
 cudaError_t launch_start(bool multi, const RoundParams& P, u32 first, u32 count, u32 max_rounds,
                          cudaStream_t st);
 int round_blocks_per_sm(int threads);
-__global__ void k_init_records(VRec* rec, const u32* outw, u32 n);
+__global__ void k_init_records(VRec* rec, int* fround, const u32* outw, const u64* in_off, u32 n);
 __global__ void k_init_records_multi(RoundParams P, u64 nrec, u32 first_page, u32 npages);
 __global__ void k_reset_ctl(Ctl* ctl, u32 ninst, u32 round_limit);
-__global__ void k_finalize(const VRec* rec, u64 base, u32 n, u32 vbits, const InstVar* iv,
-                           u64* dist, u32* parent, int* fround, u64* lower);
+__global__ void k_finalize(const VRec* rec, const int* frec, u64 base, u32 n, u32 vbits,
+                           const InstVar* iv, u64* dist, u32* parent, int* fround, u64* lower);
 __global__ void k_finalize_multi(RoundParams P, u64 nrec, u64* dist);
 __global__ void k_interleave(const u32* col, const u32* w, u64 m, uint2* adj);
 __global__ void k_count_in(const uint2* adj, u64 m, u64* cnt);
@@ -137,12 +143,15 @@ struct Context {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int grid = 0;
+    int grid_solve = 0;              // co-resident grid of the persistent kernel
     // Per-kernel event timing (sssp_profile).
     bool prof = false;
     std::vector<cudaEvent_t> ev;
     u64 prof_relax_n = 0, prof_cup_n = 0;
     double prof_relax_ms = 0, prof_cup_ms = 0;
     std::vector<float> prof_round_relax, prof_round_cup;   // last profiled solve
+    u64* trace = nullptr;            // device trace of the persistent kernel
+    u32 trace_cap = 0;
 
     void destroy() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -187,6 +196,7 @@ struct sssp_graph {
     u32* outw = nullptr;
     cudaStream_t stream = nullptr;   // internal stream for setup and host-pointer solves
     int grid = 0;
+    int grid_solve = 0;
     sssp::engine::Context single;    // single-query context
     sssp::engine::Context* batch = nullptr;  // multi-query context (grown on demand)
     std::mutex mu;

@@ -19,47 +19,105 @@
 //               minima.  The last CTA to finish closes the round.
 // Both kernels pull work dynamically: 32 list entries per warp with a
 // warp-local load balance over their edges, or one chunk of a hub vertex.
-// Every lane keeps kUnroll edges in flight (independent adjacency loads,
-// then independent 32-byte state gathers); the adjacency is streamed with
-// an evict-first policy so the state records stay in L2; list appends go
-// through warp-private buffers flushed 32 entries per atomic.
+// Edges go through a per-warp three-stage cp.async pipeline in shared
+// memory: adjacency entries two batches ahead, neighbour states one batch
+// ahead, compute on the current batch.  List appends go through
+// warp-private buffers flushed 32 entries per atomic.
 #include "sssp_dev.cuh"
 
 namespace sssp {
 
 constexpr u32 kFull = 0xFFFFFFFFu;
-constexpr u32 kUnroll = 4;     // edges per lane in flight
-constexpr u32 kWarps = 8;      // warps per CTA (256 threads)
-constexpr u32 kQCap = 64;      // entries of a warp append buffer
+constexpr u32 kWarps = 8;       // warps per CTA (256 threads)
+constexpr u32 kQCap = 64;       // entries of a warp append buffer
+constexpr u32 kB = 64;          // edges per warp batch
+constexpr u32 kBI = kB / 32;    // batch edges per lane
+constexpr u32 kAS = 3;          // adjacency slots: batches b, b + 1, b + 2 in flight
+constexpr u32 kDS = 2;          // neighbour-state slots: batches b, b + 1
 
 // ------------------------------------------------------------------ helpers
 
-__device__ __forceinline__ ulonglong4_32a ld_rec(const VRec* p) {
-    return *reinterpret_cast<const ulonglong4_32a*>(p);
-}
-// The two words a round reads from a neighbour: packed D and the lower-bound
-// word of round parity `cur` (both in the record's 32-byte sector).
-struct DC {
-    u64 d, c;
-};
-__device__ __forceinline__ DC ld_dc(const VRec* p, u32 cur) {
-    DC r;
-    if (cur == 0) {
-        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(p);
-        r.d = v.x;
-        r.c = v.y;
-    } else {
-        r.d = p->dp;
-        r.c = p->cf[1];
-    }
-    return r;
-}
-// Adjacency entries are read once per visit: stream them (evict first).
-__device__ __forceinline__ uint2 ld_stream(const uint2* p) { return __ldcs(p); }
 __device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
 __device__ __forceinline__ u64 umax64(u64 a, u64 b) { return a > b ? a : b; }
 __device__ __forceinline__ u32 ld_volatile(const u32* p) { return *(volatile const u32*)p; }
 __device__ __forceinline__ u64 ld_volatile(const u64* p) { return *(volatile const u64*)p; }
+__device__ __forceinline__ u32 lanemask_le(u32 lane) { return 0xFFFFFFFFu >> (31 - lane); }
+
+// The two words a round reads from a vertex: packed D and the lower-bound
+// word of round parity `cur` (both in the record's 32-byte sector).
+__device__ __forceinline__ ulonglong2 ld_dc(const VRec* p, u32 cur) {
+    if (cur == 0) return *reinterpret_cast<const ulonglong2*>(p);
+    return make_ulonglong2(p->dp, p->cf[1]);
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async_8(void* s, const void* g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(s)), "l"(g)
+                 : "memory");
+}
+// L2 policy for data read once per visit (adjacency): evicted first, so the
+// per-vertex state stays resident in L2.
+__device__ __forceinline__ u64 policy_evict_first() {
+    u64 pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void cp_async_8_stream(void* s, const void* g, u64 pol) {
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;\n" ::"r"(
+                     smem_addr(s)),
+                 "l"(g), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* s, const void* g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(s)), "l"(g)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Neighbour-state slot of a staged edge.  k_cupdate needs (D, C[cur]) -- 16
+// bytes; k_relax also needs outWeight and the in-degree -- the whole record.
+struct DcSlot {
+    ulonglong2 v;                       // (D word, C word of the round parity)
+    __device__ __forceinline__ void issue(const VRec* p, u32 cur) {
+        if (cur == 0) {
+            cp_async_16(&v, p);
+        } else {
+            cp_async_8(&v.x, &p->dp);
+            cp_async_8(&v.y, &p->cf[1]);
+        }
+    }
+    __device__ __forceinline__ u64 d() const { return v.x; }
+    __device__ __forceinline__ u64 c(u32) const { return v.y; }
+};
+struct RecSlot {
+    ulonglong2 lo, hi;                  // the 32-byte record
+    __device__ __forceinline__ void issue(const VRec* p, u32) {
+        cp_async_16(&lo, p);
+        cp_async_16(&hi, reinterpret_cast<const char*>(p) + 16);
+    }
+    __device__ __forceinline__ u64 d() const { return lo.x; }
+    __device__ __forceinline__ u64 c(u32 cur) const { return cur ? hi.x : lo.y; }
+    __device__ __forceinline__ u32 outw() const { return (u32)hi.y; }
+    __device__ __forceinline__ u32 indeg() const { return (u32)(hi.y >> 32); }
+};
+
+// Shared-memory pipeline of one warp: adjacency of three batches and
+// neighbour states of two; nz lists the lanes of the current tile with edges.
+template <class S>
+struct __align__(16) WarpStage {
+    S dc[kDS][kB];
+    uint2 adj[kAS][kB];                 // {neighbour, weight}
+    unsigned char own[kAS][kB];         // lane owning the edge (small tiles)
+    unsigned char nz[32];
+};
 
 __device__ __forceinline__ u32 warp_incl_scan(u32 x, u32 lane) {
 #pragma unroll
@@ -199,65 +257,192 @@ __device__ __forceinline__ const InstDesc& desc_of(const RoundParams& P, u32 g, 
     return P.g;
 }
 
-// ---------------------------------------------------------------- k_relax
+// ------------------------------------------------------------- pipeline
 
-// Relaxes kUnroll out-edges per lane (SP_4 step 3) and queues newly
-// discovered targets.  Call with all lanes of the warp.
-template <bool MULTI>
-__device__ __forceinline__ void relax_edges(const RoundParams& P, u32 cur, const bool* ev,
-                                            const uint2* e, const u64* dx, const u32* xloc,
-                                            const u64* gbase, const u64* const* in_off,
-                                            const u32* inst, Acc& a, WarpQueue& q, u32 lane) {
-    DC v[kUnroll];
-    u32 gy[kUnroll];
-#pragma unroll
-    for (u32 u = 0; u < kUnroll; ++u) {
-        gy[u] = (u32)(gbase[u] + e[u].x);
-        if (ev[u]) v[u] = ld_dc(P.rec + gy[u], cur);
+// Drives batches 0 .. nbat-1 through the pipeline.  issue_adj(b, slot) and
+// issue_dc(b, aslot, dslot) start cp.async copies (no wait); compute(b,
+// aslot, dslot) consumes a batch.  Commit groups, in order: A0 A1 D0, then
+// per batch b: A(b+2) D(b+1); so waiting for all but the newest group
+// completes A(b+1), and all but the newest two completes D(b).
+template <class IA, class ID, class CO>
+__device__ __forceinline__ void run_pipeline(u32 nbat, IA issue_adj, ID issue_dc, CO compute) {
+    if (nbat == 0) return;
+    issue_adj(0u, 0u);
+    cp_async_commit();
+    if (nbat > 1) issue_adj(1u, 1u);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();
+    issue_dc(0u, 0u, 0u);
+    cp_async_commit();
+    for (u32 b = 0; b < nbat; ++b) {
+        cp_async_wait<1>();
+        __syncwarp();
+        if (b + 2 < nbat) issue_adj(b + 2, (b + 2) % kAS);
+        cp_async_commit();
+        if (b + 1 < nbat) issue_dc(b + 1, (b + 1) % kAS, (b + 1) % kDS);
+        cp_async_commit();
+        cp_async_wait<2>();
+        __syncwarp();
+        compute(b, b % kAS, b % kDS);
+        __syncwarp();
     }
-    bool fresh[kUnroll];
-    u64 indeg[kUnroll];
+    cp_async_wait<0>();
+}
+
+// A small tile: 32 list entries, lane i with deg_i edges starting at
+// position excl_i of the tile's concatenated edge space.
+struct Tile {
+    u32 excl, total, nzmask;
+    u64 eaddr;                           // lane's first edge (uint2*)
+    u64 pol;                             // L2 policy of the adjacency copies
+};
+
+template <class S>
+__device__ __forceinline__ Tile make_tile(WarpStage<S>& st, u32 deg, u64 eaddr, u32 lane) {
+    Tile t;
+    const u32 incl = warp_incl_scan(deg, lane);
+    t.total = __shfl_sync(kFull, incl, 31);
+    t.excl = incl - deg;
+    t.eaddr = eaddr;
+    t.pol = policy_evict_first();
+    t.nzmask = __ballot_sync(kFull, deg > 0);
+    if (deg > 0) st.nz[__popc(t.nzmask & ((1u << lane) - 1u))] = (unsigned char)lane;
+    __syncwarp();
+    return t;
+}
+
+// Owner lane of position j0 + lane of a tile, and the segment heads of that
+// row (bit p: position j0 + p starts an owner's edge list).
+template <class S>
+__device__ __forceinline__ u32 row_owner(const WarpStage<S>& st, const Tile& t, u32 j0, u32 deg,
+                                         u32 lane, u32& heads) {
+    const bool hd = deg > 0 && t.excl >= j0 && t.excl < j0 + 32;
+    heads = __reduce_or_sync(kFull, hd ? (1u << (t.excl - j0)) : 0u);
+    const u32 o0 = find_owner(t.excl, j0);
+    const u32 r0 = __popc(t.nzmask & ((1u << o0) - 1u));
+    const u32 rank = r0 + __popc(heads & lanemask_le(lane)) - (heads & 1u);
+    return st.nz[rank & 31u];
+}
+
+// Starts copying edges [b0, b0 + kB) of a tile into adjacency slot s.
+template <class S>
+__device__ __forceinline__ void issue_tile_adj(WarpStage<S>& st, const Tile& t, u32 s, u32 b0,
+                                               u32 deg, u32 lane) {
 #pragma unroll
-    for (u32 u = 0; u < kUnroll; ++u) {
-        fresh[u] = false;
-        indeg[u] = 0;
-        if (!ev[u]) continue;
-        const u64 dd = dx[u] + e[u].y;
-        const u64 cand = (dd << P.vbits) | xloc[u];
-        if ((v[u].c & kFixed) || cand >= v[u].d) continue;
-        const u64 old = atomicMin(&P.rec[gy[u]].dp, cand);
-        if (cand < old) {
-            const u32 ow = P.rec[gy[u]].outw;
-            fold<MULTI>(P, inst[u], cur, dd, ow == kNoOutW ? P.dinf : dd + ow, a);
-            fresh[u] = (old == kInf64);
+    for (u32 i = 0; i < kBI; ++i) {
+        const u32 j0 = b0 + 32 * i;
+        if (j0 >= t.total) break;                 // warp-uniform
+        u32 heads;
+        const u32 own = row_owner(st, t, j0, deg, lane, heads);
+        const u32 j = j0 + lane;
+        const u32 k = j - __shfl_sync(kFull, t.excl, own);
+        const uint2* ep = reinterpret_cast<const uint2*>(__shfl_sync(kFull, t.eaddr, own)) + k;
+        if (j < t.total) {
+            cp_async_8_stream(&st.adj[s][32 * i + lane], ep, t.pol);
+            st.own[s][32 * i + lane] = (unsigned char)own;
         }
     }
+}
+
+// Starts copying contiguous edges [e0, e1) (at most kB) into slot s.
+template <class S>
+__device__ __forceinline__ void issue_range_adj(WarpStage<S>& st, u32 s, const uint2* adj, u64 e0,
+                                                u64 e1, u32 lane) {
+    const u64 pol = policy_evict_first();
 #pragma unroll
-    for (u32 u = 0; u < kUnroll; ++u)
-        if (fresh[u]) indeg[u] = in_off[u][e[u].x + 1] - in_off[u][e[u].x];
+    for (u32 i = 0; i < kBI; ++i) {
+        const u64 e = e0 + 32 * i + lane;
+        if (e < e1) cp_async_8_stream(&st.adj[s][32 * i + lane], adj + e, pol);
+    }
+}
+
+// Starts gathering the neighbour states of the nb edges in adjacency slot
+// as into state slot ds.  `base` is the record base of the edge's graph,
+// taken from the owning lane in multi-query mode.
+template <bool MULTI, class S>
+__device__ __forceinline__ void issue_dc(const RoundParams& P, WarpStage<S>& st, u32 as, u32 ds,
+                                         u32 nb, u32 cur, u64 base, bool per_owner, u32 lane) {
 #pragma unroll
-    for (u32 u = 0; u < kUnroll; ++u) {
-        const bool sm = fresh[u] && indeg[u] <= P.hub;
-        wq_push(P, q, &P.ctl->nAS[cur], P.L.AS[cur], sm, gy[u], lane);
-        if (fresh[u] && !sm) put_hub(P, &P.ctl->AHpk[cur], P.L.AH[cur], gy[u], indeg[u]);
+    for (u32 i = 0; i < kBI; ++i) {
+        if (32 * i >= nb) break;                   // warp-uniform
+        const u32 idx = 32 * i + lane;
+        const bool ev = idx < nb;
+        u64 ob = base;
+        if (MULTI && per_owner) ob = __shfl_sync(kFull, base, ev ? st.own[as][idx] : 0u);
+        if (ev) st.dc[ds][idx].issue(P.rec + (u32)(ob + st.adj[as][idx].x), cur);
+    }
+}
+
+// ---------------------------------------------------------------- k_relax
+
+typedef WarpStage<RecSlot> RelaxStage;
+
+// Relaxation of the staged edges [0, nb) (SP_4 step 3): per edge the owner's
+// distance dx and id xloc; newly discovered targets are queued.
+template <bool MULTI>
+__device__ __forceinline__ void relax_batch(const RoundParams& P, RelaxStage& st, u32 as, u32 ds,
+                                            u32 nb, u32 cur, bool per_owner, u64 dx, u32 xloc,
+                                            u64 gbase, u32 inst, Acc& a, WarpQueue& q,
+                                            u32 lane) {
+    u64 cand[kBI], old[kBI];
+    u32 gy[kBI];
+#pragma unroll
+    for (u32 i = 0; i < kBI; ++i) {
+        cand[i] = 0;
+        old[i] = 0;                                // "not lowered"
+        gy[i] = 0;
+        if (32 * i >= nb) break;                   // warp-uniform
+        const u32 idx = 32 * i + lane;
+        const bool ev = idx < nb;
+        const u32 own = (per_owner && ev) ? st.own[as][idx] : lane;
+        const u64 odx = per_owner ? __shfl_sync(kFull, dx, own) : dx;
+        const u32 ox = per_owner ? __shfl_sync(kFull, xloc, own) : xloc;
+        u64 ob = gbase;
+        if (MULTI && per_owner) ob = __shfl_sync(kFull, gbase, own);
+        if (!ev) continue;
+        const uint2 e = st.adj[as][idx];
+        const RecSlot& v = st.dc[ds][idx];
+        cand[i] = ((odx + e.y) << P.vbits) | ox;
+        gy[i] = (u32)(ob + e.x);
+        if (!(v.c(cur) & kFixed) && cand[i] < v.d()) old[i] = atomicMin(&P.rec[gy[i]].dp, cand[i]);
+        a.edges++;
+    }
+#pragma unroll
+    for (u32 i = 0; i < kBI; ++i) {
+        if (32 * i >= nb) break;                   // warp-uniform
+        const u32 idx = 32 * i + lane;
+        const bool ok = cand[i] < old[i];          // old = 0 when not tried
+        const bool fresh = ok && old[i] == kInf64;
+        u32 indeg = 0;
+        if (ok) {
+            const RecSlot& v = st.dc[ds][idx];
+            u32 oinst = inst;
+            if (MULTI && per_owner) oinst = P.page_owner[gy[i] >> P.page_shift];
+            const u32 ow = v.outw();
+            const u64 dd = cand[i] >> P.vbits;
+            fold<MULTI>(P, oinst, cur, dd, ow == kNoOutW ? P.dinf : dd + ow, a);
+            indeg = v.indeg();
+        }
+        const bool sm = fresh && indeg <= P.hub;
+        wq_push(P, q, &P.ctl->nAS[cur], P.L.AS[cur], sm, gy[i], lane);
+        if (fresh && !sm) put_hub(P, &P.ctl->AHpk[cur], P.L.AH[cur], gy[i], indeg);
     }
 }
 
 template <bool MULTI>
-__device__ void relax_small(const RoundParams& P, u32 t, u32 nfs, u32 cur, u32 lane, Acc& a,
-                            WarpQueue& q) {
+__device__ void relax_small(const RoundParams& P, RelaxStage& st, u32 t, u32 nfs, u32 cur,
+                            u32 lane, Acc& a, WarpQueue& q) {
     const u32 idx = t * 32 + lane;
     const bool valid = idx < nfs;
     u32 g = 0, xloc = 0, inst = 0, deg = 0;
     u64 gbase = 0, b = 0, dx = 0;
     const uint2* adj = P.g.out_adj;
-    const u64* in_off = P.g.in_off;
     if (valid) {
         g = P.L.FS[cur][idx];
         const InstDesc& d = desc_of<MULTI>(P, g, inst);
         gbase = d.base;
         adj = d.out_adj;
-        in_off = d.in_off;
         xloc = g - (u32)gbase;
         b = d.out_off[xloc];
         deg = (u32)(d.out_off[xloc + 1] - b);
@@ -267,48 +452,22 @@ __device__ void relax_small(const RoundParams& P, u32 t, u32 nfs, u32 cur, u32 l
         dx = cfx & kCMask;           // C = D for a fixed vertex
         a.visits++;
     }
-    const u32 incl = warp_incl_scan(deg, lane);
-    const u32 total = __shfl_sync(kFull, incl, 31);
-    const u32 excl = incl - deg;
-    const u64 eaddr = (u64)(adj + b);
-    for (u32 j0 = 0; j0 < total; j0 += 32 * kUnroll) {
-        bool ev[kUnroll];
-        uint2 e[kUnroll];
-        u64 odx[kUnroll], ob[kUnroll];
-        u32 ox[kUnroll], oinst[kUnroll];
-        const u64* oin[kUnroll];
-#pragma unroll
-        for (u32 u = 0; u < kUnroll; ++u) {
-            ev[u] = false;
-            e[u] = make_uint2(0, 0);
-            odx[u] = 0;
-            ox[u] = 0;
-            ob[u] = 0;
-            oinst[u] = 0;
-            oin[u] = in_off;
-            if (j0 + 32 * u >= total) continue;    // warp-uniform
-            const u32 j = j0 + 32 * u + lane;
-            ev[u] = j < total;
-            const u32 own = find_owner(excl, j);
-            const u32 k = j - __shfl_sync(kFull, excl, own);
-            const uint2* ep = reinterpret_cast<const uint2*>(__shfl_sync(kFull, eaddr, own)) + k;
-            odx[u] = __shfl_sync(kFull, dx, own);
-            ox[u] = __shfl_sync(kFull, xloc, own);
-            if (MULTI) {
-                ob[u] = __shfl_sync(kFull, gbase, own);
-                oin[u] = reinterpret_cast<const u64*>(__shfl_sync(kFull, (u64)in_off, own));
-                oinst[u] = __shfl_sync(kFull, inst, own);
-            }
-            if (ev[u]) e[u] = ld_stream(ep);
-            a.edges += ev[u];
-        }
-        relax_edges<MULTI>(P, cur, ev, e, odx, ox, ob, oin, oinst, a, q, lane);
-    }
+    const Tile tl = make_tile(st, deg, (u64)(adj + b), lane);
+    run_pipeline(
+        (tl.total + kB - 1) / kB,
+        [&](u32 bb, u32 s) { issue_tile_adj(st, tl, s, bb * kB, deg, lane); },
+        [&](u32 bb, u32 as, u32 ds) {
+            issue_dc<MULTI>(P, st, as, ds, min(kB, tl.total - bb * kB), cur, gbase, true, lane);
+        },
+        [&](u32 bb, u32 as, u32 ds) {
+            relax_batch<MULTI>(P, st, as, ds, min(kB, tl.total - bb * kB), cur, true, dx, xloc,
+                               gbase, inst, a, q, lane);
+        });
 }
 
 template <bool MULTI>
-__device__ void relax_hub(const RoundParams& P, u32 c, u32 nfh, u32 cur, u32 lane, Acc& a,
-                          WarpQueue& q) {
+__device__ void relax_hub(const RoundParams& P, RelaxStage& st, u32 c, u32 nfh, u32 cur,
+                          u32 lane, Acc& a, WarpQueue& q) {
     const uint2* FH = P.L.FH[cur];
     u32 lo = 0, hi = nfh;
     while (hi - lo > 1) {
@@ -329,37 +488,25 @@ __device__ void relax_hub(const RoundParams& P, u32 c, u32 nfh, u32 cur, u32 lan
         rx->cf[cur ^ 1] = cfx;
         a.visits++;
     }
-    bool ev[kUnroll];
-    uint2 e[kUnroll];
-    u64 odx[kUnroll], ob[kUnroll];
-    u32 ox[kUnroll], oinst[kUnroll];
-    const u64* oin[kUnroll];
-#pragma unroll
-    for (u32 u = 0; u < kUnroll; ++u) {
-        odx[u] = cfx & kCMask;
-        ox[u] = xloc;
-        ob[u] = d.base;
-        oinst[u] = inst;
-        oin[u] = d.in_off;
-    }
-    for (u64 e0 = cb; e0 < ce; e0 += 32 * kUnroll) {
-#pragma unroll
-        for (u32 u = 0; u < kUnroll; ++u) {
-            const u64 ei = e0 + 32 * u + lane;
-            ev[u] = ei < ce;
-            e[u] = ev[u] ? ld_stream(d.out_adj + ei) : make_uint2(0, 0);
-            a.edges += ev[u];
-        }
-        relax_edges<MULTI>(P, cur, ev, e, odx, ox, ob, oin, oinst, a, q, lane);
-    }
+    const u32 n = ce > cb ? (u32)(ce - cb) : 0u;
+    run_pipeline(
+        (n + kB - 1) / kB,
+        [&](u32 bb, u32 s) { issue_range_adj(st, s, d.out_adj, cb + bb * kB, ce, lane); },
+        [&](u32 bb, u32 as, u32 ds) {
+            issue_dc<MULTI>(P, st, as, ds, min(kB, n - bb * kB), cur, d.base, false, lane);
+        },
+        [&](u32 bb, u32 as, u32 ds) {
+            relax_batch<MULTI>(P, st, as, ds, min(kB, n - bb * kB), cur, false, cfx & kCMask,
+                               xloc, d.base, inst, a, q, lane);
+        });
 }
 
+// Step (a) of round r over the whole frontier (all CTAs of the grid).
 template <bool MULTI>
-__global__ void __launch_bounds__(256, 2) k_relax(RoundParams P) {
-    __shared__ u32 s_q[kWarps][kQCap];
+__device__ void relax_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
+    RelaxStage* s_st = reinterpret_cast<RelaxStage*>(s_dyn);
+    u32* s_q = reinterpret_cast<u32*>(s_dyn + sizeof(RelaxStage) * kWarps);
     Ctl* ctl = P.ctl;
-    if (ld_volatile(&ctl->status) != kRunning) return;
-    const u32 r = ctl->round;
     const u32 cur = r & 1u, nxt = cur ^ 1u;
     const u32 lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
 
@@ -392,29 +539,39 @@ __global__ void __launch_bounds__(256, 2) k_relax(RoundParams P) {
     const u32 total = tiles + fh_chunks;
 
     Acc a = {kInf64, kInf64, 0, 0, 0};
-    WarpQueue q = {s_q[wib], 0};
-    for (;;) {
-        u32 item = 0;
-        if (lane == 0) item = atomicAdd(&ctl->work[0], 1u);
-        item = __shfl_sync(kFull, item, 0);
-        if (item >= total) break;
-        if (item < tiles) relax_small<MULTI>(P, item, nfs, cur, lane, a, q);
-        else relax_hub<MULTI>(P, item - tiles, nfh, cur, lane, a, q);
+    WarpQueue q = {s_q + wib * kQCap, 0};
+    // First item per warp is static (no atomic); the rest are pulled.
+    const u32 nwarps = gridDim.x * kWarps;
+    for (u32 item = blockIdx.x * kWarps + wib; item < total;) {
+        if (item < tiles) relax_small<MULTI>(P, s_st[wib], item, nfs, cur, lane, a, q);
+        else relax_hub<MULTI>(P, s_st[wib], item - tiles, nfh, cur, lane, a, q);
+        u32 next = 0;
+        if (lane == 0) next = atomicAdd(&ctl->work[0], 1u) + nwarps;
+        item = __shfl_sync(kFull, next, 0);
     }
     wq_flush(P, q, &ctl->nAS[cur], P.L.AS[cur], lane);
     flush<MULTI>(P, cur, a, lane, 0, 3);
 }
 
+template <bool MULTI>
+__global__ void __launch_bounds__(256, 3) k_relax(RoundParams P) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    if (ld_volatile(&P.ctl->status) != kRunning) return;
+    relax_phase<MULTI>(P, s_dyn, P.ctl->round);
+}
+
 // -------------------------------------------------------------- k_cupdate
+
+typedef WarpStage<DcSlot> CupStage;
 
 // lb(x): the lower bound an in-neighbour contributes (Lemmas 7 and 8); with
 // rule 1 the printed SP_4 step 4 clamp (minD for unfixed vertices).
-__device__ __forceinline__ u64 lb_of(const RoundParams& P, const DC& v, u64 thr, u64 minD) {
-    const u64 dx = v.d >> P.vbits;            // infinity maps to dinf
-    const u64 cfx = v.c;
-    const u64 cx = cfx & kCMask;
+__device__ __forceinline__ u64 lb_of(const RoundParams& P, const DcSlot& v, u64 thr, u64 minD) {
+    const u64 dx = v.d() >> P.vbits;          // infinity maps to dinf
+    const u64 cw = v.c(0);
+    const u64 cx = cw & kCMask;
     if (P.rule == 0) return umax64(cx, umin64(dx, thr));
-    return (cfx & kFixed) ? cx : umax64(cx, minD);
+    return (cw & kFixed) ? cx : umax64(cx, minD);
 }
 
 // Decision for one active vertex after its Eq. (1) minimum m is known.
@@ -427,9 +584,9 @@ __device__ __forceinline__ u64 decide(const RoundParams& P, u64 dy, u64 cy, u64 
 }
 
 template <bool MULTI>
-__device__ void cup_small(const RoundParams& P, u32 t, u32 nas, u32 r, u32 cur, u32 lane,
-                          u64* smin, u64 thr0, u64 minD0, Acc& a, Acc& an, WarpQueue& qf,
-                          WarpQueue& qa) {
+__device__ void cup_small(const RoundParams& P, CupStage& st, u32 t, u32 nas, u32 r, u32 cur,
+                          u32 lane, u64* smin, u64 thr0, u64 minD0, Acc& a, Acc& an,
+                          WarpQueue& qf, WarpQueue& qa) {
     const u32 nxt = cur ^ 1u;
     const u32 idx = t * 32 + lane;
     const bool valid = idx < nas;
@@ -450,74 +607,60 @@ __device__ void cup_small(const RoundParams& P, u32 t, u32 nas, u32 r, u32 cur, 
         yloc = g - (u32)gbase;
         ib = d.in_off[yloc];
         deg = (u32)(d.in_off[yloc + 1] - ib);
-        const ulonglong4_32a v = ld_rec(P.rec + g);
+        const ulonglong2 v = ld_dc(P.rec + g, cur);
         dy = v.x >> P.vbits;
-        cy = (cur ? v.z : v.y) & kCMask;
-        outw = (u32)v.w;
+        cy = v.y & kCMask;
+        outw = P.rec[g].outw;
     }
     smin[lane] = kInf64;
+    const Tile tl = make_tile(st, deg, (u64)(in_adj + ib), lane);
+    run_pipeline(
+        (tl.total + kB - 1) / kB,
+        [&](u32 b, u32 s) { issue_tile_adj(st, tl, s, b * kB, deg, lane); },
+        [&](u32 b, u32 as, u32 ds) {
+            issue_dc<MULTI>(P, st, as, ds, min(kB, tl.total - b * kB), cur, gbase, true, lane);
+        },
+        [&](u32 b, u32 as, u32 ds) {
+            const u32 nb = min(kB, tl.total - b * kB);
+#pragma unroll
+            for (u32 i = 0; i < kBI; ++i) {
+                if (32 * i >= nb) break;                   // warp-uniform
+                const u32 sidx = 32 * i + lane;
+                const bool ev = sidx < nb;
+                const u32 own = ev ? st.own[as][sidx] : 0u;
+                u64 othr = thr, omin = minD;
+                if (MULTI) {
+                    othr = __shfl_sync(kFull, thr, own);
+                    omin = __shfl_sync(kFull, minD, own);
+                }
+                u64 val = kInf64;
+                if (ev)
+                    val = umin64(lb_of(P, st.dc[ds][sidx], othr, omin) + st.adj[as][sidx].y,
+                                 P.dinf);
+                // Segmented min over lanes sharing an owner: owners are
+                // contiguous, a lane's segment starts at the last owner
+                // change at or before it.
+                const u32 prev = __shfl_up_sync(kFull, own, 1);
+                const u32 brk = __ballot_sync(kFull, lane == 0 || !ev || prev != own);
+                const u32 span = lane - (31 - __clz(brk & lanemask_le(lane)));
+#pragma unroll
+                for (u32 dd = 1; dd < 32; dd <<= 1) {
+                    const u64 ov = __shfl_up_sync(kFull, val, dd);
+                    if (dd <= span) val = umin64(val, ov);
+                }
+                const bool tail = ev && (lane == 31 || ((brk >> (lane + 1)) & 1u));
+                if (tail) smin[own] = umin64(smin[own], val);
+                __syncwarp();
+            }
+        });
+    a.edges += (lane == 0) ? tl.total : 0;
     __syncwarp();
-    const u32 incl = warp_incl_scan(deg, lane);
-    const u32 total = __shfl_sync(kFull, incl, 31);
-    const u32 excl = incl - deg;
-    const u64 eaddr = (u64)(in_adj + ib);
-    for (u32 j0 = 0; j0 < total; j0 += 32 * kUnroll) {
-        bool ev[kUnroll];
-        uint2 e[kUnroll];
-        u32 own[kUnroll];
-        u64 othr[kUnroll], omin[kUnroll], ob[kUnroll];
-#pragma unroll
-        for (u32 u = 0; u < kUnroll; ++u) {
-            ev[u] = false;
-            own[u] = 0;
-            e[u] = make_uint2(0, 0);
-            othr[u] = thr;
-            omin[u] = minD;
-            ob[u] = 0;
-            if (j0 + 32 * u >= total) continue;    // warp-uniform
-            const u32 j = j0 + 32 * u + lane;
-            ev[u] = j < total;
-            own[u] = find_owner(excl, j);
-            const u32 k = j - __shfl_sync(kFull, excl, own[u]);
-            const uint2* ep =
-                reinterpret_cast<const uint2*>(__shfl_sync(kFull, eaddr, own[u])) + k;
-            if (MULTI) {
-                othr[u] = __shfl_sync(kFull, thr, own[u]);
-                omin[u] = __shfl_sync(kFull, minD, own[u]);
-                ob[u] = __shfl_sync(kFull, gbase, own[u]);
-            }
-            if (ev[u]) e[u] = ld_stream(ep);
-        }
-        DC v[kUnroll];
-#pragma unroll
-        for (u32 u = 0; u < kUnroll; ++u)
-            if (ev[u]) v[u] = ld_dc(P.rec + (u32)(ob[u] + e[u].x), cur);
-#pragma unroll
-        for (u32 u = 0; u < kUnroll; ++u) {
-            if (j0 + 32 * u >= total) continue;    // warp-uniform
-            u64 val = kInf64;
-            if (ev[u]) val = umin64(lb_of(P, v[u], othr[u], omin[u]) + e[u].y, P.dinf);
-            // Segmented min over lanes sharing an owner (contiguous by construction).
-            const u32 key = ev[u] ? own[u] : 32u + lane;
-#pragma unroll
-            for (u32 dd = 1; dd < 32; dd <<= 1) {
-                const u64 ov = __shfl_up_sync(kFull, val, dd);
-                const u32 ok = __shfl_up_sync(kFull, key, dd);
-                if (lane >= dd && ok == key) val = umin64(val, ov);
-            }
-            const u32 nk = __shfl_down_sync(kFull, key, 1);
-            if (ev[u] && (lane == 31 || nk != key)) smin[own[u]] = umin64(smin[own[u]], val);
-            __syncwarp();
-        }
-    }
-    a.edges += (lane == 0) ? total : 0;
 
     bool fix = false;
     if (valid) {
         const u64 cn = decide(P, dy, cy, smin[lane], thr, minD, fix);
-        VRec* ry = P.rec + g;
-        ry->cf[nxt] = cn | (fix ? kFixed : 0ull);
-        if (fix) ry->fround = (int)r;
+        P.rec[g].cf[nxt] = cn | (fix ? kFixed : 0ull);
+        if (fix) P.fround[g] = (int)r;
         a.visits++;
     }
     __syncwarp();
@@ -537,8 +680,8 @@ __device__ void cup_small(const RoundParams& P, u32 t, u32 nas, u32 r, u32 cur, 
 }
 
 template <bool MULTI>
-__device__ void cup_hub(const RoundParams& P, u32 c, u32 nah, u32 ah_chunks, u32 r, u32 cur,
-                        u32 lane, u64 thr0, u64 minD0, Acc& a, Acc& an) {
+__device__ void cup_hub(const RoundParams& P, CupStage& st, u32 c, u32 nah, u32 ah_chunks,
+                        u32 r, u32 cur, u32 lane, u64 thr0, u64 minD0, Acc& a, Acc& an) {
     const u32 nxt = cur ^ 1u;
     const uint2* AH = P.L.AH[cur];
     u32 lo = 0, hi = nah;
@@ -561,22 +704,24 @@ __device__ void cup_hub(const RoundParams& P, u32 c, u32 nah, u32 ah_chunks, u32
     const u64 cb = ib + (u64)k * P.chunk;
     const u64 ce = umin64(cb + P.chunk, ie);
     u64 val = kInf64;
-    for (u64 e0 = cb + lane; e0 < ce; e0 += 32 * kUnroll) {
-        uint2 e[kUnroll];
-        bool ev[kUnroll];
+    const u32 n = ce > cb ? (u32)(ce - cb) : 0u;
+    run_pipeline(
+        (n + kB - 1) / kB,
+        [&](u32 b, u32 s) { issue_range_adj(st, s, d.in_adj, cb + b * kB, ce, lane); },
+        [&](u32 b, u32 as, u32 ds) {
+            issue_dc<MULTI>(P, st, as, ds, min(kB, n - b * kB), cur, d.base, false, lane);
+        },
+        [&](u32 b, u32 as, u32 ds) {
+            const u32 nb = min(kB, n - b * kB);
 #pragma unroll
-        for (u32 u = 0; u < kUnroll; ++u) {
-            ev[u] = e0 + 32 * u < ce;
-            e[u] = ev[u] ? ld_stream(d.in_adj + e0 + 32 * u) : make_uint2(0, 0);
-        }
-        DC v[kUnroll];
-#pragma unroll
-        for (u32 u = 0; u < kUnroll; ++u)
-            if (ev[u]) v[u] = ld_dc(P.rec + (u32)(d.base + e[u].x), cur);
-#pragma unroll
-        for (u32 u = 0; u < kUnroll; ++u)
-            if (ev[u]) val = umin64(val, umin64(lb_of(P, v[u], thr, minD) + e[u].y, P.dinf));
-    }
+            for (u32 i = 0; i < kBI; ++i) {
+                const u32 sidx = 32 * i + lane;
+                if (sidx < nb)
+                    val = umin64(val, umin64(lb_of(P, st.dc[ds][sidx], thr, minD) +
+                                                 st.adj[as][sidx].y,
+                                             P.dinf));
+            }
+        });
     val = warp_min64(val);
     if (lane != 0) return;
     a.edges += ce - cb;
@@ -588,16 +733,16 @@ __device__ void cup_hub(const RoundParams& P, u32 c, u32 nah, u32 ah_chunks, u32
     const u64 m = atomicExch(&P.L.hubmin[lo], kInf64);
     P.L.hubcnt[lo] = 0;
     VRec* ry = P.rec + g;
-    const ulonglong4_32a v = ld_rec(ry);
+    const ulonglong2 v = ld_dc(ry, cur);
     const u64 dy = v.x >> P.vbits;
-    const u64 cy = (cur ? v.z : v.y) & kCMask;
-    const u32 outw = (u32)v.w;
+    const u64 cy = v.y & kCMask;
+    const u32 outw = ry->outw;
     bool fix;
     const u64 cn = decide(P, dy, cy, m, thr, minD, fix);
     ry->cf[nxt] = cn | (fix ? kFixed : 0ull);
     a.visits++;
     if (fix) {
-        ry->fround = (int)r;
+        P.fround[g] = (int)r;
         const u64 odeg = d.out_off[yloc + 1] - d.out_off[yloc];
         if (odeg <= P.hub) put_small(P, P.L.FS[nxt], atomicAdd(&P.ctl->nFS[nxt], 1u), g);
         else put_hub(P, &P.ctl->FHpk[nxt], P.L.FH[nxt], g, odeg);
@@ -644,23 +789,19 @@ __device__ void round_epilogue(const RoundParams& P, u32 r) {
         else if (r + 1 > ctl->round_limit) st = kErrRounds;
         ctl->status = st;
         __threadfence();
-        if (P.cond) cudaGraphSetConditional(P.cond, (st == kRunning && r + 1 <= ctl->stop_round) ? 1u : 0u);
+        if (P.cond)
+            cudaGraphSetConditional(P.cond, (st == kRunning && r + 1 <= ctl->stop_round) ? 1u : 0u);
     }
 }
 
+// Steps (b) and (c) of round r over the whole active set (all CTAs).
 template <bool MULTI>
-__global__ void __launch_bounds__(256, 2) k_cupdate(RoundParams P) {
-    __shared__ u64 s_min[kWarps][32];
-    __shared__ u32 s_qf[kWarps][kQCap];
-    __shared__ u32 s_qa[kWarps][kQCap];
-    __shared__ u32 s_last;
+__device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
+    CupStage* s_st = reinterpret_cast<CupStage*>(s_dyn);
+    u64* s_min = reinterpret_cast<u64*>(s_dyn + sizeof(CupStage) * kWarps);
+    u32* s_qf = reinterpret_cast<u32*>(s_min + kWarps * 32);
+    u32* s_qa = s_qf + kWarps * kQCap;
     Ctl* ctl = P.ctl;
-    if (ld_volatile(&ctl->status) != kRunning) {
-        // Nothing runs: make sure the device loop ends.
-        if (P.cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(P.cond, 0u);
-        return;
-    }
-    const u32 r = ctl->round;
     const u32 cur = r & 1u, nxt = cur ^ 1u;
     const u32 lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->work[0] = 0;
@@ -678,17 +819,20 @@ __global__ void __launch_bounds__(256, 2) k_cupdate(RoundParams P) {
 
     Acc a = {kInf64, kInf64, 0, 0, 0};
     Acc an = {kInf64, kInf64, 0, 0, 0};
-    WarpQueue qf = {s_qf[wib], 0}, qa = {s_qa[wib], 0};
-    for (;;) {
-        u32 item = 0;
-        if (lane == 0) item = atomicAdd(&ctl->work[1], 1u);
-        item = __shfl_sync(kFull, item, 0);
-        if (item >= total) break;
+    WarpQueue qf = {s_qf + wib * kQCap, 0}, qa = {s_qa + wib * kQCap, 0};
+    // First item per warp is static (no atomic); the rest are pulled.
+    const u32 nwarps = gridDim.x * kWarps;
+    for (u32 item = blockIdx.x * kWarps + wib; item < total;) {
         if (item < tiles)
-            cup_small<MULTI>(P, item, nas, r, cur, lane, s_min[wib], thr, minD, a, an, qf, qa);
+            cup_small<MULTI>(P, s_st[wib], item, nas, r, cur, lane, s_min + wib * 32, thr, minD, a,
+                             an, qf, qa);
         else
-            cup_hub<MULTI>(P, item - tiles, nah, ah_chunks, r, cur, lane, thr, minD, a, an);
+            cup_hub<MULTI>(P, s_st[wib], item - tiles, nah, ah_chunks, r, cur, lane, thr, minD, a,
+                           an);
         __syncwarp();
+        u32 next = 0;
+        if (lane == 0) next = atomicAdd(&ctl->work[1], 1u) + nwarps;
+        item = __shfl_sync(kFull, next, 0);
     }
     wq_flush(P, qf, &ctl->nFS[nxt], P.L.FS[nxt], lane);
     wq_flush(P, qa, &ctl->nAS[nxt], P.L.AS[nxt], lane);
@@ -696,7 +840,20 @@ __global__ void __launch_bounds__(256, 2) k_cupdate(RoundParams P) {
     a.fmin_t = an.fmin_t;
     a.nfix = an.nfix;
     flush<MULTI>(P, nxt, a, lane, 1, 2);
+}
 
+template <bool MULTI>
+__global__ void __launch_bounds__(256, 3) k_cupdate(RoundParams P) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    __shared__ u32 s_last;
+    Ctl* ctl = P.ctl;
+    if (ld_volatile(&ctl->status) != kRunning) {
+        // Nothing runs: make sure the device loop ends.
+        if (P.cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(P.cond, 0u);
+        return;
+    }
+    const u32 r = ctl->round;
+    cupdate_phase<MULTI>(P, s_dyn, r);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -706,6 +863,75 @@ __global__ void __launch_bounds__(256, 2) k_cupdate(RoundParams P) {
     if (s_last) {
         __threadfence();
         round_epilogue(P, r);
+    }
+}
+
+// ------------------------------------------------------- persistent loop
+
+// Grid-wide barrier of the persistent kernel (all CTAs are co-resident:
+// cooperative launch).  The last CTA to arrive runs the end-of-round
+// epilogue when asked, then releases the others.  A CTA that waits longer
+// than kBarrierTimeoutNs sets ctl->error bit 4 and returns false, so the
+// kernel ends instead of hanging.
+constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ bool grid_barrier(const RoundParams& P, bool epilogue, u32 r) {
+    __shared__ u32 s_last, s_gen;
+    Ctl* ctl = P.ctl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_gen = ld_volatile(&ctl->bar_gen);
+        __threadfence();
+        s_last = (atomicAdd(&ctl->bar_count, 1u) + 1 == gridDim.x) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (epilogue) round_epilogue(P, r);
+        if (threadIdx.x == 0) {
+            const u32 ti = 2 * (r - P.trace_base) + (epilogue ? 2u : 1u);
+            if (P.trace && ti < P.trace_cap) P.trace[ti] = global_ns();
+            ctl->bar_count = 0;
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        }
+    } else if (threadIdx.x == 0) {
+        const unsigned long long t0 = global_ns();
+        while (ld_volatile(&ctl->bar_gen) == s_gen) {
+            if (global_ns() - t0 > kBarrierTimeoutNs) {
+                atomicOr(&ctl->error, 4u);
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return (ld_volatile(&ctl->error) & 4u) == 0;
+}
+
+// All rounds of the running queries in one launch: relax phase, barrier,
+// lower-bound phase, barrier (whose last arriver closes the round), until
+// no query runs, the stop round is passed, or a barrier times out.
+template <bool MULTI>
+__global__ void __launch_bounds__(256, 3) k_solve(RoundParams P) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    Ctl* ctl = P.ctl;
+    if (P.trace && blockIdx.x == 0 && threadIdx.x == 0 && P.trace_cap) P.trace[0] = global_ns();
+    for (;;) {
+        if (ld_volatile(&ctl->status) != kRunning) break;
+        const u32 r = ld_volatile(&ctl->round);
+        if (r > ld_volatile(&ctl->stop_round)) break;
+        relax_phase<MULTI>(P, s_dyn, r);
+        if (!grid_barrier(P, false, r)) break;
+        cupdate_phase<MULTI>(P, s_dyn, r);
+        if (!grid_barrier(P, true, r)) break;
     }
 }
 
@@ -733,8 +959,9 @@ __global__ void k_start(RoundParams P, u32 first, u32 count, u32 max_rounds) {
         rs.cf[0] = kFixed;
         rs.cf[1] = kFixed;
         rs.outw = d.outw[s];
-        rs.fround = 0;
+        rs.indeg = (u32)(d.in_off[s + 1] - d.in_off[s]);
         P.rec[g] = rs;
+        P.fround[g] = 0;
         const u64 odeg = d.out_off[s + 1] - d.out_off[s];
         if (odeg <= P.hub) put_small(P, P.L.FS[cur], atomicAdd(&ctl->nFS[cur], 1u), g);
         else put_hub(P, &ctl->FHpk[cur], P.L.FH[cur], g, odeg);
@@ -754,6 +981,8 @@ template __global__ void k_cupdate<false>(RoundParams);
 template __global__ void k_cupdate<true>(RoundParams);
 template __global__ void k_start<false>(RoundParams, u32, u32, u32);
 template __global__ void k_start<true>(RoundParams, u32, u32, u32);
+template __global__ void k_solve<false>(RoundParams);
+template __global__ void k_solve<true>(RoundParams);
 
 // --------------------------------------------- host access for the engine
 
@@ -762,6 +991,46 @@ const void* relax_fn(bool multi) {
 }
 const void* cupdate_fn(bool multi) {
     return multi ? (const void*)k_cupdate<true> : (const void*)k_cupdate<false>;
+}
+const void* solve_fn(bool multi) {
+    return multi ? (const void*)k_solve<true> : (const void*)k_solve<false>;
+}
+size_t relax_smem_bytes() { return sizeof(RelaxStage) * kWarps + sizeof(u32) * kWarps * kQCap; }
+size_t cupdate_smem_bytes() {
+    return sizeof(CupStage) * kWarps + sizeof(u64) * kWarps * 32 + 2 * sizeof(u32) * kWarps * kQCap;
+}
+size_t solve_smem_bytes() {
+    return relax_smem_bytes() > cupdate_smem_bytes() ? relax_smem_bytes() : cupdate_smem_bytes();
+}
+
+// Co-resident CTAs per SM of the persistent kernel (its grid must fit).
+int solve_blocks_per_sm(int threads) {
+    int a = 0, b = 0;
+    const size_t sb = solve_smem_bytes();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_solve<false>, threads, sb);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_solve<true>, threads, sb);
+    return a < b ? a : b;
+}
+
+// Raises the dynamic shared-memory limit of the round kernels (once per
+// process and device).
+cudaError_t round_kernels_init() {
+    cudaError_t e = cudaSuccess;
+    const int rb = (int)relax_smem_bytes(), cb = (int)cupdate_smem_bytes();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_relax<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rb);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_relax<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rb);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cupdate<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cb);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cupdate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cb);
+    const int sb = (int)solve_smem_bytes();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+    return e;
 }
 
 cudaError_t launch_start(bool multi, const RoundParams& P, u32 first, u32 count, u32 max_rounds,
@@ -772,11 +1041,13 @@ cudaError_t launch_start(bool multi, const RoundParams& P, u32 first, u32 count,
 }
 
 int round_blocks_per_sm(int threads) {
+    if (round_kernels_init() != cudaSuccess) return 1;
     int a = 0, b = 0, c = 0, d = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cupdate<false>, threads, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_relax<false>, threads, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_cupdate<true>, threads, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_relax<true>, threads, 0);
+    const size_t rb = relax_smem_bytes(), cb = cupdate_smem_bytes();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cupdate<false>, threads, cb);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_relax<false>, threads, rb);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_cupdate<true>, threads, cb);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_relax<true>, threads, rb);
     int m = a < b ? a : b;
     m = m < c ? m : c;
     m = m < d ? m : d;

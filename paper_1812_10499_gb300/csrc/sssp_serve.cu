@@ -16,12 +16,6 @@
 #include "sssp_engine.h"
 
 namespace sssp {
-__global__ void k_init_records_multi(RoundParams P, u64 nrec, u32 first_page, u32 npages);
-__global__ void k_reset_ctl(Ctl* ctl, u32 ninst, u32 round_limit);
-__global__ void k_finalize(const VRec* rec, u64 base, u32 n, u32 vbits, const InstVar* iv,
-                           u64* dist, u32* parent, int* fround, u64* lower);
-cudaError_t launch_start(bool multi, const RoundParams& P, u32 first, u32 count, u32 max_rounds,
-                         cudaStream_t st);
 }  // namespace sssp
 
 using namespace sssp;
@@ -82,8 +76,10 @@ int open_impl(sssp_server* s) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     c.grid = std::max(1, sms) * std::max(1, round_blocks_per_sm(kThreads));
+    c.grid_solve = std::max(1, sms) * std::max(1, solve_blocks_per_sm(kThreads));
     RoundParams& P = c.P;
     RC(c.pool.get(&P.rec, nrec));
+    RC(c.pool.get(&P.fround, nrec));
     RC(c.pool.get(&P.ctl, 1));
     RC(c.pool.get(&P.ivar, c.nslots));
     InstDesc* idesc = nullptr;
@@ -172,6 +168,7 @@ int retire(sssp_server* s) {
     CK(cudaMemcpyAsync(c.h_ivar, c.P.ivar, sizeof(InstVar) * c.nslots, cudaMemcpyDeviceToHost,
                        s->stream));
     CK(cudaStreamSynchronize(s->stream));
+    if (c.h_ctl->error & 4u) return SSSP_E_DEVICE_TIMEOUT;
     if (c.h_ctl->error) return SSSP_E_INTERNAL;
     if (c.h_ctl->status == kErrRounds) return SSSP_E_ROUND_LIMIT;
     s->round_host = c.h_ctl->round;
@@ -180,7 +177,8 @@ int retire(sssp_server* s) {
         Query* q = s->slot_query[slot];
         if (!q || c.h_ivar[slot].status != kDone) continue;
         const u64 base = (u64)q->first_page << kPageShift;
-        k_finalize<<<c.grid, kThreads, 0, s->stream>>>(c.P.rec, base, q->g->n, c.P.vbits,
+        k_finalize<<<c.grid, kThreads, 0, s->stream>>>(c.P.rec, c.P.fround, base, q->g->n,
+                                                       c.P.vbits,
                                                        c.P.ivar + slot, c.stage + base, nullptr,
                                                        nullptr, nullptr);
         CK(cudaGetLastError());
@@ -210,7 +208,7 @@ int step(sssp_server* s) {
     *s->h_stop = s->round_host + k - 1;
     CK(cudaMemcpyAsync(&c.P.ctl->stop_round, s->h_stop, sizeof(u32), cudaMemcpyHostToDevice,
                        s->stream));
-    RC(run_loop(c, SSSP_LOOP_GRAPH, s->stream));
+    RC(run_loop(c, SSSP_LOOP_PERSISTENT, s->stream));
     return retire(s);
 }
 

@@ -13,7 +13,7 @@ __device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
 // ------------------------------------------------------- start / finalize
 
 // Every record of a single query: D = inf, C = 0 (Fig. SP_4 declarations).
-__global__ void k_init_records(VRec* rec, const u32* outw, u32 n) {
+__global__ void k_init_records(VRec* rec, int* fround, const u32* outw, const u64* in_off, u32 n) {
     for (u64 v = blockIdx.x * (u64)blockDim.x + threadIdx.x; v < n;
          v += (u64)gridDim.x * blockDim.x) {
         VRec r;
@@ -21,8 +21,9 @@ __global__ void k_init_records(VRec* rec, const u32* outw, u32 n) {
         r.cf[0] = 0;
         r.cf[1] = 0;
         r.outw = outw[v];
-        r.fround = -1;
+        r.indeg = (u32)(in_off[v + 1] - in_off[v]);
         rec[v] = r;
+        fround[v] = -1;
     }
 }
 
@@ -42,8 +43,9 @@ __global__ void k_init_records_multi(RoundParams P, u64 nrec, u32 first_page, u3
         r.cf[0] = 0;
         r.cf[1] = 0;
         r.outw = d.outw[v];
-        r.fround = -1;
+        r.indeg = (u32)(d.in_off[v + 1] - d.in_off[v]);
         P.rec[g] = r;
+        P.fround[g] = -1;
     }
 }
 
@@ -63,8 +65,8 @@ __global__ void k_reset_ctl(Ctl* ctl, u32 ninst, u32 round_limit) {
 // Output of one query (Sec. I: cost[x]; parents as in Sec. I's remark on
 // backward parent pointers).
 // The lower bounds after the query's last round r sit in cf[(r + 1) & 1].
-__global__ void k_finalize(const VRec* rec, u64 base, u32 n, u32 vbits, const InstVar* iv,
-                           u64* dist, u32* parent, int* fround, u64* lower) {
+__global__ void k_finalize(const VRec* rec, const int* frec, u64 base, u32 n, u32 vbits,
+                           const InstVar* iv, u64* dist, u32* parent, int* fround, u64* lower) {
     const u64 vmask = (vbits >= 64) ? ~0ull : ((1ull << vbits) - 1);
     const u32 cslot = (iv->start_round + iv->rounds) & 1u;
     for (u64 v = blockIdx.x * (u64)blockDim.x + threadIdx.x; v < n;
@@ -73,7 +75,7 @@ __global__ void k_finalize(const VRec* rec, u64 base, u32 n, u32 vbits, const In
         const bool reach = r.dp != kInf64;
         if (dist) dist[v] = reach ? (r.dp >> vbits) : kInf64;
         if (parent) parent[v] = reach ? (u32)(r.dp & vmask) : kFull;
-        if (fround) fround[v] = r.fround;
+        if (fround) fround[v] = frec[base + v];
         if (lower) lower[v] = r.cf[cslot] & kCMask;
     }
 }

@@ -69,6 +69,17 @@ def test_random_4096_config(sssp_lib):
     assert_parity(sssp_lib, g, 0)
     assert_parity(sssp_lib, g, 0, mode=oracle.RULE_MIND)
     assert_parity(sssp_lib, g, 0, loop_mode=sssp_lib.SSSP_LOOP_HOST)
+    assert_parity(sssp_lib, g, 0, loop_mode=sssp_lib.SSSP_LOOP_GRAPH)
+    assert_parity(sssp_lib, g, 0, loop_mode=sssp_lib.SSSP_LOOP_PERSISTENT)
+
+
+@pytest.mark.parametrize("mode", ["graph", "host"])
+def test_loop_modes_rmat(sssp_lib, mode):
+    """The three ways of sequencing rounds give identical results."""
+    g = gg.rmat(14, 16, 1, 255, 31)
+    s = int(np.argmax(g.out_degree()))
+    lm = sssp_lib.SSSP_LOOP_GRAPH if mode == "graph" else sssp_lib.SSSP_LOOP_HOST
+    assert_parity(sssp_lib, g, s, loop_mode=lm, hub_degree=16, chunk_edges=64)
 
 
 @pytest.mark.parametrize("seed", range(6))
