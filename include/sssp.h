@@ -50,6 +50,7 @@ extern "C" {
 #define SSSP_E_BUSY            (-9)  /* server has no free slot / budget for this query      */
 #define SSSP_E_NOT_FOUND      (-10)  /* unknown ticket                                      */
 #define SSSP_E_INTERNAL       (-11)  /* a device-side consistency guard tripped (library bug) */
+#define SSSP_E_NOALLOC_LIMIT  (-12)  /* graph larger than the fixed scratch of sssp_solve_noalloc */
 #define SSSP_PENDING            1    /* sssp_serve_poll: query still running                 */
 
 #define SSSP_DIST_INF UINT64_MAX
@@ -246,6 +247,41 @@ int sssp_profile(sssp_handle h, int enable, sssp_kernel_profile* out);
  * Errors: SSSP_E_INVAL. */
 int sssp_profile_rounds(sssp_handle h, float* relax_ms, float* cupdate_ms, uint32_t cap,
                         uint32_t* count);
+
+/* Single-source solve that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * when they solve -- code running inside another framework's memory pool
+ * (which owns all device memory), services whose memory budget is fixed at
+ * start-up, and latency-critical loops in which a cudaMalloc / cudaFree
+ * would synchronise the device.  The caller passes the graph and the output
+ * in its own device memory; all working state lives in one fixed scratch
+ * array inside the library image (about SSSP_NOALLOC_MAX_VERTICES * 100
+ * bytes), which every GPU that loads the library holds until the process
+ * exits.  No cudaMalloc, cudaFree or other allocating routine is called.
+ *   n          vertices, 1 <= n <= SSSP_NOALLOC_MAX_VERTICES; larger graphs
+ *              get SSSP_E_NOALLOC_LIMIT
+ *   out_off    device u64[n+1]: out-edges of u are entries out_off[u] ..
+ *              out_off[u+1]-1 of out_adj
+ *   out_adj    device u32[2m]: (target, weight) pairs
+ *   in_off, in_adj: the same edges by target: (source, weight) pairs
+ *   The graph must be loop-free with weights > 0 and ids < n (not checked:
+ *   it is never copied to the host).
+ *   max_weight the largest weight (for the SSSP_E_OVERFLOW check)
+ *   dist_dev   device u64[n] output, as sssp_solve
+ *   rounds_out host u32 (nullable)
+ *   cuda_stream the stream for the work (NULL = legacy default stream)
+ * The call returns after the stream has finished the solve.  The first call
+ * on a device sets up that device (looks up the scratch's device address and
+ * the kernels' launch limits); make that first call before any stream
+ * capture.  Every call shares the scratch and leaves its contents behind
+ * (each call clears what it needs), so calls that overlap on the GPU -- from
+ * several host threads or streams -- race and must be serialised by the
+ * caller. */
+#define SSSP_NOALLOC_MAX_VERTICES 131072u
+int sssp_solve_noalloc(uint32_t n, const uint64_t* out_off, const uint32_t* out_adj,
+                       const uint64_t* in_off, const uint32_t* in_adj, uint32_t source,
+                       uint32_t max_weight, uint64_t* dist_dev, uint32_t* rounds_out,
+                       void* cuda_stream);
 
 /* Releases a graph and its device memory.  NULL is ignored. */
 void sssp_destroy(sssp_handle h);

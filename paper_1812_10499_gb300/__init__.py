@@ -112,6 +112,8 @@ def load(path: str = LIB_PATH):
         "sssp_serve_close": (None, [vp]),
         "sssp_profile": (c_int, [vp, c_int, ctypes.POINTER(sssp_kernel_profile)]),
         "sssp_profile_rounds": (c_int, [vp, vp, vp, u32, ctypes.POINTER(u32)]),
+        "sssp_solve_noalloc": (c_int, [u32, vp, vp, vp, vp, u32, u32, vp,
+                                       ctypes.POINTER(u32), vp]),
         "sssp_destroy": (None, [vp]),
         "sssp_strerror": (ctypes.c_char_p, [c_int]),
         "sssp_num_vertices": (u32, [vp]),
@@ -229,6 +231,20 @@ def sssp_profile_rounds(h: int):
     _check(lib.sssp_profile_rounds(h, r.ctypes.data, c.ctypes.data, cnt.value,
                                    ctypes.byref(cnt)), "sssp_profile_rounds")
     return r, c
+
+
+def sssp_solve_noalloc(n: int, out_off, out_adj, in_off, in_adj, source: int, max_weight: int,
+                       dist_dev, stream=None) -> int:
+    """Solve for callers that cannot allocate device memory: the graph
+    (out_off u64[n+1], out_adj (target, weight) u32 pairs, and the same by
+    target) and dist_dev are the caller's CUDA tensors; the library uses only
+    its fixed scratch.  Returns the round count."""
+    r = ctypes.c_uint32(0)
+    _check(load().sssp_solve_noalloc(n, _ptr(out_off), _ptr(out_adj), _ptr(in_off),
+                                     _ptr(in_adj), source, max_weight, _ptr(dist_dev),
+                                     ctypes.byref(r), _stream_ptr(stream)),
+           "sssp_solve_noalloc")
+    return int(r.value)
 
 
 def sssp_num_vertices(h: int) -> int:

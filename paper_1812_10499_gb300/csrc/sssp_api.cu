@@ -827,6 +827,9 @@ const char* sssp_strerror(int code) {
         case SSSP_E_BUSY: return "server busy";
         case SSSP_E_NOT_FOUND: return "unknown ticket";
         case SSSP_E_INTERNAL: return "internal consistency guard tripped";
+        case SSSP_E_NOALLOC_LIMIT:
+            return "graph exceeds the fixed scratch of sssp_solve_noalloc "
+                   "(SSSP_NOALLOC_MAX_VERTICES vertices)";
         default: return "unknown status";
     }
 }
