@@ -162,6 +162,19 @@ def alg_bytes(info):
     return relax, cup
 
 
+def reduce_over_ranks(dist, device, local_ms, local_units):
+    """Replicas only: every rank times its own queries.  Returns (slowest
+    rank's time, units summed over ranks); `dist` None means one process."""
+    if dist is None:
+        return local_ms, local_units
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ------------------------------------------------------------- CPU oracle
 
 def cpu_oracle_gteps(g, sources, budget_s):
@@ -231,11 +244,8 @@ def run_ours(args):
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * args.steps * m_reach / (ms * 1e-3) / 1e9
+    ms, edges = reduce_over_ranks(dist, "cuda", ms, args.steps * m_reach)
+    value = edges / (ms * 1e-3) / 1e9
     launches = args.steps * sum((5 if args.loop == "persistent" else 4 + 2 * r) for r in rounds)
 
     # ---- dominant kernel: launch durations with CUDA events on the solve stream
@@ -295,11 +305,8 @@ def run_ours(args):
         for s in sources:
             host_out[0], _ = P.sssp_solve(h, s)
     t_e2e = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = ws * e2e_steps * m_reach / t_e2e / 1e9
+    ms_e2e, edges_e2e = reduce_over_ranks(dist, "cuda", t_e2e * 1e3, e2e_steps * m_reach)
+    e2e = edges_e2e / (ms_e2e * 1e-3) / 1e9
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -338,6 +345,193 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------- batched / served queries
+
+def batch_graphs(count, seed, nmin=1024, nmax=262144):
+    """Independent graphs: n log-uniform in [nmin, nmax], out-degree U{4..16},
+    w ~ U[1,1000], one seeded source each."""
+    import graphgen as gg
+    u = gg.unit(seed, 1, count)
+    ns = np.round(np.exp(np.log(nmin) + u * (np.log(nmax) - np.log(nmin)))).astype(int)
+    graphs = [gg.random_var_graph(int(n), 4, 16, 1, 1000, seed * 1000 + i)
+              for i, n in enumerate(ns)]
+    srcs = [int(gg.uniform(seed, 2 + i, 1, 0, g.n - 1)[0]) for i, g in enumerate(graphs)]
+    return graphs, srcs
+
+
+def run_batch(args):
+    """Queries/s of one lock-step batched launch against the plain loop of
+    one sssp_solve_device per query, same queries, results compared."""
+    import torch
+    import graphgen as gg
+    import paper_1812_10499_gb300 as P
+    P.load()
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    if args.config == "batch":
+        graphs, srcs = batch_graphs(args.batch_count, SEED + 3)
+        hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w) for g in graphs]
+        ns = [g.n for g in graphs]
+        desc = (f"{len(graphs)} independent graphs, n log-uniform in [1K, 256K], out-degree "
+                f"U{{4..16}}, w U[1,1000], one seeded source each")
+        m_total = sum(g.m for g in graphs)
+    else:
+        g = gg.rmat(18, 16, 1, 255, SEED + 3)
+        cand = np.flatnonzero(g.out_degree() > 0)
+        srcs = [int(cand[int(i)]) for i in gg.uniform(SEED + 3, 9, 64, 0, len(cand) - 1)]
+        h = P.sssp_create(g.n, g.row_ptr, g.col, g.w)
+        hs = [h] * len(srcs)
+        ns = [g.n] * len(srcs)
+        graphs = [g]
+        desc = "64 seeded sources on one R-MAT scale 18 graph (edge factor 16, w U[1,255])"
+        m_total = g.m
+    log(f"batch workload: {len(hs)} queries, {sum(ns)} vertices, setup {time.time() - t0:.1f}s")
+    outs_a = [torch.empty(n, dtype=torch.int64, device="cuda") for n in ns]
+    outs_b = [torch.empty(n, dtype=torch.int64, device="cuda") for n in ns]
+    st = torch.cuda.Stream()
+
+    def plain():
+        for h, s, o in zip(hs, srcs, outs_a):
+            P.sssp_solve_device(h, s, o, stream=st)
+
+    def batched():
+        return P.sssp_solve_batch_device(hs, srcs, outs_b, stream=st)
+
+    for _ in range(args.warmup):
+        plain()
+        batched()
+    st.synchronize()
+    same = all(torch.equal(a, b) for a, b in zip(outs_a, outs_b))
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    clocks = Clocks(0)
+    clocks.start()
+    ms_b = timed(batched)
+    ms_p = timed(plain)
+    clk = clocks.stop()
+    q = len(hs) * args.steps
+    line = {
+        "metric": "batched SSSP queries/s vs the plain per-query loop", "value": q / (ms_b * 1e-3),
+        "unit": "queries/s", "plain_value": q / (ms_p * 1e-3), "speedup": ms_p / ms_b,
+        "identical_results": bool(same), "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_b / args.steps,
+        "plain_ms_per_step": ms_p / args.steps, "higher_is_better": True, "dtype": "u64",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": desc, "queries": len(hs), "vertices": int(sum(ns)),
+                   "edges": int(m_total)},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    for h in set(hs):
+        P.sssp_destroy(h)
+
+
+def run_serve(args):
+    """Continuous batching under Poisson arrivals.  Queries on graphs of the
+    batched distribution plus 10% on R-MAT scale 20 graphs; the server admits
+    them into free slots as memory allows while others run.  For each arrival
+    rate (multiples of the plain loop's measured capacity) it reports
+    queries/s and p50/p99 latency (completion minus scheduled arrival) for the
+    server and for the plain FIFO loop of one solve at a time."""
+    import torch
+    import graphgen as gg
+    import paper_1812_10499_gb300 as P
+    P.load()
+    torch.cuda.set_device(0)
+    pool, _ = batch_graphs(args.serve_pool, SEED + 4)
+    pool += [gg.rmat(20, 16, 1, 255, SEED + 4 + i) for i in range(2)]
+    hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w) for g in pool]
+    nq = args.serve_queries
+    pick = gg.unit(SEED + 4, 3, nq)
+    which = [len(pool) - 1 - int(p * 20) % 2 if p < 0.1 else int(p * 1e6) % (len(pool) - 2)
+             for p in pick]
+    srcs = [int(gg.uniform(SEED + 4, 10 + i, 1, 0, pool[w].n - 1)[0]) for i, w in enumerate(which)]
+    outs = [np.empty(pool[w].n, dtype=np.uint64) for w in which]
+    st = torch.cuda.Stream()
+    dd = torch.empty(max(g.n for g in pool), dtype=torch.int64, device="cuda")
+    # plain capacity: one solve at a time
+    for i in range(min(nq, 20)):
+        P.sssp_solve_device(hs[which[i]], srcs[i], dd, stream=st)
+    st.synchronize()
+    t0 = time.perf_counter()
+    for i in range(nq):
+        P.sssp_solve_device(hs[which[i]], srcs[i], dd, stream=st)
+    st.synchronize()
+    service = (time.perf_counter() - t0) / nq
+    capacity = 1.0 / service
+    results = []
+    for mult in args.serve_rates:
+        lam = mult * capacity
+        gaps = -np.log(1.0 - gg.unit(SEED + 4, 4 + int(mult * 100), nq)) / lam
+        arrive = np.cumsum(gaps)
+        # plain FIFO loop
+        lat_p = []
+        t_start = time.perf_counter()
+        for i in range(nq):
+            while time.perf_counter() - t_start < arrive[i]:
+                pass
+            P.sssp_solve_device(hs[which[i]], srcs[i], dd, stream=st)
+            st.synchronize()
+            lat_p.append(time.perf_counter() - t_start - arrive[i])
+        span_p = time.perf_counter() - t_start
+        # served
+        server = P.sssp_serve_open(budget_bytes=32 << 30, max_slots=1024,
+                                   rounds_per_step=args.serve_rounds)
+        lat_s = [None] * nq
+        tickets = {}
+        nxt = 0
+        t_start = time.perf_counter()
+        while nxt < nq or tickets:
+            now = time.perf_counter() - t_start
+            while nxt < nq and arrive[nxt] <= now:
+                tickets[nxt] = P.sssp_serve_submit(server, hs[which[nxt]], srcs[nxt], outs[nxt])
+                nxt += 1
+            if not tickets:
+                continue
+            for i in sorted(tickets):
+                stt, _ = P.sssp_serve_poll(server, tickets[i])
+                if stt == P.SSSP_OK:
+                    lat_s[i] = time.perf_counter() - t_start - arrive[i]
+                    del tickets[i]
+                else:
+                    break
+        span_s = time.perf_counter() - t_start
+        P.sssp_serve_close(server)
+        ok = True
+        for i in range(0, nq, max(1, nq // 16)):
+            ref, _ = P.sssp_solve(hs[which[i]], srcs[i])
+            ok = ok and np.array_equal(ref, outs[i])
+        results.append({
+            "rate_x_capacity": mult, "arrival_qps": lam,
+            "served_qps": nq / span_s, "served_p50_ms": 1e3 * float(np.percentile(lat_s, 50)),
+            "served_p99_ms": 1e3 * float(np.percentile(lat_s, 99)),
+            "plain_qps": nq / span_p, "plain_p50_ms": 1e3 * float(np.percentile(lat_p, 50)),
+            "plain_p99_ms": 1e3 * float(np.percentile(lat_p, 99)), "results_match_alone": ok})
+    best = max(results, key=lambda r: r["served_qps"])
+    line = {
+        "metric": "served SSSP queries/s and p50/p99 latency vs the plain loop",
+        "value": best["served_qps"], "unit": "queries/s", "n_gpus": 1,
+        "plain_capacity_qps": capacity, "higher_is_better": True, "dtype": "u64",
+        "data": "synthetic (seeded generator), Poisson arrivals",
+        "config": {"workload": f"{nq} queries: 90% on {len(pool) - 2} graphs of the batched "
+                               f"distribution, 10% on 2 R-MAT scale 20 graphs; 32 GiB budget, "
+                               f"{args.serve_rounds} rounds per server step"},
+        "rates": results,
+    }
+    print(json.dumps(line), flush=True)
+    for h in hs:
+        P.sssp_destroy(h)
 
 
 # ------------------------------------------------------ reference arm
@@ -396,12 +590,21 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=150.0)
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--serve-pool", type=int, default=48)
+    ap.add_argument("--serve-queries", type=int, default=400)
+    ap.add_argument("--serve-rounds", type=int, default=8)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 1.0, 2.0, 4.0])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         log("warmup raised to 3 (timing rule)")
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.config in ("batch", "msrc"):
+        run_batch(args)
+    elif args.config == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 
