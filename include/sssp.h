@@ -74,6 +74,18 @@ extern "C" {
                                     separated by grid barriers whose waits time out
                                     (SSSP_E_DEVICE_TIMEOUT) instead of hanging            */
 
+/* Per-vertex state layout of the round kernels.  Results are identical.
+ *   SSSP_LAYOUT_AUTO     compact when n * max weight < 2^31, else wide (default)
+ *   SSSP_LAYOUT_WIDE     32-byte records: packed D, two C words, outWeight and
+ *                        in-degree of the vertex
+ *   SSSP_LAYOUT_COMPACT  16-byte records: packed D and two 31-bit C words;
+ *                        outWeight and in-degree are read from the graph.
+ *                        sssp_create fails with SSSP_E_OVERFLOW when
+ *                        n * max weight >= 2^31. */
+#define SSSP_LAYOUT_AUTO    0u
+#define SSSP_LAYOUT_WIDE    1u
+#define SSSP_LAYOUT_COMPACT 2u
+
 typedef struct sssp_graph* sssp_handle;
 typedef struct sssp_server sssp_server;
 
@@ -94,7 +106,8 @@ typedef struct sssp_options {
     uint32_t block_threads;  /* threads per CTA of the round kernels (0 = 256)             */
     uint32_t ctas_per_sm;    /* CTAs per SM of the round kernels (0 = from occupancy)      */
     int32_t device;          /* CUDA device ordinal (-1 = the calling thread's current)    */
-    uint32_t reserved;
+    uint32_t layout;         /* SSSP_LAYOUT_* (batched solves use the compact layout only
+                                when every graph of the batch does)                        */
     sssp_alloc_fn alloc;     /* NULL = cudaMalloc                                          */
     sssp_free_fn free;       /* NULL = cudaFree                                            */
     void* alloc_ctx;
@@ -292,6 +305,10 @@ const char* sssp_strerror(int code);
 /* Number of vertices / edges (after self-loop removal) of a handle. */
 uint32_t sssp_num_vertices(sssp_handle h);
 uint64_t sssp_num_edges(sssp_handle h);
+
+/* State layout the handle's single-query solves run with:
+ * SSSP_LAYOUT_WIDE or SSSP_LAYOUT_COMPACT (0 for a NULL handle). */
+uint32_t sssp_layout(sssp_handle h);
 
 #ifdef __cplusplus
 }

@@ -27,6 +27,9 @@ SSSP_RULE_MIND = 1
 SSSP_LOOP_GRAPH = 0
 SSSP_LOOP_HOST = 1
 SSSP_LOOP_PERSISTENT = 2
+SSSP_LAYOUT_AUTO = 0
+SSSP_LAYOUT_WIDE = 1
+SSSP_LAYOUT_COMPACT = 2
 SSSP_DIST_INF = 0xFFFFFFFFFFFFFFFF
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -37,7 +40,7 @@ class sssp_options(ctypes.Structure):
     _fields_ = [("rule", ctypes.c_uint32), ("loop_mode", ctypes.c_uint32),
                 ("hub_degree", ctypes.c_uint32), ("chunk_edges", ctypes.c_uint32),
                 ("block_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("device", ctypes.c_int32), ("reserved", ctypes.c_uint32),
+                ("device", ctypes.c_int32), ("layout", ctypes.c_uint32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
 
 
@@ -118,6 +121,7 @@ def load(path: str = LIB_PATH):
         "sssp_strerror": (ctypes.c_char_p, [c_int]),
         "sssp_num_vertices": (u32, [vp]),
         "sssp_num_edges": (u64, [vp]),
+        "sssp_layout": (u32, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -253,6 +257,11 @@ def sssp_num_vertices(h: int) -> int:
 
 def sssp_num_edges(h: int) -> int:
     return load().sssp_num_edges(h)
+
+
+def sssp_layout(h: int) -> int:
+    """SSSP_LAYOUT_WIDE or SSSP_LAYOUT_COMPACT: the handle's state layout."""
+    return load().sssp_layout(h)
 
 
 def sssp_solve(h: int, source: int):

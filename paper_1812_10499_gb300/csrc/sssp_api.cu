@@ -67,16 +67,16 @@ int build_loop(Context& c) {
     P.cond = h;
     void* args[] = {&P};
     cudaKernelNodeParams kp{};
-    kp.func = const_cast<void*>(relax_fn(c.multi));
+    kp.func = const_cast<void*>(relax_fn(c.multi, c.narrow));
     kp.gridDim = dim3(c.grid);
     kp.blockDim = dim3(kThreads);
-    kp.sharedMemBytes = (unsigned)relax_smem_bytes();
+    kp.sharedMemBytes = (unsigned)relax_smem_bytes(c.narrow);
     kp.kernelParams = args;
     cudaGraphNode_t n1, n2;
     e = cudaGraphAddKernelNode(&n1, body, nullptr, 0, &kp);
     if (e == cudaSuccess) {
-        kp.func = const_cast<void*>(cupdate_fn(c.multi));
-        kp.sharedMemBytes = (unsigned)cupdate_smem_bytes();
+        kp.func = const_cast<void*>(cupdate_fn(c.multi, c.narrow));
+        kp.sharedMemBytes = (unsigned)cupdate_smem_bytes(c.narrow);
         e = cudaGraphAddKernelNode(&n2, body, &n1, 1, &kp);
     }
     cudaGraphExec_t x = nullptr;
@@ -109,8 +109,8 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
             P.trace_base = c.h_ctl->round;
         }
         void* args[] = {&P};
-        CK(cudaLaunchCooperativeKernel(solve_fn(c.multi), dim3(c.grid_solve), dim3(kThreads), args,
-                                       solve_smem_bytes(), st));
+        CK(cudaLaunchCooperativeKernel(solve_fn(c.multi, c.narrow), dim3(c.grid_solve),
+                                       dim3(kThreads), args, solve_smem_bytes(c.narrow), st));
         if (c.prof) {
             CK(cudaMemcpyAsync(c.h_ctl, c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
@@ -141,8 +141,9 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
     // profiling, events bracket every launch: ev[3i] | relax | ev[3i+1] |
     // cupdate | ev[3i+2].
     constexpr int kGroup = 16;
-    const void* fr = relax_fn(c.multi);
-    const void* fc = cupdate_fn(c.multi);
+    const void* fr = relax_fn(c.multi, c.narrow);
+    const void* fc = cupdate_fn(c.multi, c.narrow);
+    const size_t smr = relax_smem_bytes(c.narrow), smc = cupdate_smem_bytes(c.narrow);
     RoundParams P = c.P;
     P.cond = 0;
     void* args[] = {&P};
@@ -160,9 +161,9 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
     for (;;) {
         for (int i = 0; i < kGroup; ++i) {
             if (c.prof) CK(cudaEventRecord(c.ev[3 * i], st));
-            CK(cudaLaunchKernel(fr, dim3(c.grid), dim3(kThreads), args, relax_smem_bytes(), st));
+            CK(cudaLaunchKernel(fr, dim3(c.grid), dim3(kThreads), args, smr, st));
             if (c.prof) CK(cudaEventRecord(c.ev[3 * i + 1], st));
-            CK(cudaLaunchKernel(fc, dim3(c.grid), dim3(kThreads), args, cupdate_smem_bytes(), st));
+            CK(cudaLaunchKernel(fc, dim3(c.grid), dim3(kThreads), args, smc, st));
             if (c.prof) CK(cudaEventRecord(c.ev[3 * i + 2], st));
         }
         CK(cudaMemcpyAsync(c.h_ctl, c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -226,7 +227,9 @@ int init_single_context(sssp_graph* h) {
     P.g.base = 0;
     P.g.n = h->n;
     P.g.source = 0;
-    RC(c.pool.get(&P.rec, h->n));
+    c.narrow = h->narrow;
+    if (c.narrow) RC(c.pool.get(&P.recn, h->n));
+    else RC(c.pool.get(&P.rec, h->n));
     RC(c.pool.get(&P.fround, h->n));
     RC(c.pool.get(&P.ctl, 1));
     RC(c.pool.get(&P.ivar, 1));
@@ -329,6 +332,11 @@ int create_impl(sssp_graph* h, u32 n, u64 m, const u64* row_ptr, const u32* col,
     // below n * wmax; it must stay below the infinity of the packed word.
     if (wmax && (unsigned __int128)n * wmax >= (unsigned __int128)h->dinf) return SSSP_E_OVERFLOW;
     h->wmax = wmax;
+    // Compact records hold 31-bit lower bounds: every finite distance
+    // (at most (n - 1) * wmax) must stay below 2^31 - 1.
+    const bool fits = (unsigned __int128)n * wmax < kNarrowLimit;
+    if (h->opt.layout == SSSP_LAYOUT_COMPACT && !fits) return SSSP_E_OVERFLOW;
+    h->narrow = fits && h->opt.layout != SSSP_LAYOUT_WIDE;
 
     std::vector<u64> o2, c2;
     std::vector<u32> i2, w2, r2, wi2;
@@ -448,6 +456,7 @@ int read_status(Context& c, cudaStream_t st, u32 ninst) {
     CK(cudaMemcpyAsync(c.h_ivar, c.P.ivar, sizeof(InstVar) * ninst, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (c.h_ctl->error & 4u) return SSSP_E_DEVICE_TIMEOUT;
+    if (c.h_ctl->error & 8u) return SSSP_E_OVERFLOW;
     if (c.h_ctl->error) return SSSP_E_INTERNAL;
     if (c.h_ctl->status == kErrRounds) return SSSP_E_ROUND_LIMIT;
     return SSSP_OK;
@@ -460,11 +469,12 @@ int enqueue_single(sssp_graph* h, u32 source, u32 max_rounds, cudaStream_t st, u
     RoundParams P = c.P;
     P.g.source = source;
     c.P.g.source = source;
-    k_init_records<<<c.grid, kThreads, 0, st>>>(P.rec, P.fround, h->outw, h->in_off, h->n);
+    k_init_records<<<c.grid, kThreads, 0, st>>>(P.rec, P.recn, P.fround, h->outw, h->in_off, h->n);
     k_reset_ctl<<<1, 32, 0, st>>>(P.ctl, 1, h->n + 2);
-    CK(launch_start(false, P, 0, 1, max_rounds, st));
+    CK(launch_start(false, c.narrow, P, 0, 1, max_rounds, st));
     RC(run_loop(c, h->opt.loop_mode, st));
-    k_finalize<<<c.grid, kThreads, 0, st>>>(P.rec, P.fround, 0, h->n, h->vbits, P.ivar, dist_dev,
+    k_finalize<<<c.grid, kThreads, 0, st>>>(P.rec, P.recn, P.fround, 0, h->n, h->vbits, P.ivar,
+                                            dist_dev,
                                             parent_dev, fround_dev, lower_dev);
     CK(cudaGetLastError());
     return SSSP_OK;
@@ -492,7 +502,7 @@ int ensure_batch(sssp_graph* h0, u64 nrec, u32 nslots, u32 npages, u64 capH) {
     c->grid = h0->grid;
     c->grid_solve = h0->grid_solve;
     RoundParams& P = c->P;
-    RC(c->pool.get(&P.rec, nrec));
+    RC(c->pool.get(&c->rec_store, nrec));   // 32-byte slots; the compact layout uses half
     RC(c->pool.get(&P.fround, nrec));
     RC(c->pool.get(&P.ctl, 1));
     RC(c->pool.get(&P.ivar, nslots));
@@ -523,6 +533,7 @@ int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist
     sssp_graph* h0 = g[0];
     if (!h0) return SSSP_E_INVAL;
     u32 vbits = 1;
+    bool narrow = true;
     u64 npages = 0, capH = 0;
     for (u32 i = 0; i < k; ++i) {
         if (!g[i] || !dist[i]) return SSSP_E_INVAL;
@@ -531,6 +542,7 @@ int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist
             return SSSP_E_INVAL;
         if (sources[i] >= g[i]->n) return SSSP_E_SOURCE_RANGE;
         vbits = std::max(vbits, g[i]->vbits);
+        narrow = narrow && g[i]->narrow;
         npages += ((u64)g[i]->n + (1u << kPageShift) - 1) >> kPageShift;
         capH += std::max(g[i]->hubs_in, g[i]->hubs_out);
     }
@@ -547,7 +559,7 @@ int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist
     cudaStream_t st = use_user_stream ? st_user : h0->stream;
     RoundParams& P = c.P;
     // The loop graph bakes the params in; rebuild it when they change.
-    if (c.exec && P.vbits != vbits) {
+    if (c.exec && (P.vbits != vbits || c.narrow != narrow)) {
         cudaGraphExecDestroy(c.exec);
         cudaGraphDestroy(c.graph);
         c.exec = nullptr;
@@ -555,6 +567,9 @@ int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist
     }
     P.vbits = vbits;
     P.dinf = dinf;
+    c.narrow = narrow;
+    P.rec = narrow ? nullptr : c.rec_store;
+    P.recn = narrow ? reinterpret_cast<VRecN*>(c.rec_store) : nullptr;
     P.g = InstDesc{g[0]->out_off, g[0]->out_adj, g[0]->in_off, g[0]->in_adj, g[0]->outw, 0,
                    g[0]->n, sources[0]};
     u64 page = 0;
@@ -573,7 +588,7 @@ int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist
     for (u32 i = 0; i < k; ++i) max_n = std::max(max_n, g[i]->n);
     k_init_records_multi<<<c.grid, kThreads, 0, st>>>(P, nrec, 0, (u32)npages);
     k_reset_ctl<<<1, 32, 0, st>>>(P.ctl, k, max_n + 2);
-    CK(launch_start(true, P, 0, k, 0, st));
+    CK(launch_start(true, c.narrow, P, 0, k, 0, st));
     RC(run_loop(c, h0->opt.loop_mode, st));
     k_finalize_multi<<<c.grid, kThreads, 0, st>>>(P, nrec, c.stage);
     CK(cudaGetLastError());
@@ -633,6 +648,7 @@ int sssp_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t*
     if (o.chunk_edges == 0) o.chunk_edges = kDefaultChunk;
     if (o.block_threads == 0) o.block_threads = kThreads;
     if (o.rule > SSSP_RULE_MIND || o.loop_mode > SSSP_LOOP_PERSISTENT || o.chunk_edges % 32 != 0 ||
+        o.layout > SSSP_LAYOUT_COMPACT ||
         o.hub_degree > (1u << 20) || o.chunk_edges > (1u << 20) ||
         o.block_threads != kThreads || (o.alloc == nullptr) != (o.free == nullptr))
         return SSSP_E_INVAL;
@@ -647,6 +663,8 @@ int sssp_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t*
         }
         const u32 vb = std::max<u32>(1, bits_for((u64)n - 1));
         if (wmax && (unsigned __int128)n * wmax >= (unsigned __int128)((~0ull) >> vb))
+            return SSSP_E_OVERFLOW;
+        if (o.layout == SSSP_LAYOUT_COMPACT && (unsigned __int128)n * wmax >= kNarrowLimit)
             return SSSP_E_OVERFLOW;
     }
     int dev = o.device;
@@ -686,6 +704,9 @@ void sssp_destroy(sssp_handle h) {
 
 uint32_t sssp_num_vertices(sssp_handle h) { return h ? h->n : 0; }
 uint64_t sssp_num_edges(sssp_handle h) { return h ? h->m : 0; }
+uint32_t sssp_layout(sssp_handle h) {
+    return h ? (h->narrow ? SSSP_LAYOUT_COMPACT : SSSP_LAYOUT_WIDE) : 0u;
+}
 
 int sssp_solve_ex(sssp_handle h, uint32_t source, const sssp_solve_args* args,
                   sssp_solve_info* info) {

@@ -33,6 +33,19 @@ struct __align__(32) VRec {
 };
 static_assert(sizeof(VRec) == 32, "VRec must be one 32-byte sector");
 
+// Compact record, used when every finite distance is below 2^31 (checked
+// from n * max weight when the graph is created): C words are 31-bit values
+// with the fixed flag in bit 31; outWeight and the in-degree are read from
+// the graph when needed.  Two records share a 32-byte sector, so the state
+// the gathers touch is half as large.
+struct __align__(16) VRecN {
+    u64 dp;        // packed upper bound D (atomicMin target)
+    u32 cf[2];     // lower bound C | kFixedN, double-buffered by round parity
+};
+static_assert(sizeof(VRecN) == 16, "VRecN must be 16 bytes");
+constexpr u32 kFixedN = 1u << 31;
+constexpr u64 kNarrowLimit = kFixedN - 1;   // distances must stay below this
+
 // Read-only description of one query's graph.
 struct InstDesc {
     const u64* out_off;     // CSR offsets, n + 1
@@ -98,7 +111,8 @@ struct RoundParams {
     const InstDesc* idesc;      // per-slot graphs (multi-query)
     InstVar* ivar;              // per-slot scalars
     const u32* page_owner;      // record page -> slot (multi-query)
-    VRec* rec;
+    VRec* rec;                  // wide records (or nullptr)
+    VRecN* recn;                // compact records (or nullptr)
     int* fround;                // per record: round in which it was fixed, -1 if never
     Ctl* ctl;
     Lists L;

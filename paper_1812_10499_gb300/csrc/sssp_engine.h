@@ -14,22 +14,25 @@
 #include "sssp_dev.cuh"
 
 namespace sssp {
-const void* relax_fn(bool multi);
-const void* cupdate_fn(bool multi);
-const void* solve_fn(bool multi);
-size_t solve_smem_bytes();
+// narrow: 16-byte records (RoundParams::recn) instead of 32-byte ones (rec).
+const void* relax_fn(bool multi, bool narrow);
+const void* cupdate_fn(bool multi, bool narrow);
+const void* solve_fn(bool multi, bool narrow);
+size_t solve_smem_bytes(bool narrow);
 int solve_blocks_per_sm(int threads);
-size_t relax_smem_bytes();
-size_t cupdate_smem_bytes();
+size_t relax_smem_bytes(bool narrow);
+size_t cupdate_smem_bytes(bool narrow);
 cudaError_t round_kernels_init();
-cudaError_t launch_start(bool multi, const RoundParams& P, u32 first, u32 count, u32 max_rounds,
-                         cudaStream_t st);
+cudaError_t launch_start(bool multi, bool narrow, const RoundParams& P, u32 first, u32 count,
+                         u32 max_rounds, cudaStream_t st);
 int round_blocks_per_sm(int threads);
-__global__ void k_init_records(VRec* rec, int* fround, const u32* outw, const u64* in_off, u32 n);
+__global__ void k_init_records(VRec* rec, VRecN* recn, int* fround, const u32* outw,
+                               const u64* in_off, u32 n);
 __global__ void k_init_records_multi(RoundParams P, u64 nrec, u32 first_page, u32 npages);
 __global__ void k_reset_ctl(Ctl* ctl, u32 ninst, u32 round_limit);
-__global__ void k_finalize(const VRec* rec, const int* frec, u64 base, u32 n, u32 vbits,
-                           const InstVar* iv, u64* dist, u32* parent, int* fround, u64* lower);
+__global__ void k_finalize(const VRec* rec, const VRecN* recn, const int* frec, u64 base, u32 n,
+                           u32 vbits, const InstVar* iv, u64* dist, u32* parent, int* fround,
+                           u64* lower);
 __global__ void k_finalize_multi(RoundParams P, u64 nrec, u64* dist);
 __global__ void k_interleave(const u32* col, const u32* w, u64 m, uint2* adj);
 __global__ void k_count_in(const uint2* adj, u64 m, u64* cnt);
@@ -128,11 +131,13 @@ inline u32 bits_for(u64 x) {
 struct Context {
     Pool pool;
     bool multi = false;
+    bool narrow = false;     // 16-byte records (P.recn) in use
     u64 nrec = 0;            // records
     u32 nslots = 0;          // query slots
     u32 npages = 0;
     u32 capH = 0;
     RoundParams P{};
+    VRec* rec_store = nullptr;  // record storage of a multi-query context (either layout)
     u64* stage = nullptr;    // device staging (distances)
     Ctl* h_ctl = nullptr;    // pinned
     InstVar* h_ivar = nullptr;
@@ -186,6 +191,7 @@ struct sssp_graph {
     u32 vbits = 1;
     u64 dinf = 0;
     u32 wmax = 0;
+    bool narrow = false;             // compact 16-byte records
     u32 hubs_out = 0, hubs_in = 0;
     sssp_options opt{};
     sssp::engine::Pool gpool;        // graph arrays

@@ -85,7 +85,10 @@ extern "C" int sssp_solve_noalloc(uint32_t n, const uint64_t* out_off, const uin
     // Lay the working state out in the scratch (no allocation).
     size_t off = 0;
     RoundParams P{};
-    P.rec = carve<VRec>(base, off, n);
+    // Compact 16-byte records when every finite distance fits 31 bits.
+    const bool narrow = (unsigned __int128)n * max_weight < kNarrowLimit;
+    if (narrow) P.recn = carve<VRecN>(base, off, n);
+    else P.rec = carve<VRec>(base, off, n);
     P.fround = carve<int>(base, off, n);
     u32* outw = carve<u32>(base, off, n);
     for (int i = 0; i < 2; ++i) {
@@ -116,14 +119,14 @@ extern "C" int sssp_solve_noalloc(uint32_t n, const uint64_t* out_off, const uin
     CK(cudaMemsetAsync(P.L.hubmin, 0xFF, sizeof(u64) * n, st));
     CK(cudaMemsetAsync(P.L.hubcnt, 0, sizeof(u32) * n, st));
     k_outw<<<grid, kThreads, 0, st>>>(P.g.out_off, P.g.out_adj, n, outw);
-    k_init_records<<<grid, kThreads, 0, st>>>(P.rec, P.fround, outw, P.g.in_off, n);
+    k_init_records<<<grid, kThreads, 0, st>>>(P.rec, P.recn, P.fround, outw, P.g.in_off, n);
     k_reset_ctl<<<1, 32, 0, st>>>(P.ctl, 1, n + 2);
     CK(cudaGetLastError());
-    CK(launch_start(false, P, 0, 1, 0, st));
+    CK(launch_start(false, narrow, P, 0, 1, 0, st));
     void* args[] = {&P};
-    CK(cudaLaunchCooperativeKernel(solve_fn(false), dim3(grid), dim3(kThreads), args,
-                                   solve_smem_bytes(), st));
-    k_finalize<<<grid, kThreads, 0, st>>>(P.rec, P.fround, 0, n, vbits, P.ivar,
+    CK(cudaLaunchCooperativeKernel(solve_fn(false, narrow), dim3(grid), dim3(kThreads), args,
+                                   solve_smem_bytes(narrow), st));
+    k_finalize<<<grid, kThreads, 0, st>>>(P.rec, P.recn, P.fround, 0, n, vbits, P.ivar,
                                           reinterpret_cast<u64*>(dist_dev), nullptr, nullptr,
                                           nullptr);
     CK(cudaGetLastError());
@@ -134,6 +137,7 @@ extern "C" int sssp_solve_noalloc(uint32_t n, const uint64_t* out_off, const uin
     CK(cudaMemcpyAsync(&hv, P.ivar, sizeof(InstVar), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (hc.error & 4u) return SSSP_E_DEVICE_TIMEOUT;
+    if (hc.error & 8u) return SSSP_E_OVERFLOW;   // a weight above max_weight
     if (hc.error) return SSSP_E_INTERNAL;
     if (hv.status != kDone) return SSSP_E_ROUND_LIMIT;
     if (rounds_out) *rounds_out = hv.rounds;

@@ -1,28 +1,31 @@
 // sssp_round.cu -- sm_103a kernels of the SP_3/SP_4 round (Garg, arXiv
 // 1812.10499, Sec. V-VI).
 //
-// One round r is two kernels:
-//   k_relax   : SP_4 step 3, label-setting (as SP_3 explores only fixed
-//               vertices): every out-edge (x, y, w) of a vertex x fixed in
-//               round r - 1 lowers D[y] by a 64-bit atomicMin on the packed
-//               (distance, parent) word when y is not fixed.  A y whose D was
-//               infinite joins the active (discovered, unfixed) set.  The
-//               minima of D and D + outWeight over the active set (SP_4 step
-//               1; Lemmas 7 and 8) are folded in as relaxations succeed.
-//   k_cupdate : SP_4 steps 4 and 5 for every active y, reading the lower
-//               bounds of the previous round (Jacobi):
-//                 lb(x) = max(C[x], min(D[x], threshold))
-//                 C'[y] = max(C[y], min(D[y], threshold),
-//                             min over in-edges (x, y) of lb(x) + w)   (Eq. 1)
-//               y is fixed iff C'[y] = D[y]; fixed vertices form the next
-//               frontier, the others stay active and seed the next round's
-//               minima.  The last CTA to finish closes the round.
-// Both kernels pull work dynamically: 32 list entries per warp with a
-// warp-local load balance over their edges, or one chunk of a hub vertex.
-// Edges go through a per-warp three-stage cp.async pipeline in shared
-// memory: adjacency entries two batches ahead, neighbour states one batch
-// ahead, compute on the current batch.  List appends go through
-// warp-private buffers flushed 32 entries per atomic.
+// One round r is two phases:
+//   relax   : SP_4 step 3, label-setting (as SP_3 explores only fixed
+//             vertices): every out-edge (x, y, w) of a vertex x fixed in
+//             round r - 1 lowers D[y] by a 64-bit atomicMin on the packed
+//             (distance, parent) word when y is not fixed.  A y whose D was
+//             infinite joins the active (discovered, unfixed) set.  The
+//             minima of D and D + outWeight over the active set (SP_4 step
+//             1; Lemmas 7 and 8) are folded in as relaxations succeed.
+//   cupdate : SP_4 steps 4 and 5 for every active y, reading the lower
+//             bounds of the previous round (Jacobi):
+//               lb(x) = max(C[x], min(D[x], threshold))
+//               C'[y] = max(C[y], min(D[y], threshold),
+//                           min over in-edges (x, y) of lb(x) + w)   (Eq. 1)
+//             y is fixed iff C'[y] = D[y]; fixed vertices form the next
+//             frontier, the others stay active and seed the next round's
+//             minima.
+// The phases run as two kernels per round (k_relax, k_cupdate, driven by a
+// CUDA graph or the host) or inside one persistent cooperative kernel
+// (k_solve).  Work is pulled per warp: 32 list entries with a warp-local
+// load balance over their edges, or one chunk of a hub vertex.  Edges go
+// through a per-warp three-stage cp.async pipeline in shared memory:
+// adjacency two batches ahead, neighbour states one batch ahead, compute on
+// the current batch.  List appends go through warp-private buffers flushed
+// 32 entries per atomic.  Every kernel is templated on the state layout:
+// 32-byte records (WideL) or 16-byte records (NarrowL).
 #include "sssp_dev.cuh"
 
 namespace sssp {
@@ -43,18 +46,15 @@ __device__ __forceinline__ u32 ld_volatile(const u32* p) { return *(volatile con
 __device__ __forceinline__ u64 ld_volatile(const u64* p) { return *(volatile const u64*)p; }
 __device__ __forceinline__ u32 lanemask_le(u32 lane) { return 0xFFFFFFFFu >> (31 - lane); }
 
-// The two words a round reads from a vertex: packed D and the lower-bound
-// word of round parity `cur` (both in the record's 32-byte sector).
-__device__ __forceinline__ ulonglong2 ld_dc(const VRec* p, u32 cur) {
-    if (cur == 0) return *reinterpret_cast<const ulonglong2*>(p);
-    return make_ulonglong2(p->dp, p->cf[1]);
-}
-
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);
 }
 __device__ __forceinline__ void cp_async_8(void* s, const void* g) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(s)), "l"(g)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* s, const void* g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(s)), "l"(g)
                  : "memory");
 }
 // L2 policy for data read once per visit (adjacency): evicted first, so the
@@ -70,10 +70,6 @@ __device__ __forceinline__ void cp_async_8_stream(void* s, const void* g, u64 po
                  "l"(g), "l"(pol)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async_16(void* s, const void* g) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(s)), "l"(g)
-                 : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -82,10 +78,20 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Neighbour-state slot of a staged edge.  k_cupdate needs (D, C[cur]) -- 16
-// bytes; k_relax also needs outWeight and the in-degree -- the whole record.
-struct DcSlot {
-    ulonglong2 v;                       // (D word, C word of the round parity)
+// ----------------------------------------------------------- state layouts
+
+// A lower-bound word is handled in the wide form: value | kFixed (bit 63).
+__device__ __forceinline__ u64 widen_c(u32 c) {
+    return (u64)(c & ~kFixedN) | ((u64)(c & kFixedN) << 32);
+}
+__device__ __forceinline__ u32 narrow_c(u64 c) {
+    return (u32)(c & kCMask) | (u32)((c >> 32) & kFixedN);
+}
+
+// Staged neighbour state.  d() is the packed D word, c(cur) the wide-form
+// lower-bound word of round parity cur.
+struct DcSlot {                         // wide, k_cupdate: (D, C[cur])
+    ulonglong2 v;
     __device__ __forceinline__ void issue(const VRec* p, u32 cur) {
         if (cur == 0) {
             cp_async_16(&v, p);
@@ -97,8 +103,8 @@ struct DcSlot {
     __device__ __forceinline__ u64 d() const { return v.x; }
     __device__ __forceinline__ u64 c(u32) const { return v.y; }
 };
-struct RecSlot {
-    ulonglong2 lo, hi;                  // the 32-byte record
+struct RecSlot {                        // wide, k_relax: the whole record
+    ulonglong2 lo, hi;
     __device__ __forceinline__ void issue(const VRec* p, u32) {
         cp_async_16(&lo, p);
         cp_async_16(&hi, reinterpret_cast<const char*>(p) + 16);
@@ -107,6 +113,38 @@ struct RecSlot {
     __device__ __forceinline__ u64 c(u32 cur) const { return cur ? hi.x : lo.y; }
     __device__ __forceinline__ u32 outw() const { return (u32)hi.y; }
     __device__ __forceinline__ u32 indeg() const { return (u32)(hi.y >> 32); }
+};
+struct NSlot {                          // compact: the whole 16-byte record
+    ulonglong2 v;
+    __device__ __forceinline__ void issue(const VRecN* p, u32) { cp_async_16(&v, p); }
+    __device__ __forceinline__ u64 d() const { return v.x; }
+    __device__ __forceinline__ u64 c(u32 cur) const { return widen_c((u32)(v.y >> (32 * cur))); }
+};
+
+struct WideL {
+    typedef VRec Rec;
+    typedef RecSlot RSlot;
+    typedef DcSlot CSlot;
+    static constexpr bool kNarrow = false;
+    __device__ static Rec* rec(const RoundParams& P) { return P.rec; }
+    // (D word, wide C word of parity cur)
+    __device__ static ulonglong2 ld_dc(const Rec* p, u32 cur) {
+        if (cur == 0) return *reinterpret_cast<const ulonglong2*>(p);
+        return make_ulonglong2(p->dp, p->cf[1]);
+    }
+    __device__ static void set_c(Rec* p, u32 slot, u64 c) { p->cf[slot] = c; }
+};
+struct NarrowL {
+    typedef VRecN Rec;
+    typedef NSlot RSlot;
+    typedef NSlot CSlot;
+    static constexpr bool kNarrow = true;
+    __device__ static Rec* rec(const RoundParams& P) { return P.recn; }
+    __device__ static ulonglong2 ld_dc(const Rec* p, u32 cur) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(p);
+        return make_ulonglong2(v.x, widen_c((u32)(v.y >> (32 * cur))));
+    }
+    __device__ static void set_c(Rec* p, u32 slot, u64 c) { p->cf[slot] = narrow_c(c); }
 };
 
 // Shared-memory pipeline of one warp: adjacency of three batches and
@@ -202,7 +240,7 @@ __device__ __forceinline__ void wq_flush(const RoundParams& P, WarpQueue& q, u32
     q.cnt = 0;
 }
 
-// Accumulators a thread carries through one kernel.
+// Accumulators a thread carries through one phase.
 struct Acc {
     u64 fmin_d, fmin_t;     // folds of minD / threshold (single-query mode)
     u64 edges, visits;
@@ -226,7 +264,7 @@ __device__ __forceinline__ void fold(const RoundParams& P, u32 inst, u32 slot, u
     }
 }
 
-// Flush register folds and counters at the end of a kernel (all lanes).
+// Flush register folds and counters at the end of a phase (all lanes).
 template <bool MULTI>
 __device__ __forceinline__ void flush(const RoundParams& P, u32 slot, Acc& a, u32 lane,
                                       int stat_edges, int stat_visits) {
@@ -255,6 +293,18 @@ __device__ __forceinline__ const InstDesc& desc_of(const RoundParams& P, u32 g, 
     }
     inst = 0;
     return P.g;
+}
+
+// outWeight of local vertex v: from the record (wide) or the graph (compact).
+template <class L>
+__device__ __forceinline__ u32 outw_of(const InstDesc& d, const typename L::Rec* r, u32 v);
+template <>
+__device__ __forceinline__ u32 outw_of<WideL>(const InstDesc&, const VRec* r, u32) {
+    return r->outw;
+}
+template <>
+__device__ __forceinline__ u32 outw_of<NarrowL>(const InstDesc& d, const VRecN*, u32 v) {
+    return d.outw[v];
 }
 
 // ------------------------------------------------------------- pipeline
@@ -312,13 +362,14 @@ __device__ __forceinline__ Tile make_tile(WarpStage<S>& st, u32 deg, u64 eaddr, 
     return t;
 }
 
-// Owner lane of position j0 + lane of a tile, and the segment heads of that
-// row (bit p: position j0 + p starts an owner's edge list).
+// Owner lane of position j0 + lane of a tile: the owner of the row's first
+// position plus the number of segment heads (an owner's first edge) at or
+// before the lane, found with one OR-reduction of the heads.
 template <class S>
 __device__ __forceinline__ u32 row_owner(const WarpStage<S>& st, const Tile& t, u32 j0, u32 deg,
-                                         u32 lane, u32& heads) {
+                                         u32 lane) {
     const bool hd = deg > 0 && t.excl >= j0 && t.excl < j0 + 32;
-    heads = __reduce_or_sync(kFull, hd ? (1u << (t.excl - j0)) : 0u);
+    const u32 heads = __reduce_or_sync(kFull, hd ? (1u << (t.excl - j0)) : 0u);
     const u32 o0 = find_owner(t.excl, j0);
     const u32 r0 = __popc(t.nzmask & ((1u << o0) - 1u));
     const u32 rank = r0 + __popc(heads & lanemask_le(lane)) - (heads & 1u);
@@ -333,8 +384,7 @@ __device__ __forceinline__ void issue_tile_adj(WarpStage<S>& st, const Tile& t, 
     for (u32 i = 0; i < kBI; ++i) {
         const u32 j0 = b0 + 32 * i;
         if (j0 >= t.total) break;                 // warp-uniform
-        u32 heads;
-        const u32 own = row_owner(st, t, j0, deg, lane, heads);
+        const u32 own = row_owner(st, t, j0, deg, lane);
         const u32 j = j0 + lane;
         const u32 k = j - __shfl_sync(kFull, t.excl, own);
         const uint2* ep = reinterpret_cast<const uint2*>(__shfl_sync(kFull, t.eaddr, own)) + k;
@@ -360,9 +410,10 @@ __device__ __forceinline__ void issue_range_adj(WarpStage<S>& st, u32 s, const u
 // Starts gathering the neighbour states of the nb edges in adjacency slot
 // as into state slot ds.  `base` is the record base of the edge's graph,
 // taken from the owning lane in multi-query mode.
-template <bool MULTI, class S>
+template <bool MULTI, class L, class S>
 __device__ __forceinline__ void issue_dc(const RoundParams& P, WarpStage<S>& st, u32 as, u32 ds,
                                          u32 nb, u32 cur, u64 base, bool per_owner, u32 lane) {
+    typename L::Rec* rec = L::rec(P);
 #pragma unroll
     for (u32 i = 0; i < kBI; ++i) {
         if (32 * i >= nb) break;                   // warp-uniform
@@ -370,28 +421,29 @@ __device__ __forceinline__ void issue_dc(const RoundParams& P, WarpStage<S>& st,
         const bool ev = idx < nb;
         u64 ob = base;
         if (MULTI && per_owner) ob = __shfl_sync(kFull, base, ev ? st.own[as][idx] : 0u);
-        if (ev) st.dc[ds][idx].issue(P.rec + (u32)(ob + st.adj[as][idx].x), cur);
+        if (ev) st.dc[ds][idx].issue(rec + (u32)(ob + st.adj[as][idx].x), cur);
     }
 }
 
-// ---------------------------------------------------------------- k_relax
-
-typedef WarpStage<RecSlot> RelaxStage;
+// ------------------------------------------------------------------ relax
 
 // Relaxation of the staged edges [0, nb) (SP_4 step 3): per edge the owner's
 // distance dx and id xloc; newly discovered targets are queued.
-template <bool MULTI>
-__device__ __forceinline__ void relax_batch(const RoundParams& P, RelaxStage& st, u32 as, u32 ds,
+template <bool MULTI, class L>
+__device__ __forceinline__ void relax_batch(const RoundParams& P,
+                                            WarpStage<typename L::RSlot>& st, u32 as, u32 ds,
                                             u32 nb, u32 cur, bool per_owner, u64 dx, u32 xloc,
                                             u64 gbase, u32 inst, Acc& a, WarpQueue& q,
                                             u32 lane) {
+    typename L::Rec* rec = L::rec(P);
     u64 cand[kBI], old[kBI];
-    u32 gy[kBI];
+    u32 gy[kBI], yl[kBI];
 #pragma unroll
     for (u32 i = 0; i < kBI; ++i) {
         cand[i] = 0;
         old[i] = 0;                                // "not lowered"
         gy[i] = 0;
+        yl[i] = 0;
         if (32 * i >= nb) break;                   // warp-uniform
         const u32 idx = 32 * i + lane;
         const bool ev = idx < nb;
@@ -402,10 +454,16 @@ __device__ __forceinline__ void relax_batch(const RoundParams& P, RelaxStage& st
         if (MULTI && per_owner) ob = __shfl_sync(kFull, gbase, own);
         if (!ev) continue;
         const uint2 e = st.adj[as][idx];
-        const RecSlot& v = st.dc[ds][idx];
-        cand[i] = ((odx + e.y) << P.vbits) | ox;
+        const typename L::RSlot& v = st.dc[ds][idx];
+        const u64 dd = odx + e.y;
+        if (L::kNarrow && dd >= kNarrowLimit) {    // cannot happen when n * max w fits
+            atomicOr(&P.ctl->error, 8u);
+            continue;
+        }
+        cand[i] = (dd << P.vbits) | ox;
+        yl[i] = e.x;
         gy[i] = (u32)(ob + e.x);
-        if (!(v.c(cur) & kFixed) && cand[i] < v.d()) old[i] = atomicMin(&P.rec[gy[i]].dp, cand[i]);
+        if (!(v.c(cur) & kFixed) && cand[i] < v.d()) old[i] = atomicMin(&rec[gy[i]].dp, cand[i]);
         a.edges++;
     }
 #pragma unroll
@@ -416,13 +474,20 @@ __device__ __forceinline__ void relax_batch(const RoundParams& P, RelaxStage& st
         const bool fresh = ok && old[i] == kInf64;
         u32 indeg = 0;
         if (ok) {
-            const RecSlot& v = st.dc[ds][idx];
             u32 oinst = inst;
             if (MULTI && per_owner) oinst = P.page_owner[gy[i] >> P.page_shift];
-            const u32 ow = v.outw();
+            u32 ow;
+            if (L::kNarrow) {
+                const InstDesc& d = MULTI ? P.idesc[oinst] : P.g;
+                ow = d.outw[yl[i]];
+                if (fresh) indeg = (u32)(d.in_off[yl[i] + 1] - d.in_off[yl[i]]);
+            } else {
+                const RecSlot& v = reinterpret_cast<const RecSlot&>(st.dc[ds][idx]);
+                ow = v.outw();
+                indeg = v.indeg();
+            }
             const u64 dd = cand[i] >> P.vbits;
             fold<MULTI>(P, oinst, cur, dd, ow == kNoOutW ? P.dinf : dd + ow, a);
-            indeg = v.indeg();
         }
         const bool sm = fresh && indeg <= P.hub;
         wq_push(P, q, &P.ctl->nAS[cur], P.L.AS[cur], sm, gy[i], lane);
@@ -430,9 +495,9 @@ __device__ __forceinline__ void relax_batch(const RoundParams& P, RelaxStage& st
     }
 }
 
-template <bool MULTI>
-__device__ void relax_small(const RoundParams& P, RelaxStage& st, u32 t, u32 nfs, u32 cur,
-                            u32 lane, Acc& a, WarpQueue& q) {
+template <bool MULTI, class L>
+__device__ void relax_small(const RoundParams& P, WarpStage<typename L::RSlot>& st, u32 t,
+                            u32 nfs, u32 cur, u32 lane, Acc& a, WarpQueue& q) {
     const u32 idx = t * 32 + lane;
     const bool valid = idx < nfs;
     u32 g = 0, xloc = 0, inst = 0, deg = 0;
@@ -446,10 +511,9 @@ __device__ void relax_small(const RoundParams& P, RelaxStage& st, u32 t, u32 nfs
         xloc = g - (u32)gbase;
         b = d.out_off[xloc];
         deg = (u32)(d.out_off[xloc + 1] - b);
-        VRec* rx = P.rec + g;
-        const u64 cfx = rx->cf[cur];
-        rx->cf[cur ^ 1] = cfx;       // keep both copies "fixed" from now on
-        dx = cfx & kCMask;           // C = D for a fixed vertex
+        typename L::Rec* rx = L::rec(P) + g;
+        rx->cf[cur ^ 1] = rx->cf[cur];              // keep both copies "fixed"
+        dx = L::ld_dc(rx, cur).y & kCMask;          // C = D for a fixed vertex
         a.visits++;
     }
     const Tile tl = make_tile(st, deg, (u64)(adj + b), lane);
@@ -457,17 +521,17 @@ __device__ void relax_small(const RoundParams& P, RelaxStage& st, u32 t, u32 nfs
         (tl.total + kB - 1) / kB,
         [&](u32 bb, u32 s) { issue_tile_adj(st, tl, s, bb * kB, deg, lane); },
         [&](u32 bb, u32 as, u32 ds) {
-            issue_dc<MULTI>(P, st, as, ds, min(kB, tl.total - bb * kB), cur, gbase, true, lane);
+            issue_dc<MULTI, L>(P, st, as, ds, min(kB, tl.total - bb * kB), cur, gbase, true, lane);
         },
         [&](u32 bb, u32 as, u32 ds) {
-            relax_batch<MULTI>(P, st, as, ds, min(kB, tl.total - bb * kB), cur, true, dx, xloc,
-                               gbase, inst, a, q, lane);
+            relax_batch<MULTI, L>(P, st, as, ds, min(kB, tl.total - bb * kB), cur, true, dx, xloc,
+                                  gbase, inst, a, q, lane);
         });
 }
 
-template <bool MULTI>
-__device__ void relax_hub(const RoundParams& P, RelaxStage& st, u32 c, u32 nfh, u32 cur,
-                          u32 lane, Acc& a, WarpQueue& q) {
+template <bool MULTI, class L>
+__device__ void relax_hub(const RoundParams& P, WarpStage<typename L::RSlot>& st, u32 c, u32 nfh,
+                          u32 cur, u32 lane, Acc& a, WarpQueue& q) {
     const uint2* FH = P.L.FH[cur];
     u32 lo = 0, hi = nfh;
     while (hi - lo > 1) {
@@ -482,10 +546,10 @@ __device__ void relax_hub(const RoundParams& P, RelaxStage& st, u32 c, u32 nfh, 
     const u64 b = d.out_off[xloc], e_end = d.out_off[xloc + 1];
     const u64 cb = b + (u64)k * P.chunk;
     const u64 ce = umin64(cb + P.chunk, e_end);
-    VRec* rx = P.rec + g;
-    const u64 cfx = rx->cf[cur];
+    typename L::Rec* rx = L::rec(P) + g;
+    const u64 dx = L::ld_dc(rx, cur).y & kCMask;
     if (k == 0 && lane == 0) {
-        rx->cf[cur ^ 1] = cfx;
+        rx->cf[cur ^ 1] = rx->cf[cur];
         a.visits++;
     }
     const u32 n = ce > cb ? (u32)(ce - cb) : 0u;
@@ -493,19 +557,30 @@ __device__ void relax_hub(const RoundParams& P, RelaxStage& st, u32 c, u32 nfh, 
         (n + kB - 1) / kB,
         [&](u32 bb, u32 s) { issue_range_adj(st, s, d.out_adj, cb + bb * kB, ce, lane); },
         [&](u32 bb, u32 as, u32 ds) {
-            issue_dc<MULTI>(P, st, as, ds, min(kB, n - bb * kB), cur, d.base, false, lane);
+            issue_dc<MULTI, L>(P, st, as, ds, min(kB, n - bb * kB), cur, d.base, false, lane);
         },
         [&](u32 bb, u32 as, u32 ds) {
-            relax_batch<MULTI>(P, st, as, ds, min(kB, n - bb * kB), cur, false, cfx & kCMask,
-                               xloc, d.base, inst, a, q, lane);
+            relax_batch<MULTI, L>(P, st, as, ds, min(kB, n - bb * kB), cur, false, dx, xloc,
+                                  d.base, inst, a, q, lane);
         });
 }
 
+template <class L>
+constexpr size_t relax_smem() {
+    return sizeof(WarpStage<typename L::RSlot>) * kWarps + sizeof(u32) * kWarps * kQCap;
+}
+template <class L>
+constexpr size_t cupdate_smem() {
+    return sizeof(WarpStage<typename L::CSlot>) * kWarps + sizeof(u64) * kWarps * 32 +
+           2 * sizeof(u32) * kWarps * kQCap;
+}
+
 // Step (a) of round r over the whole frontier (all CTAs of the grid).
-template <bool MULTI>
+template <bool MULTI, class L>
 __device__ void relax_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
-    RelaxStage* s_st = reinterpret_cast<RelaxStage*>(s_dyn);
-    u32* s_q = reinterpret_cast<u32*>(s_dyn + sizeof(RelaxStage) * kWarps);
+    typedef WarpStage<typename L::RSlot> Stage;
+    Stage* s_st = reinterpret_cast<Stage*>(s_dyn);
+    u32* s_q = reinterpret_cast<u32*>(s_dyn + sizeof(Stage) * kWarps);
     Ctl* ctl = P.ctl;
     const u32 cur = r & 1u, nxt = cur ^ 1u;
     const u32 lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
@@ -543,8 +618,9 @@ __device__ void relax_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
     // First item per warp is static (no atomic); the rest are pulled.
     const u32 nwarps = gridDim.x * kWarps;
     for (u32 item = blockIdx.x * kWarps + wib; item < total;) {
-        if (item < tiles) relax_small<MULTI>(P, s_st[wib], item, nfs, cur, lane, a, q);
-        else relax_hub<MULTI>(P, s_st[wib], item - tiles, nfh, cur, lane, a, q);
+        if (item < tiles) relax_small<MULTI, L>(P, s_st[wib], item, nfs, cur, lane, a, q);
+        else relax_hub<MULTI, L>(P, s_st[wib], item - tiles, nfh, cur, lane, a, q);
+        if (total <= nwarps) break;                // the static items were all
         u32 next = 0;
         if (lane == 0) next = atomicAdd(&ctl->work[0], 1u) + nwarps;
         item = __shfl_sync(kFull, next, 0);
@@ -553,22 +629,22 @@ __device__ void relax_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
     flush<MULTI>(P, cur, a, lane, 0, 3);
 }
 
-template <bool MULTI>
+template <bool MULTI, class L>
 __global__ void __launch_bounds__(256, 3) k_relax(RoundParams P) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     if (ld_volatile(&P.ctl->status) != kRunning) return;
-    relax_phase<MULTI>(P, s_dyn, P.ctl->round);
+    relax_phase<MULTI, L>(P, s_dyn, P.ctl->round);
 }
 
-// -------------------------------------------------------------- k_cupdate
-
-typedef WarpStage<DcSlot> CupStage;
+// ---------------------------------------------------------------- cupdate
 
 // lb(x): the lower bound an in-neighbour contributes (Lemmas 7 and 8); with
 // rule 1 the printed SP_4 step 4 clamp (minD for unfixed vertices).
-__device__ __forceinline__ u64 lb_of(const RoundParams& P, const DcSlot& v, u64 thr, u64 minD) {
+template <class S>
+__device__ __forceinline__ u64 lb_of(const RoundParams& P, const S& v, u32 cur, u64 thr,
+                                     u64 minD) {
     const u64 dx = v.d() >> P.vbits;          // infinity maps to dinf
-    const u64 cw = v.c(0);
+    const u64 cw = v.c(cur);
     const u64 cx = cw & kCMask;
     if (P.rule == 0) return umax64(cx, umin64(dx, thr));
     return (cw & kFixed) ? cx : umax64(cx, minD);
@@ -583,10 +659,10 @@ __device__ __forceinline__ u64 decide(const RoundParams& P, u64 dy, u64 cy, u64 
     return fix ? dy : cn;
 }
 
-template <bool MULTI>
-__device__ void cup_small(const RoundParams& P, CupStage& st, u32 t, u32 nas, u32 r, u32 cur,
-                          u32 lane, u64* smin, u64 thr0, u64 minD0, Acc& a, Acc& an,
-                          WarpQueue& qf, WarpQueue& qa) {
+template <bool MULTI, class L>
+__device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st, u32 t, u32 nas,
+                          u32 r, u32 cur, u32 lane, u64* smin, u64 thr0, u64 minD0, Acc& a,
+                          Acc& an, WarpQueue& qf, WarpQueue& qa) {
     const u32 nxt = cur ^ 1u;
     const u32 idx = t * 32 + lane;
     const bool valid = idx < nas;
@@ -594,6 +670,7 @@ __device__ void cup_small(const RoundParams& P, CupStage& st, u32 t, u32 nas, u3
     u64 gbase = 0, ib = 0, dy = 0, cy = 0, thr = thr0, minD = minD0;
     const uint2* in_adj = P.g.in_adj;
     const u64* out_off = P.g.out_off;
+    typename L::Rec* rec = L::rec(P);
     if (valid) {
         g = P.L.AS[cur][idx];
         const InstDesc& d = desc_of<MULTI>(P, g, inst);
@@ -607,10 +684,10 @@ __device__ void cup_small(const RoundParams& P, CupStage& st, u32 t, u32 nas, u3
         yloc = g - (u32)gbase;
         ib = d.in_off[yloc];
         deg = (u32)(d.in_off[yloc + 1] - ib);
-        const ulonglong2 v = ld_dc(P.rec + g, cur);
+        const ulonglong2 v = L::ld_dc(rec + g, cur);
         dy = v.x >> P.vbits;
         cy = v.y & kCMask;
-        outw = P.rec[g].outw;
+        outw = outw_of<L>(d, rec + g, yloc);
     }
     smin[lane] = kInf64;
     const Tile tl = make_tile(st, deg, (u64)(in_adj + ib), lane);
@@ -618,7 +695,7 @@ __device__ void cup_small(const RoundParams& P, CupStage& st, u32 t, u32 nas, u3
         (tl.total + kB - 1) / kB,
         [&](u32 b, u32 s) { issue_tile_adj(st, tl, s, b * kB, deg, lane); },
         [&](u32 b, u32 as, u32 ds) {
-            issue_dc<MULTI>(P, st, as, ds, min(kB, tl.total - b * kB), cur, gbase, true, lane);
+            issue_dc<MULTI, L>(P, st, as, ds, min(kB, tl.total - b * kB), cur, gbase, true, lane);
         },
         [&](u32 b, u32 as, u32 ds) {
             const u32 nb = min(kB, tl.total - b * kB);
@@ -635,7 +712,7 @@ __device__ void cup_small(const RoundParams& P, CupStage& st, u32 t, u32 nas, u3
                 }
                 u64 val = kInf64;
                 if (ev)
-                    val = umin64(lb_of(P, st.dc[ds][sidx], othr, omin) + st.adj[as][sidx].y,
+                    val = umin64(lb_of(P, st.dc[ds][sidx], cur, othr, omin) + st.adj[as][sidx].y,
                                  P.dinf);
                 // Segmented min over lanes sharing an owner: owners are
                 // contiguous, a lane's segment starts at the last owner
@@ -659,7 +736,7 @@ __device__ void cup_small(const RoundParams& P, CupStage& st, u32 t, u32 nas, u3
     bool fix = false;
     if (valid) {
         const u64 cn = decide(P, dy, cy, smin[lane], thr, minD, fix);
-        P.rec[g].cf[nxt] = cn | (fix ? kFixed : 0ull);
+        L::set_c(rec + g, nxt, cn | (fix ? kFixed : 0ull));
         if (fix) P.fround[g] = (int)r;
         a.visits++;
     }
@@ -679,9 +756,10 @@ __device__ void cup_small(const RoundParams& P, CupStage& st, u32 t, u32 nas, u3
     if (sv) fold<MULTI>(P, inst, nxt, dy, outw == kNoOutW ? P.dinf : dy + outw, an);
 }
 
-template <bool MULTI>
-__device__ void cup_hub(const RoundParams& P, CupStage& st, u32 c, u32 nah, u32 ah_chunks,
-                        u32 r, u32 cur, u32 lane, u64 thr0, u64 minD0, Acc& a, Acc& an) {
+template <bool MULTI, class L>
+__device__ void cup_hub(const RoundParams& P, WarpStage<typename L::CSlot>& st, u32 c, u32 nah,
+                        u32 ah_chunks, u32 r, u32 cur, u32 lane, u64 thr0, u64 minD0, Acc& a,
+                        Acc& an) {
     const u32 nxt = cur ^ 1u;
     const uint2* AH = P.L.AH[cur];
     u32 lo = 0, hi = nah;
@@ -709,7 +787,7 @@ __device__ void cup_hub(const RoundParams& P, CupStage& st, u32 c, u32 nah, u32 
         (n + kB - 1) / kB,
         [&](u32 b, u32 s) { issue_range_adj(st, s, d.in_adj, cb + b * kB, ce, lane); },
         [&](u32 b, u32 as, u32 ds) {
-            issue_dc<MULTI>(P, st, as, ds, min(kB, n - b * kB), cur, d.base, false, lane);
+            issue_dc<MULTI, L>(P, st, as, ds, min(kB, n - b * kB), cur, d.base, false, lane);
         },
         [&](u32 b, u32 as, u32 ds) {
             const u32 nb = min(kB, n - b * kB);
@@ -717,7 +795,7 @@ __device__ void cup_hub(const RoundParams& P, CupStage& st, u32 c, u32 nah, u32 
             for (u32 i = 0; i < kBI; ++i) {
                 const u32 sidx = 32 * i + lane;
                 if (sidx < nb)
-                    val = umin64(val, umin64(lb_of(P, st.dc[ds][sidx], thr, minD) +
+                    val = umin64(val, umin64(lb_of(P, st.dc[ds][sidx], cur, thr, minD) +
                                                  st.adj[as][sidx].y,
                                              P.dinf));
             }
@@ -732,14 +810,14 @@ __device__ void cup_hub(const RoundParams& P, CupStage& st, u32 c, u32 nah, u32 
     __threadfence();
     const u64 m = atomicExch(&P.L.hubmin[lo], kInf64);
     P.L.hubcnt[lo] = 0;
-    VRec* ry = P.rec + g;
-    const ulonglong2 v = ld_dc(ry, cur);
+    typename L::Rec* ry = L::rec(P) + g;
+    const ulonglong2 v = L::ld_dc(ry, cur);
     const u64 dy = v.x >> P.vbits;
     const u64 cy = v.y & kCMask;
-    const u32 outw = ry->outw;
+    const u32 outw = outw_of<L>(d, ry, yloc);
     bool fix;
     const u64 cn = decide(P, dy, cy, m, thr, minD, fix);
-    ry->cf[nxt] = cn | (fix ? kFixed : 0ull);
+    L::set_c(ry, nxt, cn | (fix ? kFixed : 0ull));
     a.visits++;
     if (fix) {
         P.fround[g] = (int)r;
@@ -795,10 +873,11 @@ __device__ void round_epilogue(const RoundParams& P, u32 r) {
 }
 
 // Steps (b) and (c) of round r over the whole active set (all CTAs).
-template <bool MULTI>
+template <bool MULTI, class L>
 __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
-    CupStage* s_st = reinterpret_cast<CupStage*>(s_dyn);
-    u64* s_min = reinterpret_cast<u64*>(s_dyn + sizeof(CupStage) * kWarps);
+    typedef WarpStage<typename L::CSlot> Stage;
+    Stage* s_st = reinterpret_cast<Stage*>(s_dyn);
+    u64* s_min = reinterpret_cast<u64*>(s_dyn + sizeof(Stage) * kWarps);
     u32* s_qf = reinterpret_cast<u32*>(s_min + kWarps * 32);
     u32* s_qa = s_qf + kWarps * kQCap;
     Ctl* ctl = P.ctl;
@@ -824,12 +903,13 @@ __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r)
     const u32 nwarps = gridDim.x * kWarps;
     for (u32 item = blockIdx.x * kWarps + wib; item < total;) {
         if (item < tiles)
-            cup_small<MULTI>(P, s_st[wib], item, nas, r, cur, lane, s_min + wib * 32, thr, minD, a,
-                             an, qf, qa);
+            cup_small<MULTI, L>(P, s_st[wib], item, nas, r, cur, lane, s_min + wib * 32, thr,
+                                minD, a, an, qf, qa);
         else
-            cup_hub<MULTI>(P, s_st[wib], item - tiles, nah, ah_chunks, r, cur, lane, thr, minD, a,
-                           an);
+            cup_hub<MULTI, L>(P, s_st[wib], item - tiles, nah, ah_chunks, r, cur, lane, thr, minD,
+                              a, an);
         __syncwarp();
+        if (total <= nwarps) break;                // the static items were all
         u32 next = 0;
         if (lane == 0) next = atomicAdd(&ctl->work[1], 1u) + nwarps;
         item = __shfl_sync(kFull, next, 0);
@@ -842,7 +922,7 @@ __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r)
     flush<MULTI>(P, nxt, a, lane, 1, 2);
 }
 
-template <bool MULTI>
+template <bool MULTI, class L>
 __global__ void __launch_bounds__(256, 3) k_cupdate(RoundParams P) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ u32 s_last;
@@ -853,7 +933,7 @@ __global__ void __launch_bounds__(256, 3) k_cupdate(RoundParams P) {
         return;
     }
     const u32 r = ctl->round;
-    cupdate_phase<MULTI>(P, s_dyn, r);
+    cupdate_phase<MULTI, L>(P, s_dyn, r);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -919,7 +999,7 @@ __device__ bool grid_barrier(const RoundParams& P, bool epilogue, u32 r) {
 // All rounds of the running queries in one launch: relax phase, barrier,
 // lower-bound phase, barrier (whose last arriver closes the round), until
 // no query runs, the stop round is passed, or a barrier times out.
-template <bool MULTI>
+template <bool MULTI, class L>
 __global__ void __launch_bounds__(256, 3) k_solve(RoundParams P) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     Ctl* ctl = P.ctl;
@@ -928,16 +1008,18 @@ __global__ void __launch_bounds__(256, 3) k_solve(RoundParams P) {
         if (ld_volatile(&ctl->status) != kRunning) break;
         const u32 r = ld_volatile(&ctl->round);
         if (r > ld_volatile(&ctl->stop_round)) break;
-        relax_phase<MULTI>(P, s_dyn, r);
+        relax_phase<MULTI, L>(P, s_dyn, r);
         if (!grid_barrier(P, false, r)) break;
-        cupdate_phase<MULTI>(P, s_dyn, r);
+        cupdate_phase<MULTI, L>(P, s_dyn, r);
         if (!grid_barrier(P, true, r)) break;
     }
 }
 
+// -------------------------------------------------- per-query start state
+
 // Starts the queries in slots [first, first + count) at the control block's
 // current round: the source is fixed with D = C = 0 and forms the frontier.
-template <bool MULTI>
+template <bool MULTI, class L>
 __global__ void k_start(RoundParams P, u32 first, u32 count, u32 max_rounds) {
     Ctl* ctl = P.ctl;
     const u32 r = ctl->round;
@@ -954,13 +1036,10 @@ __global__ void k_start(RoundParams P, u32 first, u32 count, u32 max_rounds) {
         v->max_rounds = max_rounds;
         const u32 s = d.source;
         const u32 g = (u32)(d.base + s);
-        VRec rs;
-        rs.dp = s;                    // distance 0, parent = itself
-        rs.cf[0] = kFixed;
-        rs.cf[1] = kFixed;
-        rs.outw = d.outw[s];
-        rs.indeg = (u32)(d.in_off[s + 1] - d.in_off[s]);
-        P.rec[g] = rs;
+        typename L::Rec* rs = L::rec(P) + g;
+        rs->dp = s;                   // distance 0, parent = itself
+        L::set_c(rs, 0, kFixed);
+        L::set_c(rs, 1, kFixed);
         P.fround[g] = 0;
         const u64 odeg = d.out_off[s + 1] - d.out_off[s];
         if (odeg <= P.hub) put_small(P, P.L.FS[cur], atomicAdd(&ctl->nFS[cur], 1u), g);
@@ -975,83 +1054,95 @@ __global__ void k_start(RoundParams P, u32 first, u32 count, u32 max_rounds) {
     }
 }
 
-template __global__ void k_relax<false>(RoundParams);
-template __global__ void k_relax<true>(RoundParams);
-template __global__ void k_cupdate<false>(RoundParams);
-template __global__ void k_cupdate<true>(RoundParams);
-template __global__ void k_start<false>(RoundParams, u32, u32, u32);
-template __global__ void k_start<true>(RoundParams, u32, u32, u32);
-template __global__ void k_solve<false>(RoundParams);
-template __global__ void k_solve<true>(RoundParams);
+// ----------------------------------------------- host access for the engine
 
-// --------------------------------------------- host access for the engine
-
-const void* relax_fn(bool multi) {
-    return multi ? (const void*)k_relax<true> : (const void*)k_relax<false>;
+const void* relax_fn(bool multi, bool narrow) {
+    if (multi) return narrow ? (const void*)k_relax<true, NarrowL> : (const void*)k_relax<true, WideL>;
+    return narrow ? (const void*)k_relax<false, NarrowL> : (const void*)k_relax<false, WideL>;
 }
-const void* cupdate_fn(bool multi) {
-    return multi ? (const void*)k_cupdate<true> : (const void*)k_cupdate<false>;
+const void* cupdate_fn(bool multi, bool narrow) {
+    if (multi)
+        return narrow ? (const void*)k_cupdate<true, NarrowL> : (const void*)k_cupdate<true, WideL>;
+    return narrow ? (const void*)k_cupdate<false, NarrowL> : (const void*)k_cupdate<false, WideL>;
 }
-const void* solve_fn(bool multi) {
-    return multi ? (const void*)k_solve<true> : (const void*)k_solve<false>;
+const void* solve_fn(bool multi, bool narrow) {
+    if (multi) return narrow ? (const void*)k_solve<true, NarrowL> : (const void*)k_solve<true, WideL>;
+    return narrow ? (const void*)k_solve<false, NarrowL> : (const void*)k_solve<false, WideL>;
 }
-size_t relax_smem_bytes() { return sizeof(RelaxStage) * kWarps + sizeof(u32) * kWarps * kQCap; }
-size_t cupdate_smem_bytes() {
-    return sizeof(CupStage) * kWarps + sizeof(u64) * kWarps * 32 + 2 * sizeof(u32) * kWarps * kQCap;
+size_t relax_smem_bytes(bool narrow) {
+    return narrow ? relax_smem<NarrowL>() : relax_smem<WideL>();
 }
-size_t solve_smem_bytes() {
-    return relax_smem_bytes() > cupdate_smem_bytes() ? relax_smem_bytes() : cupdate_smem_bytes();
+size_t cupdate_smem_bytes(bool narrow) {
+    return narrow ? cupdate_smem<NarrowL>() : cupdate_smem<WideL>();
+}
+size_t solve_smem_bytes(bool narrow) {
+    const size_t a = relax_smem_bytes(narrow), b = cupdate_smem_bytes(narrow);
+    return a > b ? a : b;
 }
 
-// Co-resident CTAs per SM of the persistent kernel (its grid must fit).
-int solve_blocks_per_sm(int threads) {
-    int a = 0, b = 0;
-    const size_t sb = solve_smem_bytes();
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_solve<false>, threads, sb);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_solve<true>, threads, sb);
-    return a < b ? a : b;
+cudaError_t launch_start(bool multi, bool narrow, const RoundParams& P, u32 first, u32 count,
+                         u32 max_rounds, cudaStream_t st) {
+    if (multi) {
+        if (narrow) k_start<true, NarrowL><<<1, 256, 0, st>>>(P, first, count, max_rounds);
+        else k_start<true, WideL><<<1, 256, 0, st>>>(P, first, count, max_rounds);
+    } else {
+        if (narrow) k_start<false, NarrowL><<<1, 32, 0, st>>>(P, first, count, max_rounds);
+        else k_start<false, WideL><<<1, 32, 0, st>>>(P, first, count, max_rounds);
+    }
+    return cudaGetLastError();
 }
 
 // Raises the dynamic shared-memory limit of the round kernels (once per
 // process and device).
 cudaError_t round_kernels_init() {
     cudaError_t e = cudaSuccess;
-    const int rb = (int)relax_smem_bytes(), cb = (int)cupdate_smem_bytes();
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_relax<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rb);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_relax<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rb);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_cupdate<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cb);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_cupdate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cb);
-    const int sb = (int)solve_smem_bytes();
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+    for (int m = 0; m < 2 && e == cudaSuccess; ++m)
+        for (int nw = 0; nw < 2 && e == cudaSuccess; ++nw) {
+            const bool multi = m, narrow = nw;
+            e = cudaFuncSetAttribute(relax_fn(multi, narrow),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)relax_smem_bytes(narrow));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(cupdate_fn(multi, narrow),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cupdate_smem_bytes(narrow));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(solve_fn(multi, narrow),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)solve_smem_bytes(narrow));
+        }
     return e;
 }
 
-cudaError_t launch_start(bool multi, const RoundParams& P, u32 first, u32 count, u32 max_rounds,
-                         cudaStream_t st) {
-    if (multi) k_start<true><<<1, 256, 0, st>>>(P, first, count, max_rounds);
-    else k_start<false><<<1, 32, 0, st>>>(P, first, count, max_rounds);
-    return cudaGetLastError();
-}
-
+// CTAs per SM that fit every variant of the two-kernel round.
 int round_blocks_per_sm(int threads) {
     if (round_kernels_init() != cudaSuccess) return 1;
-    int a = 0, b = 0, c = 0, d = 0;
-    const size_t rb = relax_smem_bytes(), cb = cupdate_smem_bytes();
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cupdate<false>, threads, cb);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_relax<false>, threads, rb);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_cupdate<true>, threads, cb);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_relax<true>, threads, rb);
-    int m = a < b ? a : b;
-    m = m < c ? m : c;
-    m = m < d ? m : d;
-    return m;
+    int best = 1 << 30;
+    for (int m = 0; m < 2; ++m)
+        for (int nw = 0; nw < 2; ++nw) {
+            int a = 0, b = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, relax_fn(m, nw), threads,
+                                                          relax_smem_bytes(nw));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cupdate_fn(m, nw), threads,
+                                                          cupdate_smem_bytes(nw));
+            best = a < best ? a : best;
+            best = b < best ? b : best;
+        }
+    return best;
+}
+
+// Co-resident CTAs per SM of the persistent kernel (its grid must fit).
+int solve_blocks_per_sm(int threads) {
+    if (round_kernels_init() != cudaSuccess) return 1;
+    int best = 1 << 30;
+    for (int m = 0; m < 2; ++m)
+        for (int nw = 0; nw < 2; ++nw) {
+            int a = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, solve_fn(m, nw), threads,
+                                                          solve_smem_bytes(nw));
+            best = a < best ? a : best;
+        }
+    return best;
 }
 
 }  // namespace sssp

@@ -153,7 +153,7 @@ int admit(sssp_server* s) {
                            sizeof(u32) * q->npages, cudaMemcpyHostToDevice, s->stream));
         k_init_records_multi<<<c.grid, kThreads, 0, s->stream>>>(c.P, c.nrec, first, q->npages);
         CK(cudaGetLastError());
-        CK(launch_start(true, c.P, slot, 1, 0, s->stream));
+        CK(launch_start(true, false, c.P, slot, 1, 0, s->stream));
         q->state = kInFlight;
         s->slot_query[slot] = q;
         s->inflight++;
@@ -177,7 +177,7 @@ int retire(sssp_server* s) {
         Query* q = s->slot_query[slot];
         if (!q || c.h_ivar[slot].status != kDone) continue;
         const u64 base = (u64)q->first_page << kPageShift;
-        k_finalize<<<c.grid, kThreads, 0, s->stream>>>(c.P.rec, c.P.fround, base, q->g->n,
+        k_finalize<<<c.grid, kThreads, 0, s->stream>>>(c.P.rec, nullptr, c.P.fround, base, q->g->n,
                                                        c.P.vbits,
                                                        c.P.ivar + slot, c.stage + base, nullptr,
                                                        nullptr, nullptr);

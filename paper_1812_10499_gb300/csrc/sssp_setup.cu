@@ -13,16 +13,26 @@ __device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
 // ------------------------------------------------------- start / finalize
 
 // Every record of a single query: D = inf, C = 0 (Fig. SP_4 declarations).
-__global__ void k_init_records(VRec* rec, int* fround, const u32* outw, const u64* in_off, u32 n) {
+// Exactly one of rec (32-byte records) and recn (16-byte records) is set.
+__global__ void k_init_records(VRec* rec, VRecN* recn, int* fround, const u32* outw,
+                               const u64* in_off, u32 n) {
     for (u64 v = blockIdx.x * (u64)blockDim.x + threadIdx.x; v < n;
          v += (u64)gridDim.x * blockDim.x) {
-        VRec r;
-        r.dp = kInf64;
-        r.cf[0] = 0;
-        r.cf[1] = 0;
-        r.outw = outw[v];
-        r.indeg = (u32)(in_off[v + 1] - in_off[v]);
-        rec[v] = r;
+        if (recn) {
+            VRecN r;
+            r.dp = kInf64;
+            r.cf[0] = 0;
+            r.cf[1] = 0;
+            recn[v] = r;
+        } else {
+            VRec r;
+            r.dp = kInf64;
+            r.cf[0] = 0;
+            r.cf[1] = 0;
+            r.outw = outw[v];
+            r.indeg = (u32)(in_off[v + 1] - in_off[v]);
+            rec[v] = r;
+        }
         fround[v] = -1;
     }
 }
@@ -38,13 +48,21 @@ __global__ void k_init_records_multi(RoundParams P, u64 nrec, u32 first_page, u3
         const InstDesc& d = P.idesc[inst];
         const u64 v = g - d.base;
         if (v >= d.n) continue;
-        VRec r;
-        r.dp = kInf64;
-        r.cf[0] = 0;
-        r.cf[1] = 0;
-        r.outw = d.outw[v];
-        r.indeg = (u32)(d.in_off[v + 1] - d.in_off[v]);
-        P.rec[g] = r;
+        if (P.recn) {
+            VRecN r;
+            r.dp = kInf64;
+            r.cf[0] = 0;
+            r.cf[1] = 0;
+            P.recn[g] = r;
+        } else {
+            VRec r;
+            r.dp = kInf64;
+            r.cf[0] = 0;
+            r.cf[1] = 0;
+            r.outw = d.outw[v];
+            r.indeg = (u32)(d.in_off[v + 1] - d.in_off[v]);
+            P.rec[g] = r;
+        }
         P.fround[g] = -1;
     }
 }
@@ -63,20 +81,30 @@ __global__ void k_reset_ctl(Ctl* ctl, u32 ninst, u32 round_limit) {
 }
 
 // Output of one query (Sec. I: cost[x]; parents as in Sec. I's remark on
-// backward parent pointers).
+// backward parent pointers).  Exactly one of rec and recn is set.
 // The lower bounds after the query's last round r sit in cf[(r + 1) & 1].
-__global__ void k_finalize(const VRec* rec, const int* frec, u64 base, u32 n, u32 vbits,
-                           const InstVar* iv, u64* dist, u32* parent, int* fround, u64* lower) {
+__global__ void k_finalize(const VRec* rec, const VRecN* recn, const int* frec, u64 base, u32 n,
+                           u32 vbits, const InstVar* iv, u64* dist, u32* parent, int* fround,
+                           u64* lower) {
     const u64 vmask = (vbits >= 64) ? ~0ull : ((1ull << vbits) - 1);
     const u32 cslot = (iv->start_round + iv->rounds) & 1u;
     for (u64 v = blockIdx.x * (u64)blockDim.x + threadIdx.x; v < n;
          v += (u64)gridDim.x * blockDim.x) {
-        const VRec r = rec[base + v];
-        const bool reach = r.dp != kInf64;
-        if (dist) dist[v] = reach ? (r.dp >> vbits) : kInf64;
-        if (parent) parent[v] = reach ? (u32)(r.dp & vmask) : kFull;
+        u64 dp, c;
+        if (recn) {
+            const VRecN r = recn[base + v];
+            dp = r.dp;
+            c = (cslot ? r.cf[1] : r.cf[0]) & ~kFixedN;
+        } else {
+            const VRec r = rec[base + v];
+            dp = r.dp;
+            c = (cslot ? r.cf[1] : r.cf[0]) & kCMask;
+        }
+        const bool reach = dp != kInf64;
+        if (dist) dist[v] = reach ? (dp >> vbits) : kInf64;
+        if (parent) parent[v] = reach ? (u32)(dp & vmask) : kFull;
         if (fround) fround[v] = frec[base + v];
-        if (lower) lower[v] = r.cf[cslot] & kCMask;
+        if (lower) lower[v] = c;
     }
 }
 
@@ -87,7 +115,7 @@ __global__ void k_finalize_multi(RoundParams P, u64 nrec, u64* dist) {
          g += (u64)gridDim.x * blockDim.x) {
         const u32 inst = P.page_owner[g >> P.page_shift];
         if (inst == kFull) continue;
-        const u64 dp = P.rec[g].dp;
+        const u64 dp = P.recn ? P.recn[g].dp : P.rec[g].dp;
         dist[g] = (dp == kInf64) ? kInf64 : (dp >> P.vbits);
     }
 }

@@ -88,6 +88,25 @@ def test_create_rejects_bad_graphs_before_touching_a_device(lib):
     assert _create(n, rp, [1], [0xFFFFFFFF]) == -4
 
 
+def test_layout_option_checked_on_the_host(lib):
+    import paper_1812_10499_gb300 as P
+    rp = np.array([0, 1, 1], dtype=np.uint64)
+    col = np.array([1], dtype=np.uint32)
+
+    def create(w, layout):
+        o = P.sssp_options_default()
+        o.layout = layout
+        wa = np.array([w], dtype=np.uint32)
+        h = ctypes.c_void_p()
+        return lib.sssp_create(2, 1, rp.ctypes.data, col.ctypes.data, wa.ctypes.data, None,
+                               None, None, ctypes.byref(o), ctypes.byref(h))
+    # Unknown layout.
+    assert create(5, 3) == -1
+    # Compact records need n * max weight < 2^31 - 1: 2 * 2^30 does not fit.
+    assert create(1 << 30, P.SSSP_LAYOUT_COMPACT) == -4
+    assert lib.sssp_layout(None) == 0
+
+
 def test_null_handles(lib):
     assert lib.sssp_solve(None, 0, None, None) == -1
     assert lib.sssp_solve_ex(None, 0, None, None) == -1

@@ -39,6 +39,28 @@ def test_batch_independent_graphs(sssp_lib):
             P.sssp_destroy(h)
 
 
+def test_batch_layouts(sssp_lib):
+    """A batch runs on compact records only when every graph allows them; one
+    graph with large weights switches the whole batch to wide records, and
+    the same workspace then serves a compact batch again."""
+    P = sssp_lib
+    graphs, srcs = batch_graphs(6, 7, nmax=3000)
+    big = gg.random_graph(3000, 6, 1 << 19, (1 << 20) - 1, 8)
+    hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w) for g in graphs + [big]]
+    try:
+        assert P.sssp_layout(hs[-1]) == P.SSSP_LAYOUT_WIDE
+        for sel in (list(range(6)), list(range(7)), list(range(6))):
+            gs = [(graphs + [big])[i] for i in sel]
+            ss = [(srcs + [0])[i] for i in sel]
+            dists, rounds = P.sssp_solve_batch([hs[i] for i in sel], ss)
+            for g, s, d, r in zip(gs, ss, dists, rounds):
+                ref = oracle.round_r(g, s)
+                assert np.array_equal(d, ref.dist) and int(r) == ref.rounds
+    finally:
+        for h in hs:
+            P.sssp_destroy(h)
+
+
 def test_batch_many_sources_one_graph(sssp_lib):
     P = sssp_lib
     g = gg.rmat(13, 16, 1, 255, 4)

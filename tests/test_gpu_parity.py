@@ -14,6 +14,8 @@ from tests.golden.fixtures import worked_example
 pytestmark = pytest.mark.gpu
 
 INF = np.uint64(0xFFFFFFFFFFFFFFFF)
+# Both per-vertex state layouts: 32-byte records and 16-byte records.
+LAYOUTS = pytest.mark.parametrize("layout", [1, 2], ids=["wide", "compact"])
 
 
 def make_opts(P, **kw):
@@ -53,24 +55,26 @@ def assert_parity(P, g, s, mode=oracle.RULE_THR, **opt):
 
 # ------------------------------------------------------------- fixtures
 
+@LAYOUTS
 @pytest.mark.parametrize("variant", ["A", "B", "threshold", "jacobi", "inclamp"])
-def test_worked_examples(sssp_lib, variant):
+def test_worked_examples(sssp_lib, variant, layout):
     ex = worked_example()[variant]
     g = gg.from_edges(ex["n"], ex["edges"])
-    out, _ = assert_parity(sssp_lib, g, ex["source"])
+    out, _ = assert_parity(sssp_lib, g, ex["source"], layout=layout)
     assert out["dist"].tolist() == ex["dist"]
     assert out["fixed_round"].tolist() == ex["fixed_round"]
     assert out["info"]["rounds"] == ex["rounds"]
 
 
-def test_random_4096_config(sssp_lib):
+@LAYOUTS
+def test_random_4096_config(sssp_lib, layout):
     """Random directed graph n = 4096, 8 distinct out-edges, w in [1, 100], s = 0."""
     g = gg.random_graph(4096, 8, 1, 100, 1812_10499)
-    assert_parity(sssp_lib, g, 0)
-    assert_parity(sssp_lib, g, 0, mode=oracle.RULE_MIND)
-    assert_parity(sssp_lib, g, 0, loop_mode=sssp_lib.SSSP_LOOP_HOST)
-    assert_parity(sssp_lib, g, 0, loop_mode=sssp_lib.SSSP_LOOP_GRAPH)
-    assert_parity(sssp_lib, g, 0, loop_mode=sssp_lib.SSSP_LOOP_PERSISTENT)
+    assert_parity(sssp_lib, g, 0, layout=layout)
+    assert_parity(sssp_lib, g, 0, mode=oracle.RULE_MIND, layout=layout)
+    assert_parity(sssp_lib, g, 0, loop_mode=sssp_lib.SSSP_LOOP_HOST, layout=layout)
+    assert_parity(sssp_lib, g, 0, loop_mode=sssp_lib.SSSP_LOOP_GRAPH, layout=layout)
+    assert_parity(sssp_lib, g, 0, loop_mode=sssp_lib.SSSP_LOOP_PERSISTENT, layout=layout)
 
 
 @pytest.mark.parametrize("mode", ["graph", "host"])
@@ -82,24 +86,28 @@ def test_loop_modes_rmat(sssp_lib, mode):
     assert_parity(sssp_lib, g, s, loop_mode=lm, hub_degree=16, chunk_edges=64)
 
 
+@LAYOUTS
 @pytest.mark.parametrize("seed", range(6))
-def test_random_graphs_many_tiles(sssp_lib, seed):
+def test_random_graphs_many_tiles(sssp_lib, seed, layout):
     n = [37, 300, 1000, 5000, 20000, 70001][seed]
     g = gg.random_var_graph(n, 1, 12, 1, [3, 100, 1000, 10, 255, 10000][seed], seed)
     s = int(gg.uniform(seed, 0, 1, 0, n - 1)[0])
-    assert_parity(sssp_lib, g, s)
+    assert_parity(sssp_lib, g, s, layout=layout)
 
 
+@LAYOUTS
 @pytest.mark.parametrize("hub,chunk", [(4, 32), (8, 64), (31, 32), (32, 96)])
-def test_hub_paths(sssp_lib, hub, chunk):
+def test_hub_paths(sssp_lib, hub, chunk, layout):
     """Small hub thresholds push many vertices through the chunked paths."""
     g = gg.rmat(13, 8, 1, 255, hub)
     s = int(np.argmax(g.out_degree()))
-    assert_parity(sssp_lib, g, s, hub_degree=hub, chunk_edges=chunk)
-    assert_parity(sssp_lib, g, s, mode=oracle.RULE_MIND, hub_degree=hub, chunk_edges=chunk)
+    assert_parity(sssp_lib, g, s, hub_degree=hub, chunk_edges=chunk, layout=layout)
+    assert_parity(sssp_lib, g, s, mode=oracle.RULE_MIND, hub_degree=hub, chunk_edges=chunk,
+                  layout=layout)
 
 
-def test_degree_boundaries(sssp_lib):
+@LAYOUTS
+def test_degree_boundaries(sssp_lib, layout):
     """Degrees around the hub threshold (8) and chunk size (32)."""
     edges = []
     n = 400
@@ -116,8 +124,8 @@ def test_degree_boundaries(sssp_lib):
     for j in range(1, k):
         edges.append((j, (j * 7) % k, 3))
     g = gg.from_edges(n, [e for e in edges if e[0] != e[1]])
-    assert_parity(sssp_lib, g, 0, hub_degree=8, chunk_edges=32)
-    assert_parity(sssp_lib, g, 0)
+    assert_parity(sssp_lib, g, 0, hub_degree=8, chunk_edges=32, layout=layout)
+    assert_parity(sssp_lib, g, 0, layout=layout)
 
 
 def test_star_hub_in_and_out(sssp_lib):
@@ -153,7 +161,8 @@ def test_edge_cases(sssp_lib):
     assert out["dist"].tolist() == [0, 2, 6, 7]
 
 
-def test_per_round_state(sssp_lib):
+@LAYOUTS
+def test_per_round_state(sssp_lib, layout):
     """After every round r the device state equals the oracle's: D, C and the
     rounds in which vertices were fixed (the state read with max_rounds = r)."""
     g = gg.random_var_graph(700, 1, 6, 1, 50, 11)
@@ -161,7 +170,7 @@ def test_per_round_state(sssp_lib):
     oracle.round_r(g, 0, on_round=lambda r, thr, mD, D, C, F: snaps.append(
         (D.copy(), C.copy(), F.copy())))
     for r, (D, C, F) in enumerate(snaps, start=1):
-        out = gpu_solve(sssp_lib, g, 0, max_rounds=r)
+        out = gpu_solve(sssp_lib, g, 0, max_rounds=r, layout=layout)
         assert out["info"]["rounds"] == r
         assert np.array_equal(out["dist"], D), f"D after round {r}"
         assert np.array_equal(out["lower"], C), f"C after round {r}"
@@ -178,9 +187,31 @@ def test_unit_grid_closed_form(sssp_lib):
     assert out["info"]["rounds"] == 299 + 199 + 1
 
 
-def test_weighted_grid_and_dag(sssp_lib):
-    assert_parity(sssp_lib, gg.grid(200, 150, 1, 10000, 3), 0)
-    assert_parity(sssp_lib, gg.dag(64, 512, 8, 4, 1, 1000, 2), 0)
+@LAYOUTS
+def test_weighted_grid_and_dag(sssp_lib, layout):
+    assert_parity(sssp_lib, gg.grid(200, 150, 1, 10000, 3), 0, layout=layout)
+    assert_parity(sssp_lib, gg.dag(64, 512, 8, 4, 1, 1000, 2), 0, layout=layout)
+
+
+def test_layout_selection(sssp_lib):
+    """The automatic layout is compact exactly when n * max weight < 2^31 - 1;
+    a graph whose distances need more than 31 bits solves with wide records,
+    and asking for compact records there is refused."""
+    P = sssp_lib
+    small = gg.random_graph(4096, 8, 1, 100, 5)
+    big = gg.random_graph(4096, 8, 1 << 19, (1 << 20) - 1, 5)     # 4096 * 2^20 = 2^32
+    for g, want in ((small, P.SSSP_LAYOUT_COMPACT), (big, P.SSSP_LAYOUT_WIDE)):
+        h = P.sssp_create(g.n, g.row_ptr, g.col, g.w)
+        try:
+            assert P.sssp_layout(h) == want
+        finally:
+            P.sssp_destroy(h)
+    out, ref = assert_parity(P, big, 0)
+    assert int(ref.dist[ref.dist != INF].max()) >= 1 << 21
+    with pytest.raises(P.SsspError) as e:
+        P.sssp_create(big.n, big.row_ptr, big.col, big.w,
+                      options=make_opts(P, layout=P.SSSP_LAYOUT_COMPACT))
+    assert e.value.code == -4
 
 
 def test_solve_and_solve_device(sssp_lib):
