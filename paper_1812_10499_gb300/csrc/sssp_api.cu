@@ -337,6 +337,12 @@ int create_impl(sssp_graph* h, u32 n, u64 m, const u64* row_ptr, const u32* col,
     const bool fits = (unsigned __int128)n * wmax < kNarrowLimit;
     if (h->opt.layout == SSSP_LAYOUT_COMPACT && !fits) return SSSP_E_OVERFLOW;
     h->narrow = fits && h->opt.layout != SSSP_LAYOUT_WIDE;
+    if (h->narrow) {
+        // The compact kernels keep the distance in the upper half of the
+        // packed D word.
+        h->vbits = 32;
+        h->dinf = (~0ull) >> 32;
+    }
 
     std::vector<u64> o2, c2;
     std::vector<u32> i2, w2, r2, wi2;
@@ -541,13 +547,14 @@ int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist
             g[i]->opt.chunk_edges != h0->opt.chunk_edges || g[i]->opt.rule != h0->opt.rule)
             return SSSP_E_INVAL;
         if (sources[i] >= g[i]->n) return SSSP_E_SOURCE_RANGE;
-        vbits = std::max(vbits, g[i]->vbits);
+        vbits = std::max(vbits, std::max<u32>(1, bits_for((u64)g[i]->n - 1)));
         narrow = narrow && g[i]->narrow;
         npages += ((u64)g[i]->n + (1u << kPageShift) - 1) >> kPageShift;
         capH += std::max(g[i]->hubs_in, g[i]->hubs_out);
     }
     const u64 nrec = npages << kPageShift;
     if (nrec >= 0xFFFFFFFFull) return SSSP_E_NOMEM;   // list entries are 32-bit record ids
+    if (narrow) vbits = 32;                           // compact kernels: distance in the upper half
     const u64 dinf = (~0ull) >> vbits;
     for (u32 i = 0; i < k; ++i)
         if (g[i]->wmax && (unsigned __int128)g[i]->n * g[i]->wmax >= (unsigned __int128)dinf)

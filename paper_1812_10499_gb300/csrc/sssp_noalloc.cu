@@ -72,7 +72,10 @@ extern "C" int sssp_solve_noalloc(uint32_t n, const uint64_t* out_off, const uin
     if (n == 0 || !out_off || !in_off || !dist_dev) return SSSP_E_INVAL;
     if (n > kNoAllocMaxVertices) return SSSP_E_NOALLOC_LIMIT;
     if (source >= n) return SSSP_E_SOURCE_RANGE;
-    const u32 vbits = std::max<u32>(1, bits_for((u64)n - 1));
+    // Compact 16-byte records when every finite distance fits 31 bits; their
+    // kernels keep the distance in the upper half of the packed D word.
+    const bool narrow = (unsigned __int128)n * max_weight < kNarrowLimit;
+    const u32 vbits = narrow ? 32u : std::max<u32>(1, bits_for((u64)n - 1));
     const u64 dinf = (~0ull) >> vbits;
     if ((unsigned __int128)n * max_weight >= (unsigned __int128)dinf) return SSSP_E_OVERFLOW;
     int dev = 0;
@@ -85,8 +88,6 @@ extern "C" int sssp_solve_noalloc(uint32_t n, const uint64_t* out_off, const uin
     // Lay the working state out in the scratch (no allocation).
     size_t off = 0;
     RoundParams P{};
-    // Compact 16-byte records when every finite distance fits 31 bits.
-    const bool narrow = (unsigned __int128)n * max_weight < kNarrowLimit;
     if (narrow) P.recn = carve<VRecN>(base, off, n);
     else P.rec = carve<VRec>(base, off, n);
     P.fround = carve<int>(base, off, n);

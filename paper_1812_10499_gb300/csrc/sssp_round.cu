@@ -102,6 +102,7 @@ struct DcSlot {                         // wide, k_cupdate: (D, C[cur])
     }
     __device__ __forceinline__ u64 d() const { return v.x; }
     __device__ __forceinline__ u64 c(u32) const { return v.y; }
+    __device__ __forceinline__ bool fixed(u32) const { return (v.y & kFixed) != 0; }
 };
 struct RecSlot {                        // wide, k_relax: the whole record
     ulonglong2 lo, hi;
@@ -111,6 +112,7 @@ struct RecSlot {                        // wide, k_relax: the whole record
     }
     __device__ __forceinline__ u64 d() const { return lo.x; }
     __device__ __forceinline__ u64 c(u32 cur) const { return cur ? hi.x : lo.y; }
+    __device__ __forceinline__ bool fixed(u32 cur) const { return (c(cur) & kFixed) != 0; }
     __device__ __forceinline__ u32 outw() const { return (u32)hi.y; }
     __device__ __forceinline__ u32 indeg() const { return (u32)(hi.y >> 32); }
 };
@@ -118,14 +120,48 @@ struct NSlot {                          // compact: the whole 16-byte record
     ulonglong2 v;
     __device__ __forceinline__ void issue(const VRecN* p, u32) { cp_async_16(&v, p); }
     __device__ __forceinline__ u64 d() const { return v.x; }
-    __device__ __forceinline__ u64 c(u32 cur) const { return widen_c((u32)(v.y >> (32 * cur))); }
+    __device__ __forceinline__ u32 c32(u32 cur) const {
+        return cur ? (u32)(v.y >> 32) : (u32)v.y;
+    }
+    __device__ __forceinline__ u64 c(u32 cur) const { return widen_c(c32(cur)); }
+    __device__ __forceinline__ bool fixed(u32 cur) const { return (c32(cur) & kFixedN) != 0; }
 };
+
+// Clamps an in-neighbour bound term can take: lb(x) uses threshold (rule 0)
+// or minD (rule 1) of the in-neighbour's query.
+struct Bounds64 {
+    u64 thr, minD;
+};
+struct Bounds32 {
+    u32 thr, minD;
+};
+constexpr u32 kInf31 = kFixedN - 1;     // compact-layout term infinity
+
+// lb(x): the lower bound an in-neighbour contributes (Lemmas 7 and 8); with
+// rule 1 the printed SP_4 step 4 clamp (minD for unfixed vertices).
+template <class S>
+__device__ __forceinline__ u64 lb_of(const RoundParams& P, const S& v, u32 cur, u64 thr,
+                                     u64 minD) {
+    const u64 dx = v.d() >> P.vbits;          // infinity maps to dinf
+    const u64 cw = v.c(cur);
+    const u64 cx = cw & kCMask;
+    if (P.rule == 0) return umax64(cx, umin64(dx, thr));
+    return (cw & kFixed) ? cx : umax64(cx, minD);
+}
 
 struct WideL {
     typedef VRec Rec;
     typedef RecSlot RSlot;
     typedef DcSlot CSlot;
     static constexpr bool kNarrow = false;
+    // Eq. (1) term lb(x) + w of one in-edge, clamped to the distance infinity.
+    typedef u64 Term;
+    typedef Bounds64 Bounds;
+    static constexpr u64 kTermInf = kInf64;
+    __device__ static Bounds bounds(u64 thr, u64 minD) { return Bounds64{thr, minD}; }
+    __device__ static Term term(const RoundParams& P, const CSlot& v, u32 cur, u32 w, Bounds b) {
+        return umin64(lb_of(P, v, cur, b.thr, b.minD) + w, P.dinf);
+    }
     __device__ static Rec* rec(const RoundParams& P) { return P.rec; }
     // (D word, wide C word of parity cur)
     __device__ static ulonglong2 ld_dc(const Rec* p, u32 cur) {
@@ -139,6 +175,28 @@ struct NarrowL {
     typedef NSlot RSlot;
     typedef NSlot CSlot;
     static constexpr bool kNarrow = true;
+    // The same term in 32-bit arithmetic.  Here the packed D word holds the
+    // distance in its upper half (32 parent bits) and every finite value is
+    // below 2^31 - 1, so lb(x) <= kInf31 and lb(x) + w cannot wrap.  Terms are
+    // clamped to kInf31; a clamped term never decides the minimum, because an
+    // active vertex y always has a fixed in-neighbour whose term is exactly
+    // D[y] < kInf31 (D[y] is the least D[x] + w over the fixed in-neighbours,
+    // all of which have relaxed their edges into y).
+    typedef u32 Term;
+    typedef Bounds32 Bounds;
+    static constexpr u32 kTermInf = kInf31;
+    __device__ static Bounds bounds(u64 thr, u64 minD) {
+        return Bounds32{(u32)umin64(thr, kInf31), (u32)umin64(minD, kInf31)};
+    }
+    __device__ static Term term(const RoundParams& P, const CSlot& v, u32 cur, u32 w, Bounds b) {
+        const u32 d = (u32)(v.v.x >> 32);
+        const u32 cw = v.c32(cur);
+        const u32 c = cw & ~kFixedN;
+        u32 lb;
+        if (P.rule == 0) lb = max(c, min(d, b.thr));
+        else lb = (cw & kFixedN) ? c : max(c, b.minD);
+        return min(lb + w, kInf31);
+    }
     __device__ static Rec* rec(const RoundParams& P) { return P.recn; }
     __device__ static ulonglong2 ld_dc(const Rec* p, u32 cur) {
         const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(p);
@@ -164,17 +222,6 @@ __device__ __forceinline__ u32 warp_incl_scan(u32 x, u32 lane) {
         if (lane >= d) x += y;
     }
     return x;
-}
-
-// Largest lane i with excl_i <= j (excl is non-decreasing over lanes).
-__device__ __forceinline__ u32 find_owner(u32 excl, u32 j) {
-    u32 lo = 0;
-#pragma unroll
-    for (u32 step = 16; step >= 1; step >>= 1) {
-        u32 e = __shfl_sync(kFull, excl, lo + step);
-        if (e <= j) lo += step;
-    }
-    return lo;
 }
 
 __device__ __forceinline__ u64 warp_min64(u64 v) {
@@ -344,6 +391,7 @@ __device__ __forceinline__ void run_pipeline(u32 nbat, IA issue_adj, ID issue_dc
 // position excl_i of the tile's concatenated edge space.
 struct Tile {
     u32 excl, total, nzmask;
+    u32 hc;                              // segment heads in positions already issued
     u64 eaddr;                           // lane's first edge (uint2*)
     u64 pol;                             // L2 policy of the adjacency copies
 };
@@ -357,28 +405,30 @@ __device__ __forceinline__ Tile make_tile(WarpStage<S>& st, u32 deg, u64 eaddr, 
     t.eaddr = eaddr;
     t.pol = policy_evict_first();
     t.nzmask = __ballot_sync(kFull, deg > 0);
+    t.hc = 0;
     if (deg > 0) st.nz[__popc(t.nzmask & ((1u << lane) - 1u))] = (unsigned char)lane;
     __syncwarp();
     return t;
 }
 
-// Owner lane of position j0 + lane of a tile: the owner of the row's first
-// position plus the number of segment heads (an owner's first edge) at or
-// before the lane, found with one OR-reduction of the heads.
+// Owner lane of position j0 + lane of a tile.  Rows are issued in order, so
+// the owner's rank among the lanes with edges is the number of segment
+// heads (an owner's first edge) at positions up to j0 + lane, minus one:
+// the heads before j0 are carried in t.hc, those in the row come from one
+// OR-reduction.  Position 0 is always a head.
 template <class S>
-__device__ __forceinline__ u32 row_owner(const WarpStage<S>& st, const Tile& t, u32 j0, u32 deg,
+__device__ __forceinline__ u32 row_owner(const WarpStage<S>& st, Tile& t, u32 j0, u32 deg,
                                          u32 lane) {
     const bool hd = deg > 0 && t.excl >= j0 && t.excl < j0 + 32;
     const u32 heads = __reduce_or_sync(kFull, hd ? (1u << (t.excl - j0)) : 0u);
-    const u32 o0 = find_owner(t.excl, j0);
-    const u32 r0 = __popc(t.nzmask & ((1u << o0) - 1u));
-    const u32 rank = r0 + __popc(heads & lanemask_le(lane)) - (heads & 1u);
+    const u32 rank = t.hc + __popc(heads & lanemask_le(lane)) - 1u;
+    t.hc += __popc(heads);
     return st.nz[rank & 31u];
 }
 
 // Starts copying edges [b0, b0 + kB) of a tile into adjacency slot s.
 template <class S>
-__device__ __forceinline__ void issue_tile_adj(WarpStage<S>& st, const Tile& t, u32 s, u32 b0,
+__device__ __forceinline__ void issue_tile_adj(WarpStage<S>& st, Tile& t, u32 s, u32 b0,
                                                u32 deg, u32 lane) {
 #pragma unroll
     for (u32 i = 0; i < kBI; ++i) {
@@ -448,7 +498,12 @@ __device__ __forceinline__ void relax_batch(const RoundParams& P,
         const u32 idx = 32 * i + lane;
         const bool ev = idx < nb;
         const u32 own = (per_owner && ev) ? st.own[as][idx] : lane;
-        const u64 odx = per_owner ? __shfl_sync(kFull, dx, own) : dx;
+        u64 odx = dx;
+        if (per_owner) {
+            // Compact layout: distances are below 2^31, one 32-bit shuffle.
+            if (L::kNarrow) odx = __shfl_sync(kFull, (u32)dx, own);
+            else odx = __shfl_sync(kFull, dx, own);
+        }
         const u32 ox = per_owner ? __shfl_sync(kFull, xloc, own) : xloc;
         u64 ob = gbase;
         if (MULTI && per_owner) ob = __shfl_sync(kFull, gbase, own);
@@ -460,10 +515,10 @@ __device__ __forceinline__ void relax_batch(const RoundParams& P,
             atomicOr(&P.ctl->error, 8u);
             continue;
         }
-        cand[i] = (dd << P.vbits) | ox;
+        cand[i] = (dd << (L::kNarrow ? 32u : P.vbits)) | ox;
         yl[i] = e.x;
         gy[i] = (u32)(ob + e.x);
-        if (!(v.c(cur) & kFixed) && cand[i] < v.d()) old[i] = atomicMin(&rec[gy[i]].dp, cand[i]);
+        if (!v.fixed(cur) && cand[i] < v.d()) old[i] = atomicMin(&rec[gy[i]].dp, cand[i]);
         a.edges++;
     }
 #pragma unroll
@@ -486,7 +541,7 @@ __device__ __forceinline__ void relax_batch(const RoundParams& P,
                 ow = v.outw();
                 indeg = v.indeg();
             }
-            const u64 dd = cand[i] >> P.vbits;
+            const u64 dd = cand[i] >> (L::kNarrow ? 32u : P.vbits);
             fold<MULTI>(P, oinst, cur, dd, ow == kNoOutW ? P.dinf : dd + ow, a);
         }
         const bool sm = fresh && indeg <= P.hub;
@@ -516,7 +571,7 @@ __device__ void relax_small(const RoundParams& P, WarpStage<typename L::RSlot>& 
         dx = L::ld_dc(rx, cur).y & kCMask;          // C = D for a fixed vertex
         a.visits++;
     }
-    const Tile tl = make_tile(st, deg, (u64)(adj + b), lane);
+    Tile tl = make_tile(st, deg, (u64)(adj + b), lane);
     run_pipeline(
         (tl.total + kB - 1) / kB,
         [&](u32 bb, u32 s) { issue_tile_adj(st, tl, s, bb * kB, deg, lane); },
@@ -638,18 +693,6 @@ __global__ void __launch_bounds__(256, 3) k_relax(RoundParams P) {
 
 // ---------------------------------------------------------------- cupdate
 
-// lb(x): the lower bound an in-neighbour contributes (Lemmas 7 and 8); with
-// rule 1 the printed SP_4 step 4 clamp (minD for unfixed vertices).
-template <class S>
-__device__ __forceinline__ u64 lb_of(const RoundParams& P, const S& v, u32 cur, u64 thr,
-                                     u64 minD) {
-    const u64 dx = v.d() >> P.vbits;          // infinity maps to dinf
-    const u64 cw = v.c(cur);
-    const u64 cx = cw & kCMask;
-    if (P.rule == 0) return umax64(cx, umin64(dx, thr));
-    return (cw & kFixed) ? cx : umax64(cx, minD);
-}
-
 // Decision for one active vertex after its Eq. (1) minimum m is known.
 __device__ __forceinline__ u64 decide(const RoundParams& P, u64 dy, u64 cy, u64 m, u64 thr,
                                       u64 minD, bool& fix) {
@@ -690,7 +733,8 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
         outw = outw_of<L>(d, rec + g, yloc);
     }
     smin[lane] = kInf64;
-    const Tile tl = make_tile(st, deg, (u64)(in_adj + ib), lane);
+    const typename L::Bounds bd = L::bounds(thr, minD);
+    Tile tl = make_tile(st, deg, (u64)(in_adj + ib), lane);
     run_pipeline(
         (tl.total + kB - 1) / kB,
         [&](u32 b, u32 s) { issue_tile_adj(st, tl, s, b * kB, deg, lane); },
@@ -705,15 +749,13 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
                 const u32 sidx = 32 * i + lane;
                 const bool ev = sidx < nb;
                 const u32 own = ev ? st.own[as][sidx] : 0u;
-                u64 othr = thr, omin = minD;
+                typename L::Bounds ob = bd;
                 if (MULTI) {
-                    othr = __shfl_sync(kFull, thr, own);
-                    omin = __shfl_sync(kFull, minD, own);
+                    ob.thr = __shfl_sync(kFull, bd.thr, own);
+                    ob.minD = __shfl_sync(kFull, bd.minD, own);
                 }
-                u64 val = kInf64;
-                if (ev)
-                    val = umin64(lb_of(P, st.dc[ds][sidx], cur, othr, omin) + st.adj[as][sidx].y,
-                                 P.dinf);
+                typename L::Term val = L::kTermInf;
+                if (ev) val = L::term(P, st.dc[ds][sidx], cur, st.adj[as][sidx].y, ob);
                 // Segmented min over lanes sharing an owner: owners are
                 // contiguous, a lane's segment starts at the last owner
                 // change at or before it.
@@ -722,11 +764,11 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
                 const u32 span = lane - (31 - __clz(brk & lanemask_le(lane)));
 #pragma unroll
                 for (u32 dd = 1; dd < 32; dd <<= 1) {
-                    const u64 ov = __shfl_up_sync(kFull, val, dd);
-                    if (dd <= span) val = umin64(val, ov);
+                    const typename L::Term ov = __shfl_up_sync(kFull, val, dd);
+                    if (dd <= span) val = min(val, ov);
                 }
                 const bool tail = ev && (lane == 31 || ((brk >> (lane + 1)) & 1u));
-                if (tail) smin[own] = umin64(smin[own], val);
+                if (tail) smin[own] = umin64(smin[own], (u64)val);
                 __syncwarp();
             }
         });
@@ -781,7 +823,8 @@ __device__ void cup_hub(const RoundParams& P, WarpStage<typename L::CSlot>& st, 
     const u64 ib = d.in_off[yloc], ie = d.in_off[yloc + 1];
     const u64 cb = ib + (u64)k * P.chunk;
     const u64 ce = umin64(cb + P.chunk, ie);
-    u64 val = kInf64;
+    const typename L::Bounds bd = L::bounds(thr, minD);
+    typename L::Term tv = L::kTermInf;
     const u32 n = ce > cb ? (u32)(ce - cb) : 0u;
     run_pipeline(
         (n + kB - 1) / kB,
@@ -794,13 +837,10 @@ __device__ void cup_hub(const RoundParams& P, WarpStage<typename L::CSlot>& st, 
 #pragma unroll
             for (u32 i = 0; i < kBI; ++i) {
                 const u32 sidx = 32 * i + lane;
-                if (sidx < nb)
-                    val = umin64(val, umin64(lb_of(P, st.dc[ds][sidx], cur, thr, minD) +
-                                                 st.adj[as][sidx].y,
-                                             P.dinf));
+                if (sidx < nb) tv = min(tv, L::term(P, st.dc[ds][sidx], cur, st.adj[as][sidx].y, bd));
             }
         });
-    val = warp_min64(val);
+    const u64 val = warp_min64((u64)tv);
     if (lane != 0) return;
     a.edges += ce - cb;
     atomicMin(&P.L.hubmin[lo], val);
