@@ -41,7 +41,8 @@ int scan_excl(u64* in, u64 cnt, u64* out, u64* tmp, cudaStream_t st) {
     return SSSP_OK;
 }
 
-// Builds the device-side while loop: body = relax -> cupdate.
+// Builds the device-side while loop: body = relax -> cupdate -> tail (the
+// cluster kernel that runs the following rounds while they are small).
 int build_loop(Context& c) {
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0));
@@ -78,6 +79,20 @@ int build_loop(Context& c) {
         kp.func = const_cast<void*>(cupdate_fn(c.multi, c.narrow));
         kp.sharedMemBytes = (unsigned)cupdate_smem_bytes(c.narrow);
         e = cudaGraphAddKernelNode(&n2, body, &n1, 1, &kp);
+    }
+    if (e == cudaSuccess && c.tail_ctas) {
+        cudaGraphNode_t n3;
+        kp.func = const_cast<void*>(tail_fn(c.multi, c.narrow));
+        kp.gridDim = dim3(c.tail_ctas);
+        kp.sharedMemBytes = (unsigned)solve_smem_bytes(c.narrow);
+        e = cudaGraphAddKernelNode(&n3, body, &n2, 1, &kp);
+        if (e == cudaSuccess) {
+            cudaLaunchAttributeValue v{};
+            v.clusterDim.x = c.tail_ctas;
+            v.clusterDim.y = 1;
+            v.clusterDim.z = 1;
+            e = cudaGraphKernelNodeSetAttribute(n3, cudaLaunchAttributeClusterDimension, &v);
+        }
     }
     cudaGraphExec_t x = nullptr;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
@@ -218,12 +233,14 @@ int init_single_context(sssp_graph* h) {
     c.nslots = 1;
     c.grid = h->grid;
     c.grid_solve = h->grid_solve;
+    c.tail_ctas = h->tail_ctas;
     RoundParams& P = c.P;
+    P.tail_items = h->tail_items;
     P.g.out_off = h->out_off;
     P.g.out_adj = h->out_adj;
     P.g.in_off = h->in_off;
     P.g.in_adj = h->in_adj;
-    P.g.outw = h->outw;
+    P.g.outw = h->narrow ? h->outw_pack : h->outw;
     P.g.base = 0;
     P.g.n = h->n;
     P.g.source = 0;
@@ -369,6 +386,11 @@ int create_impl(sssp_graph* h, u32 n, u64 m, const u64* row_ptr, const u32* col,
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
         h->grid_solve = std::max(1, sms) * std::max(1, solve_blocks_per_sm(kThreads));
+        // Small rounds run in one thread-block cluster (SSSP_TAIL_ITEMS: most
+        // work items per phase of such a round; 0 disables it).
+        h->tail_items = kDefaultTailItems;
+        if (const char* v = getenv("SSSP_TAIL_ITEMS")) h->tail_items = (u32)strtoul(v, nullptr, 10);
+        h->tail_ctas = h->tail_items ? tail_cluster_ctas() : 0;
     }
     Pool& gp = h->gpool;
     RC(gp.get(&h->out_off, (size_t)n + 1));
@@ -419,6 +441,12 @@ int create_impl(sssp_graph* h, u32 n, u64 m, const u64* row_ptr, const u32* col,
     }
     k_outw<<<h->grid, kThreads, 0, h->stream>>>(h->out_off, h->out_adj, n, h->outw);
     CK(cudaGetLastError());
+    if (h->narrow) {
+        RC(gp.get(&h->outw_pack, n));
+        k_pack_outw<<<h->grid, kThreads, 0, h->stream>>>(h->outw, h->in_off, n, h->opt.hub_degree,
+                                                         h->outw_pack);
+        CK(cudaGetLastError());
+    }
     {
         Pool tmp;
         tmp.al = gp.al;
@@ -507,7 +535,9 @@ int ensure_batch(sssp_graph* h0, u64 nrec, u32 nslots, u32 npages, u64 capH) {
     c->npages = npages;
     c->grid = h0->grid;
     c->grid_solve = h0->grid_solve;
+    c->tail_ctas = h0->tail_ctas;
     RoundParams& P = c->P;
+    P.tail_items = h0->tail_items;
     RC(c->pool.get(&c->rec_store, nrec));   // 32-byte slots; the compact layout uses half
     RC(c->pool.get(&P.fround, nrec));
     RC(c->pool.get(&P.ctl, 1));
@@ -577,13 +607,14 @@ int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist
     c.narrow = narrow;
     P.rec = narrow ? nullptr : c.rec_store;
     P.recn = narrow ? reinterpret_cast<VRecN*>(c.rec_store) : nullptr;
-    P.g = InstDesc{g[0]->out_off, g[0]->out_adj, g[0]->in_off, g[0]->in_adj, g[0]->outw, 0,
-                   g[0]->n, sources[0]};
+    P.g = InstDesc{g[0]->out_off, g[0]->out_adj, g[0]->in_off, g[0]->in_adj,
+                   narrow ? g[0]->outw_pack : g[0]->outw, 0, g[0]->n, sources[0]};
     u64 page = 0;
     for (u32 i = 0; i < k; ++i) {
         const sssp_graph* gi = g[i];
-        c.h_desc[i] = InstDesc{gi->out_off, gi->out_adj, gi->in_off, gi->in_adj, gi->outw,
-                               page << kPageShift, gi->n, sources[i]};
+        c.h_desc[i] = InstDesc{gi->out_off, gi->out_adj, gi->in_off, gi->in_adj,
+                               narrow ? gi->outw_pack : gi->outw, page << kPageShift, gi->n,
+                               sources[i]};
         const u64 np = ((u64)gi->n + (1u << kPageShift) - 1) >> kPageShift;
         for (u64 p = 0; p < np; ++p) c.h_pages[page + p] = i;
         page += np;

@@ -89,6 +89,9 @@ struct __align__(16) Ctl {
     u32 loop_iters;     // loop bodies started (watchdog against a stuck loop)
     u32 bar_count;      // grid barrier of the persistent kernel: arrivals
     u32 bar_gen;        // grid barrier generation (bumped on release)
+    u32 tail_go;        // cluster tail kernel: run the next step (set before a cluster barrier)
+    u32 cup_only;       // the round's relaxation is done (by the tail kernel): the next
+                        // full-grid relax launch is skipped
     u32 pad1;
     u64 stats[4];       // out-edges scanned, in-edges scanned, active visits, frontier visits
 };
@@ -124,7 +127,7 @@ struct RoundParams {
     u32 page_shift;
     u32 trace_cap;              // entries of `trace`
     u32 trace_base;             // round number of the first traced round
-    u32 pad2;
+    u32 tail_items;             // cluster tail kernel: most work items a round may have
     unsigned long long cond;    // cudaGraphConditionalHandle of the device loop, 0 = none
     u64* trace;                 // persistent kernel: globaltimer at launch, then at the end of
                                 // every phase (2 per round); nullable

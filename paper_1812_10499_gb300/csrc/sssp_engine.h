@@ -18,6 +18,8 @@ namespace sssp {
 const void* relax_fn(bool multi, bool narrow);
 const void* cupdate_fn(bool multi, bool narrow);
 const void* solve_fn(bool multi, bool narrow);
+const void* tail_fn(bool multi, bool narrow);
+u32 tail_cluster_ctas();
 size_t solve_smem_bytes(bool narrow);
 int solve_blocks_per_sm(int threads);
 size_t relax_smem_bytes(bool narrow);
@@ -39,6 +41,7 @@ __global__ void k_count_in(const uint2* adj, u64 m, u64* cnt);
 __global__ void k_scatter_in(const u64* out_off, const uint2* out_adj, u32 n, u64* cursor,
                              uint2* in_adj);
 __global__ void k_outw(const u64* out_off, const uint2* out_adj, u32 n, u32* outw);
+__global__ void k_pack_outw(const u32* outw, const u64* in_off, u32 n, u32 hub, u32* out);
 __global__ void k_count_hubs(const u64* out_off, const u64* in_off, u32 n, u32 hub, u32* cnt);
 __global__ void k_scan_tiles(const u64* in, u64 cnt, u64* tile_sums);
 __global__ void k_scan_sums(u64* tile_sums, u32 ntiles);
@@ -53,6 +56,7 @@ constexpr u32 kThreads = 256;
 constexpr u32 kPageShift = 10;
 constexpr u32 kDefaultHub = 256;
 constexpr u32 kDefaultChunk = 512;
+constexpr u32 kDefaultTailItems = 512;
 
 #define CK(call)                                       \
     do {                                               \
@@ -149,6 +153,7 @@ struct Context {
     cudaGraphExec_t exec = nullptr;
     int grid = 0;
     int grid_solve = 0;              // co-resident grid of the persistent kernel
+    u32 tail_ctas = 0;               // cluster size of the tail kernel, 0 = not in the loop
     // Per-kernel event timing (sssp_profile).
     bool prof = false;
     std::vector<cudaEvent_t> ev;
@@ -200,9 +205,12 @@ struct sssp_graph {
     u64* in_off = nullptr;
     uint2* in_adj = nullptr;
     u32* outw = nullptr;
+    u32* outw_pack = nullptr;        // compact layout: outWeight | in-hub flag (k_pack_outw)
     cudaStream_t stream = nullptr;   // internal stream for setup and host-pointer solves
     int grid = 0;
     int grid_solve = 0;
+    u32 tail_ctas = 0;               // see Context::tail_ctas
+    u32 tail_items = 0;
     sssp::engine::Context single;    // single-query context
     sssp::engine::Context* batch = nullptr;  // multi-query context (grown on demand)
     std::mutex mu;

@@ -120,6 +120,8 @@ extern "C" int sssp_solve_noalloc(uint32_t n, const uint64_t* out_off, const uin
     CK(cudaMemsetAsync(P.L.hubmin, 0xFF, sizeof(u64) * n, st));
     CK(cudaMemsetAsync(P.L.hubcnt, 0, sizeof(u32) * n, st));
     k_outw<<<grid, kThreads, 0, st>>>(P.g.out_off, P.g.out_adj, n, outw);
+    if (narrow)   // compact kernels read outWeight with the in-hub flag (in place)
+        k_pack_outw<<<grid, kThreads, 0, st>>>(outw, P.g.in_off, n, kDefaultHub, outw);
     k_init_records<<<grid, kThreads, 0, st>>>(P.rec, P.recn, P.fround, outw, P.g.in_off, n);
     k_reset_ctl<<<1, 32, 0, st>>>(P.ctl, 1, n + 2);
     CK(cudaGetLastError());

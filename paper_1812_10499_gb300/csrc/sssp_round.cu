@@ -32,8 +32,17 @@ namespace sssp {
 
 constexpr u32 kFull = 0xFFFFFFFFu;
 constexpr u32 kWarps = 8;       // warps per CTA (256 threads)
+constexpr u32 kSmallGrid = 32;  // grids up to this many CTAs run latency-bound rounds
 constexpr u32 kQCap = 64;       // entries of a warp append buffer
-constexpr u32 kB = 64;          // edges per warp batch
+// Build-time tuning: CTAs per SM the round kernels are compiled for, and
+// edges per warp batch of the copy pipeline.
+#ifndef SSSP_MIN_CTAS
+#define SSSP_MIN_CTAS 3
+#endif
+#ifndef SSSP_BATCH
+#define SSSP_BATCH 64
+#endif
+constexpr u32 kB = SSSP_BATCH;  // edges per warp batch
 constexpr u32 kBI = kB / 32;    // batch edges per lane
 constexpr u32 kAS = 3;          // adjacency slots: batches b, b + 1, b + 2 in flight
 constexpr u32 kDS = 2;          // neighbour-state slots: batches b, b + 1
@@ -287,6 +296,23 @@ __device__ __forceinline__ void wq_flush(const RoundParams& P, WarpQueue& q, u32
     q.cnt = 0;
 }
 
+// Flushes two queues; both counter atomics are in flight together.
+__device__ __forceinline__ void wq_flush2(const RoundParams& P, WarpQueue& q1, u32* c1, u32* l1,
+                                          WarpQueue& q2, u32* c2, u32* l2, u32 lane) {
+    u32 b1 = 0, b2 = 0;
+    if (lane == 0) {
+        if (q1.cnt) b1 = atomicAdd(c1, q1.cnt);
+        if (q2.cnt) b2 = atomicAdd(c2, q2.cnt);
+    }
+    b1 = __shfl_sync(kFull, b1, 0);
+    b2 = __shfl_sync(kFull, b2, 0);
+    if (lane < q1.cnt) put_small(P, l1, b1 + lane, q1.buf[lane]);
+    if (lane < q2.cnt) put_small(P, l2, b2 + lane, q2.buf[lane]);
+    __syncwarp();
+    q1.cnt = 0;
+    q2.cnt = 0;
+}
+
 // Accumulators a thread carries through one phase.
 struct Acc {
     u64 fmin_d, fmin_t;     // folds of minD / threshold (single-query mode)
@@ -320,8 +346,16 @@ __device__ __forceinline__ void flush(const RoundParams& P, u32 slot, Acc& a, u3
     if (!MULTI) {
         const u64 d = warp_min64(a.fmin_d), t = warp_min64(a.fmin_t);
         if (lane == 0) {
-            if (d != kInf64) atomic_min_checked(&P.ivar[0].minD[slot], d);
-            if (t != kInf64) atomic_min_checked(&P.ivar[0].thr[slot], t);
+            // A large grid first reads the minimum, so that most warps skip
+            // the atomic on this one address; a cluster-sized grid (few
+            // warps, latency-bound rounds) fires the atomics without waiting.
+            if (gridDim.x > kSmallGrid) {
+                if (d != kInf64) atomic_min_checked(&P.ivar[0].minD[slot], d);
+                if (t != kInf64) atomic_min_checked(&P.ivar[0].thr[slot], t);
+            } else {
+                if (d != kInf64) atomicMin(&P.ivar[0].minD[slot], d);
+                if (t != kInf64) atomicMin(&P.ivar[0].thr[slot], t);
+            }
             if (nf) atomicAdd(&P.ivar[0].nfix[slot], (u32)nf);
         }
     }
@@ -351,7 +385,8 @@ __device__ __forceinline__ u32 outw_of<WideL>(const InstDesc&, const VRec* r, u3
 }
 template <>
 __device__ __forceinline__ u32 outw_of<NarrowL>(const InstDesc& d, const VRecN*, u32 v) {
-    return d.outw[v];
+    const u32 ow = d.outw[v] & kInf31;            // bit 31: in-hub flag
+    return ow == kInf31 ? kNoOutW : ow;
 }
 
 // ------------------------------------------------------------- pipeline
@@ -477,24 +512,33 @@ __device__ __forceinline__ void issue_dc(const RoundParams& P, WarpStage<S>& st,
 
 // ------------------------------------------------------------------ relax
 
-// Relaxation of the staged edges [0, nb) (SP_4 step 3): per edge the owner's
-// distance dx and id xloc; newly discovered targets are queued.
+// Relaxations whose atomicMin results are still in flight.  A batch's
+// results are consumed while the next batch is handled, so a warp does not
+// wait for the atomics' round trip; the last batch of a phase is consumed
+// at its end.
+struct Pend {
+    u64 cand[kBI], old[kBI];        // old = 0: nothing was tried
+    u32 gy[kBI], yl[kBI];           // target record / local id
+    u32 ow[kBI];                    // target outWeight (compact: | in-hub flag in bit 31)
+    u32 deg[kBI];                   // target in-degree (wide layout)
+    u32 inst[kBI];                  // target's query (multi-query mode)
+    bool any;                       // a batch is pending (warp-uniform)
+};
+
+// Issues the relaxations of the staged edges [0, nb) (SP_4 step 3): per edge
+// the owner's distance dx and id xloc.  A target that is fixed, or whose
+// staged D is already no larger, is skipped.
 template <bool MULTI, class L>
-__device__ __forceinline__ void relax_batch(const RoundParams& P,
+__device__ __forceinline__ void relax_issue(const RoundParams& P,
                                             WarpStage<typename L::RSlot>& st, u32 as, u32 ds,
                                             u32 nb, u32 cur, bool per_owner, u64 dx, u32 xloc,
-                                            u64 gbase, u32 inst, Acc& a, WarpQueue& q,
-                                            u32 lane) {
+                                            u64 gbase, u32 inst, Acc& a, Pend& pd, u32 lane) {
     typename L::Rec* rec = L::rec(P);
-    u64 cand[kBI], old[kBI];
-    u32 gy[kBI], yl[kBI];
 #pragma unroll
     for (u32 i = 0; i < kBI; ++i) {
-        cand[i] = 0;
-        old[i] = 0;                                // "not lowered"
-        gy[i] = 0;
-        yl[i] = 0;
-        if (32 * i >= nb) break;                   // warp-uniform
+        pd.cand[i] = 0;
+        pd.old[i] = 0;
+        if (32 * i >= nb) continue;                // warp-uniform
         const u32 idx = 32 * i + lane;
         const bool ev = idx < nb;
         const u32 own = (per_owner && ev) ? st.own[as][idx] : lane;
@@ -506,7 +550,11 @@ __device__ __forceinline__ void relax_batch(const RoundParams& P,
         }
         const u32 ox = per_owner ? __shfl_sync(kFull, xloc, own) : xloc;
         u64 ob = gbase;
-        if (MULTI && per_owner) ob = __shfl_sync(kFull, gbase, own);
+        u32 oi = inst;                             // an edge's target is in its source's query
+        if (MULTI && per_owner) {
+            ob = __shfl_sync(kFull, gbase, own);
+            oi = __shfl_sync(kFull, inst, own);
+        }
         if (!ev) continue;
         const uint2 e = st.adj[as][idx];
         const typename L::RSlot& v = st.dc[ds][idx];
@@ -515,44 +563,72 @@ __device__ __forceinline__ void relax_batch(const RoundParams& P,
             atomicOr(&P.ctl->error, 8u);
             continue;
         }
-        cand[i] = (dd << (L::kNarrow ? 32u : P.vbits)) | ox;
-        yl[i] = e.x;
-        gy[i] = (u32)(ob + e.x);
-        if (!v.fixed(cur) && cand[i] < v.d()) old[i] = atomicMin(&rec[gy[i]].dp, cand[i]);
+        const u64 cand = (dd << (L::kNarrow ? 32u : P.vbits)) | ox;
+        pd.yl[i] = e.x;
+        pd.gy[i] = (u32)(ob + e.x);
+        pd.inst[i] = oi;
+        if (!v.fixed(cur) && cand < v.d()) {
+            pd.cand[i] = cand;
+            pd.old[i] = atomicMin(&rec[pd.gy[i]].dp, cand);
+            if (L::kNarrow) {
+                const InstDesc& d = MULTI ? P.idesc[oi] : P.g;
+                pd.ow[i] = d.outw[e.x];
+            } else {
+                const RecSlot& w = reinterpret_cast<const RecSlot&>(v);
+                pd.ow[i] = w.outw();
+                pd.deg[i] = w.indeg();
+            }
+        }
         a.edges++;
     }
+    pd.any = true;
+}
+
+// Consumes a pending batch: successful relaxations fold the target's D and
+// D + outWeight into the minima of the round (Lemmas 7 and 8); a target
+// whose D was infinite is newly discovered and joins the active set.
+template <bool MULTI, class L>
+__device__ __forceinline__ void relax_consume(const RoundParams& P, u32 cur, Acc& a, WarpQueue& q,
+                                              Pend& pd, u32 lane) {
+    if (!pd.any) return;
+    pd.any = false;
 #pragma unroll
     for (u32 i = 0; i < kBI; ++i) {
-        if (32 * i >= nb) break;                   // warp-uniform
-        const u32 idx = 32 * i + lane;
-        const bool ok = cand[i] < old[i];          // old = 0 when not tried
-        const bool fresh = ok && old[i] == kInf64;
-        u32 indeg = 0;
+        const bool ok = pd.cand[i] < pd.old[i];
+        const bool fresh = ok && pd.old[i] == kInf64;
+        bool hub = false;
         if (ok) {
-            u32 oinst = inst;
-            if (MULTI && per_owner) oinst = P.page_owner[gy[i] >> P.page_shift];
-            u32 ow;
+            u32 ow = pd.ow[i];
+            bool none;
             if (L::kNarrow) {
-                const InstDesc& d = MULTI ? P.idesc[oinst] : P.g;
-                ow = d.outw[yl[i]];
-                if (fresh) indeg = (u32)(d.in_off[yl[i] + 1] - d.in_off[yl[i]]);
+                hub = (ow >> 31) != 0;
+                ow &= kInf31;
+                none = ow == kInf31;
             } else {
-                const RecSlot& v = reinterpret_cast<const RecSlot&>(st.dc[ds][idx]);
-                ow = v.outw();
-                indeg = v.indeg();
+                hub = pd.deg[i] > P.hub;
+                none = ow == kNoOutW;
             }
-            const u64 dd = cand[i] >> (L::kNarrow ? 32u : P.vbits);
-            fold<MULTI>(P, oinst, cur, dd, ow == kNoOutW ? P.dinf : dd + ow, a);
+            const u64 dd = pd.cand[i] >> (L::kNarrow ? 32u : P.vbits);
+            fold<MULTI>(P, pd.inst[i], cur, dd, none ? P.dinf : dd + ow, a);
         }
-        const bool sm = fresh && indeg <= P.hub;
-        wq_push(P, q, &P.ctl->nAS[cur], P.L.AS[cur], sm, gy[i], lane);
-        if (fresh && !sm) put_hub(P, &P.ctl->AHpk[cur], P.L.AH[cur], gy[i], indeg);
+        const bool sm = fresh && !hub;
+        wq_push(P, q, &P.ctl->nAS[cur], P.L.AS[cur], sm, pd.gy[i], lane);
+        if (fresh && hub) {
+            u64 deg;
+            if (L::kNarrow) {
+                const InstDesc& d = MULTI ? P.idesc[pd.inst[i]] : P.g;
+                deg = d.in_off[pd.yl[i] + 1] - d.in_off[pd.yl[i]];
+            } else {
+                deg = pd.deg[i];
+            }
+            put_hub(P, &P.ctl->AHpk[cur], P.L.AH[cur], pd.gy[i], deg);
+        }
     }
 }
 
 template <bool MULTI, class L>
 __device__ void relax_small(const RoundParams& P, WarpStage<typename L::RSlot>& st, u32 t,
-                            u32 nfs, u32 cur, u32 lane, Acc& a, WarpQueue& q) {
+                            u32 nfs, u32 cur, u32 lane, Acc& a, WarpQueue& q, Pend& pd) {
     const u32 idx = t * 32 + lane;
     const bool valid = idx < nfs;
     u32 g = 0, xloc = 0, inst = 0, deg = 0;
@@ -579,14 +655,15 @@ __device__ void relax_small(const RoundParams& P, WarpStage<typename L::RSlot>& 
             issue_dc<MULTI, L>(P, st, as, ds, min(kB, tl.total - bb * kB), cur, gbase, true, lane);
         },
         [&](u32 bb, u32 as, u32 ds) {
-            relax_batch<MULTI, L>(P, st, as, ds, min(kB, tl.total - bb * kB), cur, true, dx, xloc,
-                                  gbase, inst, a, q, lane);
+            relax_consume<MULTI, L>(P, cur, a, q, pd, lane);
+            relax_issue<MULTI, L>(P, st, as, ds, min(kB, tl.total - bb * kB), cur, true, dx, xloc,
+                                  gbase, inst, a, pd, lane);
         });
 }
 
 template <bool MULTI, class L>
 __device__ void relax_hub(const RoundParams& P, WarpStage<typename L::RSlot>& st, u32 c, u32 nfh,
-                          u32 cur, u32 lane, Acc& a, WarpQueue& q) {
+                          u32 cur, u32 lane, Acc& a, WarpQueue& q, Pend& pd) {
     const uint2* FH = P.L.FH[cur];
     u32 lo = 0, hi = nfh;
     while (hi - lo > 1) {
@@ -615,8 +692,9 @@ __device__ void relax_hub(const RoundParams& P, WarpStage<typename L::RSlot>& st
             issue_dc<MULTI, L>(P, st, as, ds, min(kB, n - bb * kB), cur, d.base, false, lane);
         },
         [&](u32 bb, u32 as, u32 ds) {
-            relax_batch<MULTI, L>(P, st, as, ds, min(kB, n - bb * kB), cur, false, dx, xloc,
-                                  d.base, inst, a, q, lane);
+            relax_consume<MULTI, L>(P, cur, a, q, pd, lane);
+            relax_issue<MULTI, L>(P, st, as, ds, min(kB, n - bb * kB), cur, false, dx, xloc,
+                                  d.base, inst, a, pd, lane);
         });
 }
 
@@ -670,24 +748,28 @@ __device__ void relax_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
 
     Acc a = {kInf64, kInf64, 0, 0, 0};
     WarpQueue q = {s_q + wib * kQCap, 0};
+    Pend pd;
+    pd.any = false;
     // First item per warp is static (no atomic); the rest are pulled.
     const u32 nwarps = gridDim.x * kWarps;
     for (u32 item = blockIdx.x * kWarps + wib; item < total;) {
-        if (item < tiles) relax_small<MULTI, L>(P, s_st[wib], item, nfs, cur, lane, a, q);
-        else relax_hub<MULTI, L>(P, s_st[wib], item - tiles, nfh, cur, lane, a, q);
+        if (item < tiles) relax_small<MULTI, L>(P, s_st[wib], item, nfs, cur, lane, a, q, pd);
+        else relax_hub<MULTI, L>(P, s_st[wib], item - tiles, nfh, cur, lane, a, q, pd);
         if (total <= nwarps) break;                // the static items were all
         u32 next = 0;
         if (lane == 0) next = atomicAdd(&ctl->work[0], 1u) + nwarps;
         item = __shfl_sync(kFull, next, 0);
     }
+    relax_consume<MULTI, L>(P, cur, a, q, pd, lane);
     wq_flush(P, q, &ctl->nAS[cur], P.L.AS[cur], lane);
     flush<MULTI>(P, cur, a, lane, 0, 3);
 }
 
 template <bool MULTI, class L>
-__global__ void __launch_bounds__(256, 3) k_relax(RoundParams P) {
+__global__ void __launch_bounds__(256, SSSP_MIN_CTAS) k_relax(RoundParams P) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     if (ld_volatile(&P.ctl->status) != kRunning) return;
+    if (ld_volatile(&P.ctl->cup_only)) return;     // relaxed already (tail kernel)
     relax_phase<MULTI, L>(P, s_dyn, P.ctl->round);
 }
 
@@ -710,16 +792,14 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
     const u32 idx = t * 32 + lane;
     const bool valid = idx < nas;
     u32 g = 0, yloc = 0, inst = 0, deg = 0, outw = kNoOutW;
-    u64 gbase = 0, ib = 0, dy = 0, cy = 0, thr = thr0, minD = minD0;
+    u64 gbase = 0, ib = 0, dy = 0, cy = 0, thr = thr0, minD = minD0, odeg = 0;
     const uint2* in_adj = P.g.in_adj;
-    const u64* out_off = P.g.out_off;
     typename L::Rec* rec = L::rec(P);
     if (valid) {
         g = P.L.AS[cur][idx];
         const InstDesc& d = desc_of<MULTI>(P, g, inst);
         gbase = d.base;
         in_adj = d.in_adj;
-        out_off = d.out_off;
         if (MULTI) {
             thr = ld_volatile(&P.ivar[inst].thr[cur]);
             minD = ld_volatile(&P.ivar[inst].minD[cur]);
@@ -727,6 +807,8 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
         yloc = g - (u32)gbase;
         ib = d.in_off[yloc];
         deg = (u32)(d.in_off[yloc + 1] - ib);
+        // Out-degree now, in the same round trip (needed if y gets fixed).
+        odeg = d.out_off[yloc + 1] - d.out_off[yloc];
         const ulonglong2 v = L::ld_dc(rec + g, cur);
         dy = v.x >> P.vbits;
         cy = v.y & kCMask;
@@ -784,8 +866,6 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
     }
     __syncwarp();
     const bool fx = valid && fix, sv = valid && !fix;
-    u64 odeg = 0;
-    if (fx) odeg = out_off[yloc + 1] - out_off[yloc];
     const bool fs = fx && odeg <= P.hub;
     wq_push(P, qf, &P.ctl->nFS[nxt], P.L.FS[nxt], fs, g, lane);
     if (fx && !fs) put_hub(P, &P.ctl->FHpk[nxt], P.L.FH[nxt], g, odeg);
@@ -901,6 +981,7 @@ __device__ void round_epilogue(const RoundParams& P, u32 r) {
     if (threadIdx.x == 0) {
         const u32 total = s_running;
         ctl->running = total;
+        ctl->cup_only = 0;
         ctl->round = r + 1;
         u32 st = kRunning;
         if (total == 0) st = kDone;
@@ -954,8 +1035,7 @@ __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r)
         if (lane == 0) next = atomicAdd(&ctl->work[1], 1u) + nwarps;
         item = __shfl_sync(kFull, next, 0);
     }
-    wq_flush(P, qf, &ctl->nFS[nxt], P.L.FS[nxt], lane);
-    wq_flush(P, qa, &ctl->nAS[nxt], P.L.AS[nxt], lane);
+    wq_flush2(P, qf, &ctl->nFS[nxt], P.L.FS[nxt], qa, &ctl->nAS[nxt], P.L.AS[nxt], lane);
     a.fmin_d = an.fmin_d;
     a.fmin_t = an.fmin_t;
     a.nfix = an.nfix;
@@ -963,7 +1043,7 @@ __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r)
 }
 
 template <bool MULTI, class L>
-__global__ void __launch_bounds__(256, 3) k_cupdate(RoundParams P) {
+__global__ void __launch_bounds__(256, SSSP_MIN_CTAS) k_cupdate(RoundParams P) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ u32 s_last;
     Ctl* ctl = P.ctl;
@@ -1040,7 +1120,7 @@ __device__ bool grid_barrier(const RoundParams& P, bool epilogue, u32 r) {
 // lower-bound phase, barrier (whose last arriver closes the round), until
 // no query runs, the stop round is passed, or a barrier times out.
 template <bool MULTI, class L>
-__global__ void __launch_bounds__(256, 3) k_solve(RoundParams P) {
+__global__ void __launch_bounds__(256, SSSP_MIN_CTAS) k_solve(RoundParams P) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     Ctl* ctl = P.ctl;
     if (P.trace && blockIdx.x == 0 && threadIdx.x == 0 && P.trace_cap) P.trace[0] = global_ns();
@@ -1052,6 +1132,90 @@ __global__ void __launch_bounds__(256, 3) k_solve(RoundParams P) {
         if (!grid_barrier(P, false, r)) break;
         cupdate_phase<MULTI, L>(P, s_dyn, r);
         if (!grid_barrier(P, true, r)) break;
+    }
+}
+
+// ---------------------------------------------------- cluster tail kernel
+
+// Rounds whose work is small are latency chains: list -> offsets ->
+// adjacency -> neighbour states, twice per round.  Two full-grid launches
+// and a grid-wide arrival add several microseconds to each.  The tail kernel
+// runs such rounds back to back in one thread-block cluster (kTailCTAs CTAs,
+// hardware cluster barriers between phases).  Appended to every iteration
+// of the device loop, it starts only when the next round is small and hands
+// back to the full grid when a round grows.
+constexpr u32 kTailCTAs = 16;
+
+// Cluster-wide barrier; its release / acquire semantics order every global
+// memory access before it (in any CTA of the cluster) before every access
+// after it.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// Whether round ctl->round starts in the tail kernel: the loop is running
+// and not past its stop round, and the frontier and the active set known
+// before the round each make at most P.tail_items work items (32-entry
+// tiles plus hub chunks).  The relaxation may add active vertices: the
+// second phase is checked again after it (tail_cup_fits).
+__device__ __forceinline__ u32 tail_decide(const RoundParams& P) {
+    const Ctl* ctl = P.ctl;
+    if (ld_volatile(&ctl->status) != kRunning) return 0;
+    const u32 r = ld_volatile(&ctl->round);
+    if (r > ld_volatile(&ctl->stop_round)) return 0;
+    const u32 cur = r & 1u;
+    const u32 fi = ((ld_volatile(&ctl->nFS[cur]) + 31) >> 5) + (u32)ld_volatile(&ctl->FHpk[cur]);
+    const u32 ai = ((ld_volatile(&ctl->nAS[cur]) + 31) >> 5) + (u32)ld_volatile(&ctl->AHpk[cur]);
+    return (fi <= P.tail_items && ai <= P.tail_items) ? 1u : 0u;
+}
+
+__device__ __forceinline__ u32 tail_cup_fits(const RoundParams& P, u32 r) {
+    const Ctl* ctl = P.ctl;
+    const u32 cur = r & 1u;
+    const u32 ai = ((ld_volatile(&ctl->nAS[cur]) + 31) >> 5) + (u32)ld_volatile(&ctl->AHpk[cur]);
+    return ai <= P.tail_items ? 1u : 0u;
+}
+
+// Launched as one cluster of kTailCTAs CTAs.  Every CTA takes the same
+// number of cluster barriers: the loop decision is written by CTA 0 before
+// a barrier and read by all after it, and nothing writes it again before
+// every CTA has passed the next barrier.
+template <bool MULTI, class L>
+__global__ void __launch_bounds__(256, 1) k_tail(RoundParams P) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    Ctl* ctl = P.ctl;
+    const bool lead = blockIdx.x == 0;
+    if (lead && threadIdx.x == 0) ctl->tail_go = tail_decide(P);
+    cluster_sync_all();
+    for (;;) {
+        if (ld_volatile(&ctl->tail_go) == 0) break;
+        const u32 r = ld_volatile(&ctl->round);
+        relax_phase<MULTI, L>(P, s_dyn, r);
+        cluster_sync_all();
+        if (lead && threadIdx.x == 0) ctl->tail_go = tail_cup_fits(P, r);
+        cluster_sync_all();
+        if (ld_volatile(&ctl->tail_go) == 0) {
+            // The relaxation grew the active set: the full grid finishes
+            // the round (its relax launch is skipped).
+            if (lead && threadIdx.x == 0) ctl->cup_only = 1;
+            break;
+        }
+        cupdate_phase<MULTI, L>(P, s_dyn, r);
+        cluster_sync_all();
+        if (lead) {
+            round_epilogue(P, r);
+            if (threadIdx.x == 0) ctl->tail_go = tail_decide(P);
+        }
+        cluster_sync_all();
+    }
+    // The device loop goes on while rounds remain (the epilogue's setting
+    // is overridden here because the tail kernel ends the loop body).
+    if (lead && threadIdx.x == 0 && P.cond) {
+        const u32 st = ld_volatile(&ctl->status);
+        const u32 r = ld_volatile(&ctl->round);
+        cudaGraphSetConditional(P.cond,
+                                (st == kRunning && r <= ld_volatile(&ctl->stop_round)) ? 1u : 0u);
     }
 }
 
@@ -1109,6 +1273,10 @@ const void* solve_fn(bool multi, bool narrow) {
     if (multi) return narrow ? (const void*)k_solve<true, NarrowL> : (const void*)k_solve<true, WideL>;
     return narrow ? (const void*)k_solve<false, NarrowL> : (const void*)k_solve<false, WideL>;
 }
+const void* tail_fn(bool multi, bool narrow) {
+    if (multi) return narrow ? (const void*)k_tail<true, NarrowL> : (const void*)k_tail<true, WideL>;
+    return narrow ? (const void*)k_tail<false, NarrowL> : (const void*)k_tail<false, WideL>;
+}
 size_t relax_smem_bytes(bool narrow) {
     return narrow ? relax_smem<NarrowL>() : relax_smem<WideL>();
 }
@@ -1150,8 +1318,42 @@ cudaError_t round_kernels_init() {
                 e = cudaFuncSetAttribute(solve_fn(multi, narrow),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)solve_smem_bytes(narrow));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(tail_fn(multi, narrow),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)solve_smem_bytes(narrow));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(tail_fn(multi, narrow),
+                                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         }
     return e;
+}
+
+// CTAs of the tail kernel's cluster, or 0 when such a cluster cannot be
+// scheduled on the current device (the device loop then runs without it).
+u32 tail_cluster_ctas() {
+    if (round_kernels_init() != cudaSuccess) return 0;
+    for (int m = 0; m < 2; ++m)
+        for (int nw = 0; nw < 2; ++nw) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = kTailCTAs;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(kTailCTAs);
+            cfg.blockDim = dim3(256);
+            cfg.dynamicSmemBytes = solve_smem_bytes(nw);
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, tail_fn(m, nw), &cfg) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return 0;
+            }
+            if (nclusters < 1) return 0;
+        }
+    return kTailCTAs;
 }
 
 // CTAs per SM that fit every variant of the two-kernel round.

@@ -161,6 +161,18 @@ __global__ void k_outw(const u64* out_off, const uint2* out_adj, u32 n, u32* out
     }
 }
 
+// outWeight word of the compact layout: the minimum out-weight (below 2^31
+// there; 2^31 - 1 when the vertex has no out-edge) with bit 31 set when the
+// in-degree is above the hub degree.  May run in place (out == outw).
+__global__ void k_pack_outw(const u32* outw, const u64* in_off, u32 n, u32 hub, u32* out) {
+    for (u64 v = blockIdx.x * (u64)blockDim.x + threadIdx.x; v < n;
+         v += (u64)gridDim.x * blockDim.x) {
+        const u32 ow = outw[v];
+        const u32 lo = ow == kNoOutW ? (kFixedN - 1) : ow;
+        out[v] = lo | ((in_off[v + 1] - in_off[v] > hub) ? kFixedN : 0u);
+    }
+}
+
 // Vertices above the hub degree, by direction (list capacities).
 __global__ void k_count_hubs(const u64* out_off, const u64* in_off, u32 n, u32 hub, u32* cnt) {
     u32 a = 0, b = 0;

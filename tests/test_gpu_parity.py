@@ -193,6 +193,25 @@ def test_weighted_grid_and_dag(sssp_lib, layout):
     assert_parity(sssp_lib, gg.dag(64, 512, 8, 4, 1, 1000, 2), 0, layout=layout)
 
 
+@LAYOUTS
+@pytest.mark.parametrize("tail_items", ["0", "64", "1000000"])
+def test_cluster_tail_rounds(sssp_lib, layout, tail_items, monkeypatch):
+    """Small rounds run in one thread-block cluster inside the device loop:
+    never (0), from a moderate size down (64 work items), or every round
+    after the first (a bound no round reaches).  Results are identical."""
+    monkeypatch.setenv("SSSP_TAIL_ITEMS", tail_items)
+    g = gg.rmat(14, 16, 1, 255, 17)
+    s = int(np.argmax(g.out_degree()))
+    assert_parity(sssp_lib, g, s, layout=layout)
+    assert_parity(sssp_lib, g, s, mode=oracle.RULE_MIND, layout=layout)
+    g2 = gg.random_var_graph(5000, 1, 9, 1, 300, 23)
+    assert_parity(sssp_lib, g2, 7, layout=layout, hub_degree=8, chunk_edges=32)
+    out, ref = assert_parity(sssp_lib, g2, 7, layout=layout)
+    # Per-round state with the loop stopped early, inside the tail.
+    part = gpu_solve(sssp_lib, g2, 7, max_rounds=ref.rounds - 3, layout=layout)
+    assert part["info"]["rounds"] == ref.rounds - 3
+
+
 def test_layout_selection(sssp_lib):
     """The automatic layout is compact exactly when n * max weight < 2^31 - 1;
     a graph whose distances need more than 31 bits solves with wide records,
