@@ -203,14 +203,18 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
     return SSSP_OK;
 }
 
-int alloc_lists(Context& c, u64 capS, u64 capH) {
+int alloc_lists(Context& c, u64 capS, u64 capH, u64 capC) {
     capH = std::max<u64>(capH, 1);
+    capC = std::min<u64>(std::max<u64>(capC, 1), 0xFFFFFFFFull);
     for (int i = 0; i < 2; ++i) {
         RC(c.pool.get(&c.P.L.FS[i], capS));
         RC(c.pool.get(&c.P.L.AS[i], capS));
         RC(c.pool.get(&c.P.L.FH[i], capH));
         RC(c.pool.get(&c.P.L.AH[i], capH));
+        RC(c.pool.get(&c.P.L.FC[i], capC));
+        RC(c.pool.get(&c.P.L.AC[i], capC));
     }
+    c.P.L.capC = (u32)capC;
     RC(c.pool.get(&c.P.L.hubmin, capH));
     RC(c.pool.get(&c.P.L.hubcnt, capH));
     c.P.L.capS = (u32)std::min<u64>(capS, 0xFFFFFFFFull);
@@ -223,6 +227,12 @@ int alloc_pinned(Context& c, u32 slots) {
     CK(cudaHostAlloc((void**)&c.h_ctl, sizeof(Ctl), cudaHostAllocDefault));
     CK(cudaHostAlloc((void**)&c.h_ivar, sizeof(InstVar) * slots, cudaHostAllocDefault));
     return SSSP_OK;
+}
+
+// Hub chunks a list can hold: at most m / chunk plus one partial chunk per
+// hub, in either direction.
+u64 hub_chunks(const sssp_graph* h) {
+    return h->m / h->opt.chunk_edges + std::max(h->hubs_in, h->hubs_out) + 1;
 }
 
 int init_single_context(sssp_graph* h) {
@@ -251,7 +261,7 @@ int init_single_context(sssp_graph* h) {
     RC(c.pool.get(&P.ctl, 1));
     RC(c.pool.get(&P.ivar, 1));
     RC(c.pool.get(&c.stage, h->n));
-    RC(alloc_lists(c, h->n, std::max(h->hubs_in, h->hubs_out)));
+    RC(alloc_lists(c, h->n, std::max(h->hubs_in, h->hubs_out), hub_chunks(h)));
     P.dinf = h->dinf;
     P.vbits = h->vbits;
     P.hub = h->opt.hub_degree;
@@ -516,9 +526,10 @@ int enqueue_single(sssp_graph* h, u32 source, u32 max_rounds, cudaStream_t st, u
 
 // ----------------------------------------------------------- multi-query
 
-int ensure_batch(sssp_graph* h0, u64 nrec, u32 nslots, u32 npages, u64 capH) {
+int ensure_batch(sssp_graph* h0, u64 nrec, u32 nslots, u32 npages, u64 capH, u64 capC) {
     Context* c = h0->batch;
-    if (c && c->nrec >= nrec && c->nslots >= nslots && c->npages >= npages && c->capH >= capH)
+    if (c && c->nrec >= nrec && c->nslots >= nslots && c->npages >= npages && c->capH >= capH &&
+        c->P.L.capC >= capC)
         return SSSP_OK;
     if (c) {
         c->destroy();
@@ -549,7 +560,7 @@ int ensure_batch(sssp_graph* h0, u64 nrec, u32 nslots, u32 npages, u64 capH) {
     P.idesc = idesc;
     P.page_owner = pages;
     RC(c->pool.get(&c->stage, nrec));
-    RC(alloc_lists(*c, nrec, capH));
+    RC(alloc_lists(*c, nrec, capH, capC));
     P.page_shift = kPageShift;
     P.hub = h0->opt.hub_degree;
     P.chunk = h0->opt.chunk_edges;
@@ -570,7 +581,7 @@ int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist
     if (!h0) return SSSP_E_INVAL;
     u32 vbits = 1;
     bool narrow = true;
-    u64 npages = 0, capH = 0;
+    u64 npages = 0, capH = 0, capC = 0;
     for (u32 i = 0; i < k; ++i) {
         if (!g[i] || !dist[i]) return SSSP_E_INVAL;
         if (g[i]->device != h0->device || g[i]->opt.hub_degree != h0->opt.hub_degree ||
@@ -581,6 +592,7 @@ int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist
         narrow = narrow && g[i]->narrow;
         npages += ((u64)g[i]->n + (1u << kPageShift) - 1) >> kPageShift;
         capH += std::max(g[i]->hubs_in, g[i]->hubs_out);
+        capC += hub_chunks(g[i]);
     }
     const u64 nrec = npages << kPageShift;
     if (nrec >= 0xFFFFFFFFull) return SSSP_E_NOMEM;   // list entries are 32-bit record ids
@@ -591,7 +603,7 @@ int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist
             return SSSP_E_OVERFLOW;
     DeviceGuard dg(h0->device);
     std::lock_guard<std::mutex> lk(h0->mu);
-    RC(ensure_batch(h0, nrec, k, (u32)npages, capH));
+    RC(ensure_batch(h0, nrec, k, (u32)npages, capH, capC));
     Context& c = *h0->batch;
     cudaStream_t st = use_user_stream ? st_user : h0->stream;
     RoundParams& P = c.P;

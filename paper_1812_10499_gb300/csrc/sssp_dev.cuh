@@ -106,7 +106,11 @@ struct Lists {
     uint2* AH[2];
     u64* hubmin;    // per active-hub entry: running min of Eq. (1) terms
     u32* hubcnt;    // per active-hub entry: chunks finished
+    u32* FC[2];     // chunk -> FH entry, written with the entry (chunks below capC)
+    u32* AC[2];     // chunk -> AH entry
     u32 capS, capH; // capacities of the small and hub lists
+    u32 capC;       // capacity of the chunk maps (chunks beyond it are found by search)
+    u32 pad;
 };
 
 struct RoundParams {

@@ -221,7 +221,7 @@ namespace sssp {
 namespace engine {
 int build_loop(Context& c);
 int run_loop(Context& c, u32 loop_mode, cudaStream_t st);
-int alloc_lists(Context& c, u64 capS, u64 capH);
+int alloc_lists(Context& c, u64 capS, u64 capH, u64 capC);
 int alloc_pinned(Context& c, u32 slots);
 }  // namespace engine
 }  // namespace sssp

@@ -105,6 +105,7 @@ extern "C" int sssp_solve_noalloc(uint32_t n, const uint64_t* out_off, const uin
     if (off > kNoAllocBytes) return SSSP_E_INTERNAL;
     P.L.capS = n;
     P.L.capH = n;
+    P.L.capC = 0;   // no chunk maps here: hub chunks find their vertex by search
     P.g = InstDesc{reinterpret_cast<const u64*>(out_off), reinterpret_cast<const uint2*>(out_adj),
                    reinterpret_cast<const u64*>(in_off), reinterpret_cast<const uint2*>(in_adj),
                    outw, 0, n, source};

@@ -248,13 +248,29 @@ __device__ __forceinline__ void put_small(const RoundParams& P, u32* list, u32 i
     if (idx < P.L.capS) list[idx] = g;
     else atomicOr(&P.ctl->error, 1u);
 }
-__device__ __forceinline__ void put_hub(const RoundParams& P, u64* pk, uint2* list, u32 g,
-                                        u64 deg) {
-    u32 nch = (u32)((deg + P.chunk - 1) / P.chunk);
-    u64 old = atomicAdd(pk, (1ull << 32) | nch);
-    u32 idx = (u32)(old >> 32);
-    if (idx < P.L.capH) list[idx] = make_uint2(g, (u32)old);
+__device__ __forceinline__ void put_hub(const RoundParams& P, u64* pk, uint2* list, u32* cmap,
+                                        u32 g, u64 deg) {
+    const u32 nch = (u32)((deg + P.chunk - 1) / P.chunk);
+    const u64 old = atomicAdd(pk, (1ull << 32) | nch);
+    const u32 idx = (u32)(old >> 32), first = (u32)old;
+    if (idx < P.L.capH) list[idx] = make_uint2(g, first);
     else atomicOr(&P.ctl->error, 2u);
+    // Chunk -> entry map, so that a chunk finds its vertex with one load.
+    const u32 end = min(first + nch, P.L.capC);
+    for (u32 k = first; k < end; ++k) cmap[k] = idx;
+}
+
+// Entry of hub list `list` (n entries) that chunk c belongs to: from the
+// chunk map, else by binary search over the entries' first chunks.
+__device__ __forceinline__ u32 hub_entry(const RoundParams& P, const uint2* list, const u32* cmap,
+                                         u32 n, u32 c) {
+    if (c < P.L.capC) return min(cmap[c], n - 1);
+    u32 lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const u32 mid = (lo + hi) >> 1;
+        if (list[mid].y <= c) lo = mid; else hi = mid;
+    }
+    return lo;
 }
 
 // Warp-private append buffer of one small list (in shared memory); the
@@ -621,7 +637,7 @@ __device__ __forceinline__ void relax_consume(const RoundParams& P, u32 cur, Acc
             } else {
                 deg = pd.deg[i];
             }
-            put_hub(P, &P.ctl->AHpk[cur], P.L.AH[cur], pd.gy[i], deg);
+            put_hub(P, &P.ctl->AHpk[cur], P.L.AH[cur], P.L.AC[cur], pd.gy[i], deg);
         }
     }
 }
@@ -665,12 +681,7 @@ template <bool MULTI, class L>
 __device__ void relax_hub(const RoundParams& P, WarpStage<typename L::RSlot>& st, u32 c, u32 nfh,
                           u32 cur, u32 lane, Acc& a, WarpQueue& q, Pend& pd) {
     const uint2* FH = P.L.FH[cur];
-    u32 lo = 0, hi = nfh;
-    while (hi - lo > 1) {
-        u32 mid = (lo + hi) >> 1;
-        if (FH[mid].y <= c) lo = mid; else hi = mid;
-    }
-    const uint2 ent = FH[lo];
+    const uint2 ent = FH[hub_entry(P, FH, P.L.FC[cur], nfh, c)];
     const u32 g = ent.x, k = c - ent.y;
     u32 inst;
     const InstDesc& d = desc_of<MULTI>(P, g, inst);
@@ -868,7 +879,7 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
     const bool fx = valid && fix, sv = valid && !fix;
     const bool fs = fx && odeg <= P.hub;
     wq_push(P, qf, &P.ctl->nFS[nxt], P.L.FS[nxt], fs, g, lane);
-    if (fx && !fs) put_hub(P, &P.ctl->FHpk[nxt], P.L.FH[nxt], g, odeg);
+    if (fx && !fs) put_hub(P, &P.ctl->FHpk[nxt], P.L.FH[nxt], P.L.FC[nxt], g, odeg);
     wq_push(P, qa, &P.ctl->nAS[nxt], P.L.AS[nxt], sv, g, lane);
     if (MULTI) {
         if (fx) atomicAdd(&P.ivar[inst].nfix[nxt], 1u);
@@ -880,18 +891,12 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
 
 template <bool MULTI, class L>
 __device__ void cup_hub(const RoundParams& P, WarpStage<typename L::CSlot>& st, u32 c, u32 nah,
-                        u32 ah_chunks, u32 r, u32 cur, u32 lane, u64 thr0, u64 minD0, Acc& a,
-                        Acc& an) {
+                        u32 r, u32 cur, u32 lane, u64 thr0, u64 minD0, Acc& a, Acc& an) {
     const u32 nxt = cur ^ 1u;
     const uint2* AH = P.L.AH[cur];
-    u32 lo = 0, hi = nah;
-    while (hi - lo > 1) {
-        u32 mid = (lo + hi) >> 1;
-        if (AH[mid].y <= c) lo = mid; else hi = mid;
-    }
+    const u32 lo = hub_entry(P, AH, P.L.AC[cur], nah, c);
     const uint2 ent = AH[lo];
     const u32 g = ent.x, k = c - ent.y;
-    const u32 nch = ((lo + 1 < nah) ? AH[lo + 1].y : ah_chunks) - ent.y;
     u32 inst;
     const InstDesc& d = desc_of<MULTI>(P, g, inst);
     u64 thr = thr0, minD = minD0;
@@ -901,6 +906,7 @@ __device__ void cup_hub(const RoundParams& P, WarpStage<typename L::CSlot>& st, 
     }
     const u32 yloc = g - (u32)d.base;
     const u64 ib = d.in_off[yloc], ie = d.in_off[yloc + 1];
+    const u32 nch = (u32)((ie - ib + P.chunk - 1) / P.chunk);   // as counted by put_hub
     const u64 cb = ib + (u64)k * P.chunk;
     const u64 ce = umin64(cb + P.chunk, ie);
     const typename L::Bounds bd = L::bounds(thr, minD);
@@ -943,11 +949,11 @@ __device__ void cup_hub(const RoundParams& P, WarpStage<typename L::CSlot>& st, 
         P.fround[g] = (int)r;
         const u64 odeg = d.out_off[yloc + 1] - d.out_off[yloc];
         if (odeg <= P.hub) put_small(P, P.L.FS[nxt], atomicAdd(&P.ctl->nFS[nxt], 1u), g);
-        else put_hub(P, &P.ctl->FHpk[nxt], P.L.FH[nxt], g, odeg);
+        else put_hub(P, &P.ctl->FHpk[nxt], P.L.FH[nxt], P.L.FC[nxt], g, odeg);
         if (MULTI) atomicAdd(&P.ivar[inst].nfix[nxt], 1u);
         else an.nfix++;
     } else {
-        put_hub(P, &P.ctl->AHpk[nxt], P.L.AH[nxt], g, ie - ib);
+        put_hub(P, &P.ctl->AHpk[nxt], P.L.AH[nxt], P.L.AC[nxt], g, ie - ib);
         fold<MULTI>(P, inst, nxt, dy, outw == kNoOutW ? P.dinf : dy + outw, an);
     }
 }
@@ -1027,8 +1033,7 @@ __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r)
             cup_small<MULTI, L>(P, s_st[wib], item, nas, r, cur, lane, s_min + wib * 32, thr,
                                 minD, a, an, qf, qa);
         else
-            cup_hub<MULTI, L>(P, s_st[wib], item - tiles, nah, ah_chunks, r, cur, lane, thr, minD,
-                              a, an);
+            cup_hub<MULTI, L>(P, s_st[wib], item - tiles, nah, r, cur, lane, thr, minD, a, an);
         __syncwarp();
         if (total <= nwarps) break;                // the static items were all
         u32 next = 0;
@@ -1247,7 +1252,7 @@ __global__ void k_start(RoundParams P, u32 first, u32 count, u32 max_rounds) {
         P.fround[g] = 0;
         const u64 odeg = d.out_off[s + 1] - d.out_off[s];
         if (odeg <= P.hub) put_small(P, P.L.FS[cur], atomicAdd(&ctl->nFS[cur], 1u), g);
-        else put_hub(P, &ctl->FHpk[cur], P.L.FH[cur], g, odeg);
+        else put_hub(P, &ctl->FHpk[cur], P.L.FH[cur], P.L.FC[cur], g, odeg);
         __threadfence();
         v->status = kRunning;
     }

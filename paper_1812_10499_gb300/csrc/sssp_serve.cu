@@ -89,7 +89,8 @@ int open_impl(sssp_server* s) {
     P.idesc = idesc;
     P.page_owner = pages;
     RC(c.pool.get(&c.stage, nrec));
-    RC(alloc_lists(c, nrec, nrec));
+    // Chunk maps sized like the record pool; chunks beyond are found by search.
+    RC(alloc_lists(c, nrec, nrec, nrec));
     P.page_shift = kPageShift;
     P.hub = kDefaultHub;
     P.chunk = kDefaultChunk;
