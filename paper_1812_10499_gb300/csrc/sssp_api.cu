@@ -24,11 +24,13 @@ using namespace sssp::engine;
 namespace sssp {
 namespace engine {
 
-int occupancy_grid(int device, const sssp_options& o) {
+// Grid of a round kernel: SMs x CTAs per SM (the option, else occupancy).
+int occupancy_grid(int device, const sssp_options& o, bool cupdate = false) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     int per = (int)o.ctas_per_sm;
-    if (per <= 0) per = std::max(1, round_blocks_per_sm(kThreads));
+    if (per <= 0)
+        per = std::max(1, cupdate ? cupdate_blocks_per_sm(kThreads) : round_blocks_per_sm(kThreads));
     return std::max(1, sms) * per;
 }
 
@@ -77,6 +79,7 @@ int build_loop(Context& c) {
     e = cudaGraphAddKernelNode(&n1, body, nullptr, 0, &kp);
     if (e == cudaSuccess) {
         kp.func = const_cast<void*>(cupdate_fn(c.multi, c.narrow));
+        kp.gridDim = dim3(c.grid_cup);
         kp.sharedMemBytes = (unsigned)cupdate_smem_bytes(c.narrow);
         e = cudaGraphAddKernelNode(&n2, body, &n1, 1, &kp);
     }
@@ -178,7 +181,7 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
             if (c.prof) CK(cudaEventRecord(c.ev[3 * i], st));
             CK(cudaLaunchKernel(fr, dim3(c.grid), dim3(kThreads), args, smr, st));
             if (c.prof) CK(cudaEventRecord(c.ev[3 * i + 1], st));
-            CK(cudaLaunchKernel(fc, dim3(c.grid), dim3(kThreads), args, smc, st));
+            CK(cudaLaunchKernel(fc, dim3(c.grid_cup), dim3(kThreads), args, smc, st));
             if (c.prof) CK(cudaEventRecord(c.ev[3 * i + 2], st));
         }
         CK(cudaMemcpyAsync(c.h_ctl, c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -242,6 +245,7 @@ int init_single_context(sssp_graph* h) {
     c.nrec = h->n;
     c.nslots = 1;
     c.grid = h->grid;
+    c.grid_cup = h->grid_cup;
     c.grid_solve = h->grid_solve;
     c.tail_ctas = h->tail_ctas;
     RoundParams& P = c.P;
@@ -392,6 +396,7 @@ int create_impl(sssp_graph* h, u32 n, u64 m, const u64* row_ptr, const u32* col,
 
     CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     h->grid = occupancy_grid(h->device, h->opt);
+    h->grid_cup = occupancy_grid(h->device, h->opt, true);
     {
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -545,6 +550,7 @@ int ensure_batch(sssp_graph* h0, u64 nrec, u32 nslots, u32 npages, u64 capH, u64
     c->nslots = nslots;
     c->npages = npages;
     c->grid = h0->grid;
+    c->grid_cup = h0->grid_cup;
     c->grid_solve = h0->grid_solve;
     c->tail_ctas = h0->tail_ctas;
     RoundParams& P = c->P;

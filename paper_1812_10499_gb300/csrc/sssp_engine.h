@@ -28,6 +28,7 @@ cudaError_t round_kernels_init();
 cudaError_t launch_start(bool multi, bool narrow, const RoundParams& P, u32 first, u32 count,
                          u32 max_rounds, cudaStream_t st);
 int round_blocks_per_sm(int threads);
+int cupdate_blocks_per_sm(int threads);
 __global__ void k_init_records(VRec* rec, VRecN* recn, int* fround, const u32* outw,
                                const u64* in_off, u32 n);
 __global__ void k_init_records_multi(RoundParams P, u64 nrec, u32 first_page, u32 npages);
@@ -153,6 +154,7 @@ struct Context {
     cudaGraphExec_t exec = nullptr;
     int grid = 0;
     int grid_solve = 0;              // co-resident grid of the persistent kernel
+    int grid_cup = 0;                // grid of the lower-bound kernel
     u32 tail_ctas = 0;               // cluster size of the tail kernel, 0 = not in the loop
     // Per-kernel event timing (sssp_profile).
     bool prof = false;
@@ -209,6 +211,7 @@ struct sssp_graph {
     cudaStream_t stream = nullptr;   // internal stream for setup and host-pointer solves
     int grid = 0;
     int grid_solve = 0;
+    int grid_cup = 0;
     u32 tail_ctas = 0;               // see Context::tail_ctas
     u32 tail_items = 0;
     sssp::engine::Context single;    // single-query context

@@ -39,6 +39,9 @@ constexpr u32 kQCap = 64;       // entries of a warp append buffer
 #ifndef SSSP_MIN_CTAS
 #define SSSP_MIN_CTAS 3
 #endif
+#ifndef SSSP_CUP_MIN_CTAS
+#define SSSP_CUP_MIN_CTAS 3
+#endif
 #ifndef SSSP_BATCH
 #define SSSP_BATCH 64
 #endif
@@ -411,7 +414,8 @@ __device__ __forceinline__ u32 outw_of<NarrowL>(const InstDesc& d, const VRecN*,
 // issue_dc(b, aslot, dslot) start cp.async copies (no wait); compute(b,
 // aslot, dslot) consumes a batch.  Commit groups, in order: A0 A1 D0, then
 // per batch b: A(b+2) D(b+1); so waiting for all but the newest group
-// completes A(b+1), and all but the newest two completes D(b).
+// completes A(b+1), and all but the newest two completes D(b).  Batches are
+// issued in increasing order.
 template <class IA, class ID, class CO>
 __device__ __forceinline__ void run_pipeline(u32 nbat, IA issue_adj, ID issue_dc, CO compute) {
     if (nbat == 0) return;
@@ -786,6 +790,28 @@ __global__ void __launch_bounds__(256, SSSP_MIN_CTAS) k_relax(RoundParams P) {
 
 // ---------------------------------------------------------------- cupdate
 
+// Segment minimum: brk has a bit at the first lane of every segment of
+// contiguous lanes.  The 32-bit form gives every lane its segment's minimum
+// (one warp reduction over the segment's lanes); the 64-bit form is an
+// inclusive segmented scan, exact at the segment's last lane.
+__device__ __forceinline__ u32 seg_min(u32 v, u32 brk, u32 lane) {
+    const u32 le = lanemask_le(lane);
+    const u32 first = 31 - __clz(brk & le);
+    const u32 above = brk & ~le;
+    const u32 last = above ? (u32)(__ffs(above) - 2) : 31u;
+    const u32 mask = (kFull >> (31 - last)) & (kFull << first);
+    return __reduce_min_sync(mask, v);
+}
+__device__ __forceinline__ u64 seg_min(u64 v, u32 brk, u32 lane) {
+    const u32 span = lane - (31 - __clz(brk & lanemask_le(lane)));
+#pragma unroll
+    for (u32 dd = 1; dd < 32; dd <<= 1) {
+        const u64 ov = __shfl_up_sync(kFull, v, dd);
+        if (dd <= span) v = umin64(v, ov);
+    }
+    return v;
+}
+
 // Decision for one active vertex after its Eq. (1) minimum m is known.
 __device__ __forceinline__ u64 decide(const RoundParams& P, u64 dy, u64 cy, u64 m, u64 thr,
                                       u64 minD, bool& fix) {
@@ -849,17 +875,11 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
                 }
                 typename L::Term val = L::kTermInf;
                 if (ev) val = L::term(P, st.dc[ds][sidx], cur, st.adj[as][sidx].y, ob);
-                // Segmented min over lanes sharing an owner: owners are
-                // contiguous, a lane's segment starts at the last owner
-                // change at or before it.
+                // Min over the lanes sharing an owner (contiguous lanes; a
+                // segment starts at every owner change).
                 const u32 prev = __shfl_up_sync(kFull, own, 1);
                 const u32 brk = __ballot_sync(kFull, lane == 0 || !ev || prev != own);
-                const u32 span = lane - (31 - __clz(brk & lanemask_le(lane)));
-#pragma unroll
-                for (u32 dd = 1; dd < 32; dd <<= 1) {
-                    const typename L::Term ov = __shfl_up_sync(kFull, val, dd);
-                    if (dd <= span) val = min(val, ov);
-                }
+                val = seg_min(val, brk, lane);
                 const bool tail = ev && (lane == 31 || ((brk >> (lane + 1)) & 1u));
                 if (tail) smin[own] = umin64(smin[own], (u64)val);
                 __syncwarp();
@@ -1048,7 +1068,7 @@ __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r)
 }
 
 template <bool MULTI, class L>
-__global__ void __launch_bounds__(256, SSSP_MIN_CTAS) k_cupdate(RoundParams P) {
+__global__ void __launch_bounds__(256, SSSP_CUP_MIN_CTAS) k_cupdate(RoundParams P) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ u32 s_last;
     Ctl* ctl = P.ctl;
@@ -1361,18 +1381,28 @@ u32 tail_cluster_ctas() {
     return kTailCTAs;
 }
 
-// CTAs per SM that fit every variant of the two-kernel round.
+// CTAs per SM of the relax kernel (every variant fits), and of the
+// lower-bound kernel, which is compiled for more CTAs per SM.
 int round_blocks_per_sm(int threads) {
     if (round_kernels_init() != cudaSuccess) return 1;
     int best = 1 << 30;
     for (int m = 0; m < 2; ++m)
         for (int nw = 0; nw < 2; ++nw) {
-            int a = 0, b = 0;
+            int a = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, relax_fn(m, nw), threads,
                                                           relax_smem_bytes(nw));
+            best = a < best ? a : best;
+        }
+    return best;
+}
+int cupdate_blocks_per_sm(int threads) {
+    if (round_kernels_init() != cudaSuccess) return 1;
+    int best = 1 << 30;
+    for (int m = 0; m < 2; ++m)
+        for (int nw = 0; nw < 2; ++nw) {
+            int b = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cupdate_fn(m, nw), threads,
                                                           cupdate_smem_bytes(nw));
-            best = a < best ? a : best;
             best = b < best ? b : best;
         }
     return best;

@@ -76,6 +76,7 @@ int open_impl(sssp_server* s) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     c.grid = std::max(1, sms) * std::max(1, round_blocks_per_sm(kThreads));
+    c.grid_cup = std::max(1, sms) * std::max(1, cupdate_blocks_per_sm(kThreads));
     c.grid_solve = std::max(1, sms) * std::max(1, solve_blocks_per_sm(kThreads));
     RoundParams& P = c.P;
     RC(c.pool.get(&P.rec, nrec));
