@@ -59,7 +59,8 @@ def _bind(lib):
     lib.orc_floyd_warshall.restype = c_int
     lib.orc_floyd_warshall.argtypes = [u32, vp, vp, vp, u32, vp]
     lib.orc_round.restype = c_int
-    lib.orc_round.argtypes = [u32, vp, vp, vp, u32, u32, vp, vp, vp, vp, vp, vp, ROUND_CB, vp]
+    lib.orc_round.argtypes = [u32, vp, vp, vp, u32, u32, ctypes.c_int64, vp, vp, vp, vp, vp, vp,
+                              ROUND_CB, vp]
     lib.orc_prune.restype = c_int
     lib.orc_prune.argtypes = [u32, vp, vp, u32, vp]
     for f in (lib.orc_sp1, lib.orc_sp2):
@@ -147,11 +148,13 @@ class RoundResult:
     stats: dict
 
 
-def round_r(g, s: int, mode: int = RULE_THR, on_round=None, lib=None) -> RoundResult:
+def round_r(g, s: int, mode: int = RULE_THR, on_round=None, lib=None,
+            target: int | None = None) -> RoundResult:
     """Sequential Round R (the SP_3/SP_4 round; see oracle.c).
 
     on_round(round, thr, minD, D, C, fixed_round) is called after every round
-    with numpy views of the state (valid only during the call)."""
+    with numpy views of the state (valid only during the call).  target: stop
+    after the round that fixes this vertex (single-target query)."""
     lib = lib or load()
     rp, col, w = _csr(g)
     n = g.n
@@ -171,7 +174,8 @@ def round_r(g, s: int, mode: int = RULE_THR, on_round=None, lib=None) -> RoundRe
     else:
         cb = ROUND_CB()
     _check(lib.orc_round(n, rp.ctypes.data, col.ctypes.data, w.ctypes.data, s, mode,
-                         dist.ctypes.data, parent.ctypes.data, C.ctypes.data, fr.ctypes.data,
+                         -1 if target is None else int(target), dist.ctypes.data,
+                         parent.ctypes.data, C.ctypes.data, fr.ctypes.data,
                          ctypes.byref(rounds), stats.ctypes.data, cb, None), "round")
     return RoundResult(dist, parent, C, fr, int(rounds.value),
                        {k: int(v) for k, v in zip(_STATS, stats)})

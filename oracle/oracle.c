@@ -227,7 +227,7 @@ int orc_floyd_warshall(uint32_t n, const uint64_t* row_ptr, const uint32_t* col,
 /* ----------------------------------------------------------------- Round R */
 
 int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* w,
-              uint32_t s, uint32_t mode,
+              uint32_t s, uint32_t mode, int64_t target,
               uint64_t* dist, uint32_t* parent, uint64_t* C_out, int32_t* fixed_round,
               uint32_t* rounds_out, uint64_t* stats, orc_round_cb cb, void* ctx) {
     /*
@@ -256,7 +256,7 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
      * discovered vertices; a vertex whose D is unchanged has nothing new to
      * relax), each with the D it had at the start of the step.
      */
-    if (s >= n) return ORC_EINVAL;
+    if (s >= n || target >= (int64_t)n) return ORC_EINVAL;
     const int rule_mind = (mode & ORC_RULE_MIND) != 0;
     const int label_correct = (mode & ORC_LABEL_CORRECT) != 0;
     uint64_t m = row_ptr[n];
@@ -302,6 +302,7 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
     uint64_t nf = 1, na = 0;
     front[0] = s;
     uint32_t r = 0;
+    if (target == (int64_t)s) nf = 0;   /* the source is fixed before round 1 */
 
     while (nf > 0) {
         r++;
@@ -376,6 +377,7 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
         nf = nf2;
         na = na2;
         if (cb) cb(ctx, r, thr, minD, D, C, fr);
+        if (target >= 0 && fr[target] >= 0) break;   /* single-target query answered */
     }
 
     uint64_t reached = 0;

@@ -79,9 +79,12 @@ int orc_floyd_warshall(uint32_t n, const uint64_t* row_ptr, const uint32_t* col,
 /* The data-parallel round of SP_3/SP_4 executed sequentially ("Round R").
  * Outputs (all nullable except dist): dist, parent (u32, UINT32_MAX if
  * unreachable), C (final lower bounds), fixed_round (-1 if never fixed),
- * rounds_out, stats[ORC_NSTATS].  cb (nullable) is called after each round. */
+ * rounds_out, stats[ORC_NSTATS].  cb (nullable) is called after each round.
+ * target >= 0: single-target query (Sec. I: the method also answers the
+ * distance to one vertex): stop after the round in which target is fixed
+ * (no round when target = s). */
 int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* w,
-              uint32_t s, uint32_t mode,
+              uint32_t s, uint32_t mode, int64_t target,
               uint64_t* dist, uint32_t* parent, uint64_t* C_out, int32_t* fixed_round,
               uint32_t* rounds_out, uint64_t* stats, orc_round_cb cb, void* ctx);
 

@@ -338,3 +338,36 @@ def test_multi_edges_and_self_loops():
     assert oracle.round_r(g, 0).dist.tolist() == [0, 2, 6]
     with pytest.raises(ValueError):
         oracle.round_r(gg.from_edges(2, [(0, 1, 0)]), 0)
+
+
+# ------------------------------------------------ single-target query (Sec. I)
+
+def test_single_target_query_is_the_full_run_cut_at_the_targets_round():
+    """Stopping when the target is fixed gives exactly the state of the full
+    run after round fixed_round[target], and the target's distance is the
+    textbook one (Dijkstra); a target equal to the source needs no round; an
+    unreachable target runs to completion."""
+    g = gg.random_var_graph(1500, 1, 7, 1, 90, 77)
+    snaps = []
+    full = oracle.round_r(g, 0, on_round=lambda r, thr, mD, D, C, F: snaps.append(
+        (D.copy(), C.copy(), F.copy())))
+    dj, _ = oracle.dijkstra(g, 0)
+    reach = np.flatnonzero(full.fixed_round >= 0)
+    assert len(reach) > 100
+    for t in [int(x) for x in reach[:: max(1, len(reach) // 25)]] + [int(reach[-1])]:
+        res = oracle.round_r(g, 0, target=t)
+        k = int(full.fixed_round[t])
+        assert res.rounds == k
+        assert res.dist[t] == dj[t]
+        if k > 0:
+            D, C, F = snaps[k - 1]
+            assert np.array_equal(res.dist, D)
+            assert np.array_equal(res.C, C)
+            assert np.array_equal(res.fixed_round, F)
+    src = oracle.round_r(g, 0, target=0)
+    assert src.rounds == 0 and src.dist[0] == 0
+    assert np.count_nonzero(src.dist != INF) == 1
+    unreach = np.flatnonzero(full.fixed_round < 0)
+    if len(unreach):
+        res = oracle.round_r(g, 0, target=int(unreach[0]))
+        assert res.rounds == full.rounds and np.array_equal(res.dist, full.dist)
