@@ -9,7 +9,7 @@ the same metric through the host-pointer API (sssp_solve: distances copied
 back to host memory every solve).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--config rmat22|random4096|grid|dag|unitgrid|batch|msrc|serve]
+                  [--config rmat22|random4096|grid|dag|unitgrid|batch|msrc|serve|p2p]
 
 Multi-GPU: replicas only (queries are independent); each rank solves the same
 8 sources on its own GPU, `value` sums all ranks' edges over the slowest
@@ -18,7 +18,9 @@ rank's time ("scaling": "weak").
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import re
 import math
 import os
 import statistics
@@ -158,6 +160,32 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def kernel_source_sha256():
+    """sha256 over the round kernels' sources (layout header, then kernels)."""
+    h = hashlib.sha256()
+    for f in ("sssp_dev.cuh", "sssp_round.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1812_10499_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel, config):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of this
+    workload, or None when there is none or the kernel source has changed
+    since it was captured (the summary records the source's sha256)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{config}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, None
+    fields = dict(re.findall(r"^(\w+): (\S+)$", text, flags=re.M))
+    sha = kernel_source_sha256()
+    if fields.get("kernel_source_sha256") != sha or "traffic_bytes_per_launch" not in fields:
+        return None, f"profiles/{kernel}_{config}.md is stale (kernel source changed)"
+    return float(fields["traffic_bytes_per_launch"]), (
+        f"profiles/{kernel}_{config}.md: DRAM bytes per launch over one whole solve, "
+        "ncu --cache-control none")
+
+
 def alg_bytes(info):
     relax = B_OUT_EDGE * info["out_scanned"] + B_FRONT * info["front_visits"]
     cup = B_IN_EDGE * info["in_scanned"] + B_ACTIVE * info["active_visits"]
@@ -251,7 +279,9 @@ def run_ours(args):
     clk = clocks.stop()
     ms, edges = reduce_over_ranks(dist, "cuda", ms, args.steps * m_reach)
     value = edges / (ms * 1e-3) / 1e9
-    launches = args.steps * sum((5 if args.loop == "persistent" else 4 + 2 * r) for r in rounds)
+    # Kernels launched per solve, counted by the library (start, round kernels
+    # including the cluster tail kernel of every device-loop iteration, output).
+    launches = args.steps * sum(i["kernel_launches"] for i in infos)
 
     # ---- dominant kernel: launch durations with CUDA events on the solve stream
     relax_b, cup_b = 0, 0
@@ -298,6 +328,7 @@ def run_ours(args):
         bytes_per_launch = cup_b * reps / max(1, prof["cupdate_launches"])
         timing = "CUDA events around every launch on the solve stream, host-launched rounds"
     dom_gbs = bytes_per_launch / (ms_per_launch * 1e-3) / 1e9
+    traffic, traffic_src = measured_traffic(kernel, args.config)
 
     # ---- end to end through the public host API (dist copied to host)
     e2e_steps = max(1, min(args.steps, 10))
@@ -331,7 +362,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "kernel": kernel, "achieved": dom_gbs, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": dom_gbs / peak,
-                     "traffic": None,
+                     "traffic": traffic, "traffic_source": traffic_src,
                      "bytes_per_launch": bytes_per_launch,
                      "ms_per_launch": ms_per_launch,
                      "cupdate_phase_achieved": cup_gbs, "relax_phase_achieved": relax_gbs,
@@ -364,6 +395,67 @@ def batch_graphs(count, seed, nmin=1024, nmax=262144):
               for i, n in enumerate(ns)]
     srcs = [int(gg.uniform(seed, 2 + i, 1, 0, g.n - 1)[0]) for i, g in enumerate(graphs)]
     return graphs, srcs
+
+
+def run_p2p(args):
+    """Single-target queries (Sec. I): stop once the target is fixed.  64
+    (source, target) pairs on the R-MAT scale 22 graph: 8 targets drawn
+    uniformly among the vertices each of the 8 benchmark sources reaches.
+    Per-query wall time of sssp_solve_to against a full solve from the same
+    source (both synchronous host calls, device-resident graph)."""
+    import torch
+    import graphgen as gg
+    import paper_1812_10499_gb300 as P
+    P.load()
+    torch.cuda.set_device(0)
+    g, sources, desc0 = workload("rmat22")
+    h = P.sssp_create(g.n, g.row_ptr, g.col, g.w)
+    pairs, ref = [], {}
+    for k, s in enumerate(sources):
+        d, _ = P.sssp_solve(h, s)
+        reach = np.flatnonzero(d != np.uint64(0xFFFFFFFFFFFFFFFF))
+        for i in gg.uniform(SEED + 5, k, 8, 0, len(reach) - 1):
+            t = int(reach[int(i)])
+            pairs.append((s, t))
+            ref[(s, t)] = int(d[t])
+    for _ in range(args.warmup):
+        for s, t in pairs[:8]:
+            P.sssp_solve_to(h, s, t)
+    clocks = Clocks(0)
+    clocks.start()
+    same, rounds, t_p2p = True, [], []
+    for _ in range(max(1, args.steps // 10)):
+        for s, t in pairs:
+            t0 = time.perf_counter()
+            d, r = P.sssp_solve_to(h, s, t)
+            t_p2p.append(time.perf_counter() - t0)
+            same = same and d == ref[(s, t)]
+            rounds.append(r)
+    t_full, full_rounds = [], []
+    for _ in range(max(1, args.steps // 10)):
+        for s in sources:
+            t0 = time.perf_counter()
+            info = P.sssp_solve_ex(h, s, dist=False)["info"]
+            t_full.append(time.perf_counter() - t0)
+            full_rounds.append(info["rounds"])
+    clk = clocks.stop()
+    ms_p2p = 1e3 * statistics.fmean(t_p2p)
+    ms_full = 1e3 * statistics.fmean(t_full)
+    line = {
+        "metric": "single-target SSSP queries/s (stop when the target is fixed)",
+        "value": 1e3 / ms_p2p, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_query": ms_p2p, "ms_per_query_p50":
+        1e3 * statistics.median(t_p2p), "full_solve_ms": ms_full, "speedup": ms_full / ms_p2p,
+        "mean_rounds": statistics.fmean(rounds), "full_mean_rounds": statistics.fmean(full_rounds),
+        "identical_results": bool(same), "higher_is_better": True, "dtype": "u64",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": desc0.replace("8 seeded sources one at a time",
+                                             "64 (source, target) pairs, 8 per source"),
+                   "timing": "wall clock per synchronous call (host API, graph resident)"},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    P.sssp_destroy(h)
 
 
 def run_batch(args):
@@ -611,6 +703,8 @@ def main():
         run_batch(args)
     elif args.config == "serve":
         run_serve(args)
+    elif args.config == "p2p":
+        run_p2p(args)
     else:
         run_ours(args)
 

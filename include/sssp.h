@@ -166,6 +166,10 @@ typedef struct sssp_solve_args {
                                 outputs then hold the state after that round               */
     uint32_t dev;            /* 1: output pointers are device pointers                     */
     void* cuda_stream;       /* stream for the work (NULL = legacy default stream)         */
+    uint32_t has_target;     /* 1: single-target query (Sec. I): stop after the round that
+                                fixes `target`; dist[target] is then exact, the other
+                                outputs hold the state after that round                    */
+    uint32_t target;         /* vertex id, < n (checked: SSSP_E_SOURCE_RANGE)              */
 } sssp_solve_args;
 
 typedef struct sssp_solve_info {
@@ -176,6 +180,7 @@ typedef struct sssp_solve_info {
     uint64_t in_scanned;     /* in-edges scanned by step (b)                               */
     uint64_t active_visits;  /* sum over rounds of the discovered-unfixed set size         */
     uint64_t front_visits;   /* sum over rounds of the frontier size                       */
+    uint64_t kernel_launches;/* kernels the solve launched (start, rounds, output)          */
 } sssp_solve_info;
 
 /* General form of sssp_solve.  Synchronises the stream before returning.
@@ -305,6 +310,15 @@ const char* sssp_strerror(int code);
 /* Number of vertices / edges (after self-loop removal) of a handle. */
 uint32_t sssp_num_vertices(sssp_handle h);
 uint64_t sssp_num_edges(sssp_handle h);
+
+/* Single-target query (Sec. I: the distance from source to one vertex): the
+ * rounds stop as soon as `target` is fixed, which is when its distance is
+ * known.  *dist_target (host) receives cost[target] or SSSP_DIST_INF when
+ * target is unreachable (then every round runs).  rounds_out (nullable):
+ * rounds executed (0 when target = source).  Synchronous.  Errors: as
+ * sssp_solve; SSSP_E_SOURCE_RANGE also for target >= n. */
+int sssp_solve_to(sssp_handle h, uint32_t source, uint32_t target, uint64_t* dist_target,
+                  uint32_t* rounds_out);
 
 /* State layout the handle's single-query solves run with:
  * SSSP_LAYOUT_WIDE or SSSP_LAYOUT_COMPACT (0 for a NULL handle). */

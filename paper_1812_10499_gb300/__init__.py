@@ -48,14 +48,15 @@ class sssp_solve_args(ctypes.Structure):
     _fields_ = [("dist", ctypes.c_void_p), ("parent", ctypes.c_void_p),
                 ("fixed_round", ctypes.c_void_p), ("lower", ctypes.c_void_p),
                 ("max_rounds", ctypes.c_uint32), ("dev", ctypes.c_uint32),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("has_target", ctypes.c_uint32),
+                ("target", ctypes.c_uint32)]
 
 
 class sssp_solve_info(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_uint32), ("finished", ctypes.c_uint32),
                 ("reached", ctypes.c_uint64), ("out_scanned", ctypes.c_uint64),
                 ("in_scanned", ctypes.c_uint64), ("active_visits", ctypes.c_uint64),
-                ("front_visits", ctypes.c_uint64)]
+                ("front_visits", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -122,6 +123,7 @@ def load(path: str = LIB_PATH):
         "sssp_num_vertices": (u32, [vp]),
         "sssp_num_edges": (u64, [vp]),
         "sssp_layout": (u32, [vp]),
+        "sssp_solve_to": (c_int, [vp, u32, u32, ctypes.POINTER(u64), ctypes.POINTER(u32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -259,6 +261,15 @@ def sssp_num_edges(h: int) -> int:
     return load().sssp_num_edges(h)
 
 
+def sssp_solve_to(h: int, source: int, target: int):
+    """Single-target query: (cost[target] or SSSP_DIST_INF, rounds executed)."""
+    d = ctypes.c_uint64(0)
+    r = ctypes.c_uint32(0)
+    _check(load().sssp_solve_to(h, source, target, ctypes.byref(d), ctypes.byref(r)),
+           "sssp_solve_to")
+    return int(d.value), int(r.value)
+
+
 def sssp_layout(h: int) -> int:
     """SSSP_LAYOUT_WIDE or SSSP_LAYOUT_COMPACT: the handle's state layout."""
     return load().sssp_layout(h)
@@ -286,7 +297,7 @@ def sssp_solve_device(h: int, source: int, dist_dev, stream=None, want_rounds: b
 
 
 def sssp_solve_ex(h: int, source: int, *, dist=True, parent=False, fixed_round=False,
-                  lower=False, max_rounds: int = 0, stream=None) -> dict:
+                  lower=False, max_rounds: int = 0, stream=None, target: int | None = None) -> dict:
     """Host outputs chosen by flag, plus the solve counters."""
     lib = load()
     n = lib.sssp_num_vertices(h)
@@ -305,6 +316,8 @@ def sssp_solve_ex(h: int, source: int, *, dist=True, parent=False, fixed_round=F
         out["lower"] = np.empty(n, dtype=np.uint64)
         a.lower = out["lower"].ctypes.data
     a.max_rounds = max_rounds
+    a.has_target = 0 if target is None else 1
+    a.target = 0 if target is None else int(target)
     a.dev = 0
     a.cuda_stream = _stream_ptr(stream)
     info = sssp_solve_info()

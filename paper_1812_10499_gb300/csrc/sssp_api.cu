@@ -111,6 +111,11 @@ int build_loop(Context& c) {
 // Runs rounds until the device loop stops (all queries done, stop round hit,
 // or an error).
 int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
+    // Round kernels per loop iteration (for the launch count of a solve).
+    const bool graph = loop_mode == SSSP_LOOP_GRAPH && !c.prof;
+    c.last_loop = graph ? SSSP_LOOP_GRAPH : (loop_mode == SSSP_LOOP_PERSISTENT ? loop_mode
+                                                                               : SSSP_LOOP_HOST);
+    c.launches_per_iter = c.last_loop == SSSP_LOOP_PERSISTENT ? 0 : (graph && c.tail_ctas ? 3 : 2);
     if (loop_mode == SSSP_LOOP_PERSISTENT) {
         RoundParams P = c.P;
         P.cond = 0;
@@ -513,14 +518,14 @@ int read_status(Context& c, cudaStream_t st, u32 ninst) {
 
 // Enqueues one single-query solve on `st` (no synchronisation).
 int enqueue_single(sssp_graph* h, u32 source, u32 max_rounds, cudaStream_t st, u64* dist_dev,
-                   u32* parent_dev, int* fround_dev, u64* lower_dev) {
+                   u32* parent_dev, int* fround_dev, u64* lower_dev, u32 target = kNoTarget) {
     Context& c = h->single;
     RoundParams P = c.P;
     P.g.source = source;
     c.P.g.source = source;
     k_init_records<<<c.grid, kThreads, 0, st>>>(P.rec, P.recn, P.fround, h->outw, h->in_off, h->n);
     k_reset_ctl<<<1, 32, 0, st>>>(P.ctl, 1, h->n + 2);
-    CK(launch_start(false, c.narrow, P, 0, 1, max_rounds, st));
+    CK(launch_start(false, c.narrow, P, 0, 1, max_rounds, st, target));
     RC(run_loop(c, h->opt.loop_mode, st));
     k_finalize<<<c.grid, kThreads, 0, st>>>(P.rec, P.recn, P.fround, 0, h->n, h->vbits, P.ivar,
                                             dist_dev,
@@ -760,6 +765,25 @@ void sssp_destroy(sssp_handle h) {
 
 uint32_t sssp_num_vertices(sssp_handle h) { return h ? h->n : 0; }
 uint64_t sssp_num_edges(sssp_handle h) { return h ? h->m : 0; }
+int sssp_solve_to(sssp_handle h, uint32_t source, uint32_t target, uint64_t* dist_target,
+                  uint32_t* rounds_out) {
+    if (!h || !dist_target) return SSSP_E_INVAL;
+    if (source >= h->n || target >= h->n) return SSSP_E_SOURCE_RANGE;
+    DeviceGuard dg(h->device);
+    std::lock_guard<std::mutex> lk(h->mu);
+    Context& c = h->single;
+    cudaStream_t st = h->stream;
+    RC(enqueue_single(h, source, 0, st, c.stage, nullptr, nullptr, nullptr, target));
+    u64 d = 0;
+    CK(cudaMemcpyAsync(&d, c.stage + target, sizeof(u64), cudaMemcpyDeviceToHost, st));
+    RC(read_status(c, st, 1));
+    const InstVar& v = c.h_ivar[0];
+    if (v.status != kDone && v.status != kStopped) return SSSP_E_ROUND_LIMIT;
+    *dist_target = d;
+    if (rounds_out) *rounds_out = v.rounds;
+    return SSSP_OK;
+}
+
 uint32_t sssp_layout(sssp_handle h) {
     return h ? (h->narrow ? SSSP_LAYOUT_COMPACT : SSSP_LAYOUT_WIDE) : 0u;
 }
@@ -770,6 +794,7 @@ int sssp_solve_ex(sssp_handle h, uint32_t source, const sssp_solve_args* args,
     if (source >= h->n) return SSSP_E_SOURCE_RANGE;
     sssp_solve_args a{};
     if (args) a = *args;
+    if (a.has_target && a.target >= h->n) return SSSP_E_SOURCE_RANGE;
     DeviceGuard dg(h->device);
     std::lock_guard<std::mutex> lk(h->mu);
     cudaStream_t st = a.cuda_stream ? (cudaStream_t)a.cuda_stream : h->stream;
@@ -785,7 +810,8 @@ int sssp_solve_ex(sssp_handle h, uint32_t source, const sssp_solve_args* args,
     Pool tmp;
     tmp.al = c.pool.al;
     if (a.lower && !a.dev) RC(tmp.get(&lower_dev, h->n));
-    int rc = enqueue_single(h, source, a.max_rounds, st, dist_dev, parent_dev, fround_dev, lower_dev);
+    int rc = enqueue_single(h, source, a.max_rounds, st, dist_dev, parent_dev, fround_dev, lower_dev,
+                            a.has_target ? a.target : kNoTarget);
     if (rc == SSSP_OK) rc = read_status(c, st, 1);
     if (rc == SSSP_OK && !a.dev) {
         cudaError_t e = cudaSuccess;
@@ -816,6 +842,8 @@ int sssp_solve_ex(sssp_handle h, uint32_t source, const sssp_solve_args* args,
         info->active_visits = c.h_ctl->stats[2];
         info->front_visits = c.h_ctl->stats[3];
         info->reached = c.h_ctl->stats[3];
+        info->kernel_launches = 4 + c.launches_per_iter * (u64)c.h_ctl->body_iters +
+                                (c.last_loop == SSSP_LOOP_PERSISTENT ? 1 : 0);
     }
     return SSSP_OK;
 }

@@ -69,7 +69,9 @@ struct __align__(16) InstVar {
     u32 rounds;         // rounds executed (set when the query stops)
     u32 status;         // kIdle / kRunning / kDone / kStopped
     u32 max_rounds;     // stop after this many rounds (0 = unlimited)
+    u32 target;         // single-target query: stop once this local vertex is fixed
 };
+constexpr u32 kNoTarget = 0xFFFFFFFFu;
 
 // Engine control block (one per solve context).
 struct __align__(16) Ctl {
@@ -92,7 +94,7 @@ struct __align__(16) Ctl {
     u32 tail_go;        // cluster tail kernel: run the next step (set before a cluster barrier)
     u32 cup_only;       // the round's relaxation is done (by the tail kernel): the next
                         // full-grid relax launch is skipped
-    u32 pad1;
+    u32 body_iters;     // launches of the relax kernel (one per loop iteration)
     u64 stats[4];       // out-edges scanned, in-edges scanned, active visits, frontier visits
 };
 

@@ -26,7 +26,7 @@ size_t relax_smem_bytes(bool narrow);
 size_t cupdate_smem_bytes(bool narrow);
 cudaError_t round_kernels_init();
 cudaError_t launch_start(bool multi, bool narrow, const RoundParams& P, u32 first, u32 count,
-                         u32 max_rounds, cudaStream_t st);
+                         u32 max_rounds, cudaStream_t st, u32 target = kNoTarget);
 int round_blocks_per_sm(int threads);
 int cupdate_blocks_per_sm(int threads);
 __global__ void k_init_records(VRec* rec, VRecN* recn, int* fround, const u32* outw,
@@ -156,6 +156,8 @@ struct Context {
     int grid_solve = 0;              // co-resident grid of the persistent kernel
     int grid_cup = 0;                // grid of the lower-bound kernel
     u32 tail_ctas = 0;               // cluster size of the tail kernel, 0 = not in the loop
+    u32 last_loop = 0;               // loop mode of the last run_loop
+    u32 launches_per_iter = 0;       // round kernels per loop iteration in that mode
     // Per-kernel event timing (sssp_profile).
     bool prof = false;
     std::vector<cudaEvent_t> ev;

@@ -783,6 +783,7 @@ __device__ void relax_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
 template <bool MULTI, class L>
 __global__ void __launch_bounds__(256, SSSP_MIN_CTAS) k_relax(RoundParams P) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.ctl->body_iters++;   // launch count
     if (ld_volatile(&P.ctl->status) != kRunning) return;
     if (ld_volatile(&P.ctl->cup_only)) return;     // relaxed already (tail kernel)
     relax_phase<MULTI, L>(P, s_dyn, P.ctl->round);
@@ -992,9 +993,15 @@ __device__ void round_epilogue(const RoundParams& P, u32 r) {
         InstVar* v = P.ivar + i;
         if (ld_volatile(&v->status) != kRunning) continue;
         const u32 nr = r - v->start_round + 1;
+        const u32 tgt = v->target;
         if (ld_volatile(&v->nfix[nxt]) == 0) {
             v->rounds = nr;
             v->status = kDone;
+        } else if (tgt != kNoTarget &&
+                   *(volatile const int*)&P.fround[(P.idesc ? P.idesc[i].base : P.g.base) + tgt] >=
+                       0) {
+            v->rounds = nr;                     // the target is fixed: query answered
+            v->status = kStopped;
         } else if (v->max_rounds != 0 && nr >= v->max_rounds) {
             v->rounds = nr;
             v->status = kStopped;
@@ -1248,11 +1255,16 @@ __global__ void __launch_bounds__(256, 1) k_tail(RoundParams P) {
 
 // Starts the queries in slots [first, first + count) at the control block's
 // current round: the source is fixed with D = C = 0 and forms the frontier.
+// target (single query only, kNoTarget otherwise): stop once it is fixed; a
+// target equal to the source is answered without any round.
 template <bool MULTI, class L>
-__global__ void k_start(RoundParams P, u32 first, u32 count, u32 max_rounds) {
+__global__ void k_start(RoundParams P, u32 first, u32 count, u32 max_rounds, u32 target) {
+    __shared__ u32 s_run;
     Ctl* ctl = P.ctl;
     const u32 r = ctl->round;
     const u32 cur = r & 1u;
+    if (threadIdx.x == 0) s_run = 0;
+    __syncthreads();
     for (u32 i = threadIdx.x; i < count; i += blockDim.x) {
         const u32 slot = first + i;
         const InstDesc& d = MULTI ? P.idesc[slot] : P.g;
@@ -1263,6 +1275,7 @@ __global__ void k_start(RoundParams P, u32 first, u32 count, u32 max_rounds) {
         v->start_round = r;
         v->rounds = 0;
         v->max_rounds = max_rounds;
+        v->target = target;
         const u32 s = d.source;
         const u32 g = (u32)(d.base + s);
         typename L::Rec* rs = L::rec(P) + g;
@@ -1270,16 +1283,22 @@ __global__ void k_start(RoundParams P, u32 first, u32 count, u32 max_rounds) {
         L::set_c(rs, 0, kFixed);
         L::set_c(rs, 1, kFixed);
         P.fround[g] = 0;
+        if (target == s) {            // answered: the source is fixed
+            __threadfence();
+            v->status = kStopped;
+            continue;
+        }
         const u64 odeg = d.out_off[s + 1] - d.out_off[s];
         if (odeg <= P.hub) put_small(P, P.L.FS[cur], atomicAdd(&ctl->nFS[cur], 1u), g);
         else put_hub(P, &ctl->FHpk[cur], P.L.FH[cur], P.L.FC[cur], g, odeg);
         __threadfence();
         v->status = kRunning;
+        atomicAdd(&s_run, 1u);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && s_run) {
         ctl->status = kRunning;
-        ctl->running += count;
+        ctl->running += s_run;
     }
 }
 
@@ -1314,13 +1333,13 @@ size_t solve_smem_bytes(bool narrow) {
 }
 
 cudaError_t launch_start(bool multi, bool narrow, const RoundParams& P, u32 first, u32 count,
-                         u32 max_rounds, cudaStream_t st) {
+                         u32 max_rounds, cudaStream_t st, u32 target) {
     if (multi) {
-        if (narrow) k_start<true, NarrowL><<<1, 256, 0, st>>>(P, first, count, max_rounds);
-        else k_start<true, WideL><<<1, 256, 0, st>>>(P, first, count, max_rounds);
+        if (narrow) k_start<true, NarrowL><<<1, 256, 0, st>>>(P, first, count, max_rounds, target);
+        else k_start<true, WideL><<<1, 256, 0, st>>>(P, first, count, max_rounds, target);
     } else {
-        if (narrow) k_start<false, NarrowL><<<1, 32, 0, st>>>(P, first, count, max_rounds);
-        else k_start<false, WideL><<<1, 32, 0, st>>>(P, first, count, max_rounds);
+        if (narrow) k_start<false, NarrowL><<<1, 32, 0, st>>>(P, first, count, max_rounds, target);
+        else k_start<false, WideL><<<1, 32, 0, st>>>(P, first, count, max_rounds, target);
     }
     return cudaGetLastError();
 }

@@ -212,6 +212,64 @@ def test_cluster_tail_rounds(sssp_lib, layout, tail_items, monkeypatch):
     assert part["info"]["rounds"] == ref.rounds - 3
 
 
+@LAYOUTS
+@pytest.mark.parametrize("loop", ["graph", "host", "persistent"])
+def test_single_target_query(sssp_lib, layout, loop):
+    """Stopping at the round that fixes the target: the whole state (D,
+    parents, C, fixing rounds, counters) equals the oracle's single-target
+    run, and sssp_solve_to returns the target's distance."""
+    P = sssp_lib
+    lm = {"graph": P.SSSP_LOOP_GRAPH, "host": P.SSSP_LOOP_HOST,
+          "persistent": P.SSSP_LOOP_PERSISTENT}[loop]
+    g = gg.random_var_graph(3000, 0, 8, 1, 200, 43)
+    full = oracle.round_r(g, 0)
+    reach = np.flatnonzero(full.fixed_round >= 0)
+    unreach = np.flatnonzero(full.fixed_round < 0)
+    assert len(unreach) > 0
+    order = reach[np.argsort(full.fixed_round[reach], kind="stable")]
+    targets = [0, int(order[1]), int(order[len(order) // 2]), int(order[-1]), int(unreach[0])]
+    h = P.sssp_create(g.n, g.row_ptr, g.col, g.w, options=make_opts(P, layout=layout, loop_mode=lm))
+    try:
+        for t in targets:
+            ref = oracle.round_r(g, 0, target=t)
+            out = P.sssp_solve_ex(h, 0, parent=True, fixed_round=True, lower=True, target=t)
+            assert np.array_equal(out["dist"], ref.dist), t
+            assert np.array_equal(out["parent"], ref.parent), t
+            assert np.array_equal(out["fixed_round"], ref.fixed_round), t
+            assert np.array_equal(out["lower"], ref.C), t
+            info = out["info"]
+            assert info["rounds"] == ref.rounds
+            assert info["finished"] == (1 if full.fixed_round[t] < 0 else 0)
+            assert info["out_scanned"] == ref.stats["out_scanned"]
+            assert info["in_scanned"] == ref.stats["in_scanned"]
+            d, r = P.sssp_solve_to(h, 0, t)
+            assert d == int(full.dist[t]) and r == ref.rounds
+        with pytest.raises(P.SsspError) as e:
+            P.sssp_solve_to(h, 0, g.n)
+        assert e.value.code == -3
+    finally:
+        P.sssp_destroy(h)
+
+
+def test_kernel_launch_count(sssp_lib, monkeypatch):
+    """The solve reports the kernels it launched: four start/output kernels
+    plus the round kernels of its loop mode."""
+    P = sssp_lib
+    g = gg.random_var_graph(3000, 1, 8, 1, 200, 41)
+    ref = oracle.round_r(g, 0)
+    r = ref.rounds
+    host = gpu_solve(P, g, 0, loop_mode=P.SSSP_LOOP_HOST)["info"]
+    assert host["kernel_launches"] == 4 + 2 * 16 * ((r + 15) // 16)   # groups of 16 rounds
+    pers = gpu_solve(P, g, 0, loop_mode=P.SSSP_LOOP_PERSISTENT)["info"]
+    assert pers["kernel_launches"] == 5
+    monkeypatch.setenv("SSSP_TAIL_ITEMS", "0")
+    plain = gpu_solve(P, g, 0)["info"]
+    assert plain["kernel_launches"] == 4 + 2 * r                       # relax + cupdate per round
+    monkeypatch.setenv("SSSP_TAIL_ITEMS", "1000000")
+    tail = gpu_solve(P, g, 0)["info"]                                  # rounds 2.. in the cluster
+    assert 4 + 3 <= tail["kernel_launches"] <= 4 + 3 * 2
+
+
 def test_layout_selection(sssp_lib):
     """The automatic layout is compact exactly when n * max weight < 2^31 - 1;
     a graph whose distances need more than 31 bits solves with wide records,
