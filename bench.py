@@ -38,6 +38,8 @@ SEED = 1812_10499
 METRIC = "SSSP GTEPS and % HBM roofline at 1 GB300; batched queries/s and p99 vs plain loop"
 # Per-vertex state layout of the round kernels (SSSP_LAYOUT_*).
 LAYOUTS = {"auto": 0, "wide": 1, "compact": 2}
+# Round rule (SSSP_RULE_* bits): threshold clamp, minD clamp, label-correcting.
+RULES = {"thr": 0, "mind": 1, "lc": 2, "lc-mind": 3}
 
 # Algorithmic bytes (what the round must move, at element size):
 #   per out-edge scanned by k_relax: 8 B {target, w} + 8 B target D word;
@@ -243,11 +245,16 @@ def run_ours(args):
     opt.loop_mode = {"persistent": P.SSSP_LOOP_PERSISTENT, "graph": P.SSSP_LOOP_GRAPH,
                      "host": P.SSSP_LOOP_HOST}[args.loop]
     opt.layout = LAYOUTS[args.layout]
+    opt.rule = RULES[args.rule]
     h = P.sssp_create(g.n, g.row_ptr, g.col, g.w, options=opt)
     layout = {P.SSSP_LAYOUT_WIDE: "wide 32 B records",
               P.SSSP_LAYOUT_COMPACT: "compact 16 B records"}[P.sssp_layout(h)]
-    infos = [P.sssp_solve_ex(h, s, dist=False)["info"] for s in sources]
-    m_reach = sum(i["out_scanned"] for i in infos)
+    # Edges of the reachable vertices, each counted once (the label-correcting
+    # rule scans some of them more than once).
+    outs = [P.sssp_solve_ex(h, s) for s in sources]
+    infos = [o["info"] for o in outs]
+    deg = g.out_degree()
+    m_reach = sum(int(deg[o["dist"] != np.uint64(0xFFFFFFFFFFFFFFFF)].sum()) for o in outs)
     rounds = [i["rounds"] for i in infos]
     stream = torch.cuda.Stream()
     dd = torch.empty(g.n, dtype=torch.int64, device="cuda")
@@ -358,6 +365,7 @@ def run_ours(args):
         "data": "synthetic (seeded generator)",
         "config": {"workload": desc, "n": g.n, "m": g.m, "sources": sources,
                    "rounds": rounds, "m_reach_per_step": m_reach, "state_layout": layout,
+                   "rule": args.rule,
                    "l2": "inputs larger than L2 (CSR+CSC+state > 1 GB)",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "kernel": kernel, "achieved": dom_gbs, "peak": peak,
@@ -685,6 +693,7 @@ def main():
     ap.add_argument("--config", default="rmat22")
     ap.add_argument("--loop", default="graph", choices=["persistent", "graph", "host"])
     ap.add_argument("--layout", default="auto", choices=list(LAYOUTS))
+    ap.add_argument("--rule", default="thr", choices=list(RULES))
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=150.0)

@@ -64,6 +64,15 @@ extern "C" {
  *     round count may differ. */
 #define SSSP_RULE_THRESHOLD 0u
 #define SSSP_RULE_MIND      1u
+/* Flag OR-ed into the rule: label-correcting relaxation, SP_4 step 3 as
+ * printed (Sec. VI) -- every round relaxes the out-edges of every vertex whose
+ * D changed in the previous round's relaxation (with its D from the start of
+ * the relaxation), not only of the vertices fixed in the previous round; the
+ * loop ends when a relaxation changes nothing.  Distances are the same; the
+ * rounds, the work and the fixing rounds differ (vertices whose D is final
+ * may stay unfixed: fixed_round -1 for a reachable vertex is possible).
+ * Not available for the server (sssp_serve_submit returns SSSP_E_INVAL). */
+#define SSSP_RULE_LABEL_CORRECTING 2u
 
 /* How the rounds are sequenced.  All modes give identical results. */
 #define SSSP_LOOP_GRAPH      0u  /* two kernels per round in a CUDA graph with a device-side

@@ -24,6 +24,7 @@ SSSP_OK = 0
 SSSP_PENDING = 1
 SSSP_RULE_THRESHOLD = 0
 SSSP_RULE_MIND = 1
+SSSP_RULE_LABEL_CORRECTING = 2
 SSSP_LOOP_GRAPH = 0
 SSSP_LOOP_HOST = 1
 SSSP_LOOP_PERSISTENT = 2

@@ -275,7 +275,14 @@ int init_single_context(sssp_graph* h) {
     P.vbits = h->vbits;
     P.hub = h->opt.hub_degree;
     P.chunk = h->opt.chunk_edges;
-    P.rule = h->opt.rule;
+    P.rule = h->opt.rule & SSSP_RULE_MIND;
+    P.lc = (h->opt.rule & SSSP_RULE_LABEL_CORRECTING) ? 1u : 0u;
+    if (P.lc) {
+        RC(c.pool.get(&P.snap, h->n));
+        RC(c.pool.get(&P.chg, h->n));
+        RC(c.pool.get(&P.L.FX[0], h->n));
+        RC(c.pool.get(&P.L.FX[1], h->n));
+    }
     P.page_shift = kPageShift;
     RC(alloc_pinned(c, 1));
     CK(cudaMemsetAsync(P.L.hubmin, 0xFF, sizeof(u64) * c.capH, h->stream));
@@ -523,7 +530,8 @@ int enqueue_single(sssp_graph* h, u32 source, u32 max_rounds, cudaStream_t st, u
     RoundParams P = c.P;
     P.g.source = source;
     c.P.g.source = source;
-    k_init_records<<<c.grid, kThreads, 0, st>>>(P.rec, P.recn, P.fround, h->outw, h->in_off, h->n);
+    k_init_records<<<c.grid, kThreads, 0, st>>>(P.rec, P.recn, P.fround, h->outw, h->in_off, h->n,
+                                                P.chg);
     k_reset_ctl<<<1, 32, 0, st>>>(P.ctl, 1, h->n + 2);
     CK(launch_start(false, c.narrow, P, 0, 1, max_rounds, st, target));
     RC(run_loop(c, h->opt.loop_mode, st));
@@ -575,7 +583,14 @@ int ensure_batch(sssp_graph* h0, u64 nrec, u32 nslots, u32 npages, u64 capH, u64
     P.page_shift = kPageShift;
     P.hub = h0->opt.hub_degree;
     P.chunk = h0->opt.chunk_edges;
-    P.rule = h0->opt.rule;
+    P.rule = h0->opt.rule & SSSP_RULE_MIND;
+    P.lc = (h0->opt.rule & SSSP_RULE_LABEL_CORRECTING) ? 1u : 0u;
+    if (P.lc) {
+        RC(c->pool.get(&P.snap, nrec));
+        RC(c->pool.get(&P.chg, nrec));
+        RC(c->pool.get(&P.L.FX[0], nrec));
+        RC(c->pool.get(&P.L.FX[1], nrec));
+    }
     RC(alloc_pinned(*c, nslots));
     CK(cudaHostAlloc((void**)&c->h_desc, sizeof(InstDesc) * nslots, cudaHostAllocDefault));
     CK(cudaHostAlloc((void**)&c->h_pages, sizeof(u32) * npages, cudaHostAllocDefault));
@@ -708,7 +723,8 @@ int sssp_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t*
     if (o.hub_degree == 0) o.hub_degree = kDefaultHub;
     if (o.chunk_edges == 0) o.chunk_edges = kDefaultChunk;
     if (o.block_threads == 0) o.block_threads = kThreads;
-    if (o.rule > SSSP_RULE_MIND || o.loop_mode > SSSP_LOOP_PERSISTENT || o.chunk_edges % 32 != 0 ||
+    if ((o.rule & ~(SSSP_RULE_MIND | SSSP_RULE_LABEL_CORRECTING)) != 0 ||
+        o.loop_mode > SSSP_LOOP_PERSISTENT || o.chunk_edges % 32 != 0 ||
         o.layout > SSSP_LAYOUT_COMPACT ||
         o.hub_degree > (1u << 20) || o.chunk_edges > (1u << 20) ||
         o.block_threads != kThreads || (o.alloc == nullptr) != (o.free == nullptr))
@@ -841,7 +857,7 @@ int sssp_solve_ex(sssp_handle h, uint32_t source, const sssp_solve_args* args,
         info->in_scanned = c.h_ctl->stats[1];
         info->active_visits = c.h_ctl->stats[2];
         info->front_visits = c.h_ctl->stats[3];
-        info->reached = c.h_ctl->stats[3];
+        info->reached = c.h_ctl->stats[4];
         info->kernel_launches = 4 + c.launches_per_iter * (u64)c.h_ctl->body_iters +
                                 (c.last_loop == SSSP_LOOP_PERSISTENT ? 1 : 0);
     }

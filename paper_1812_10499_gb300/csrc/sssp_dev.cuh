@@ -95,7 +95,9 @@ struct __align__(16) Ctl {
     u32 cup_only;       // the round's relaxation is done (by the tail kernel): the next
                         // full-grid relax launch is skipped
     u32 body_iters;     // launches of the relax kernel (one per loop iteration)
-    u64 stats[4];       // out-edges scanned, in-edges scanned, active visits, frontier visits
+    u32 nFX[2];         // label-correcting: vertices fixed in the round (see Lists::FX)
+    u64 stats[5];       // out-edges scanned, in-edges scanned, active visits, frontier
+                        // visits, vertices fixed (single query)
 };
 
 // Work lists.  Small-degree vertices are processed 32 per warp with a
@@ -108,6 +110,10 @@ struct Lists {
     uint2* AH[2];
     u64* hubmin;    // per active-hub entry: running min of Eq. (1) terms
     u32* hubcnt;    // per active-hub entry: chunks finished
+    u32* FX[2];     // label-correcting: vertices fixed in the round.  Their lower-bound
+                    // word is fixed in one parity slot only; the next round's
+                    // relaxation phase copies it to the other (in label-setting mode
+                    // the frontier, which is these vertices, does it)
     u32* FC[2];     // chunk -> FH entry, written with the entry (chunks below capC)
     u32* AC[2];     // chunk -> AH entry
     u32 capS, capH; // capacities of the small and hub lists
@@ -134,6 +140,13 @@ struct RoundParams {
     u32 trace_cap;              // entries of `trace`
     u32 trace_base;             // round number of the first traced round
     u32 tail_items;             // cluster tail kernel: most work items a round may have
+    u32 lc;                     // 1: label-correcting relaxation (SP_4 step 3 as printed):
+                                // the frontier is every vertex whose D changed in the
+                                // previous round's relaxation
+    u32 pad3;
+    unsigned long long* snap;   // label-correcting: distance of each frontier vertex at
+                                // the start of the relaxation (written the round before)
+    u32* chg;                   // label-correcting: last round in which D changed
     unsigned long long cond;    // cudaGraphConditionalHandle of the device loop, 0 = none
     u64* trace;                 // persistent kernel: globaltimer at launch, then at the end of
                                 // every phase (2 per round); nullable

@@ -30,7 +30,7 @@ cudaError_t launch_start(bool multi, bool narrow, const RoundParams& P, u32 firs
 int round_blocks_per_sm(int threads);
 int cupdate_blocks_per_sm(int threads);
 __global__ void k_init_records(VRec* rec, VRecN* recn, int* fround, const u32* outw,
-                               const u64* in_off, u32 n);
+                               const u64* in_off, u32 n, u32* chg = nullptr);
 __global__ void k_init_records_multi(RoundParams P, u64 nrec, u32 first_page, u32 npages);
 __global__ void k_reset_ctl(Ctl* ctl, u32 ninst, u32 round_limit);
 __global__ void k_finalize(const VRec* rec, const VRecN* recn, const int* frec, u64 base, u32 n,

@@ -358,8 +358,8 @@ __device__ __forceinline__ void fold(const RoundParams& P, u32 inst, u32 slot, u
 
 // Flush register folds and counters at the end of a phase (all lanes).
 template <bool MULTI>
-__device__ __forceinline__ void flush(const RoundParams& P, u32 slot, Acc& a, u32 lane,
-                                      int stat_edges, int stat_visits) {
+__device__ __forceinline__ void flush(const RoundParams& P, u32 slot, u32 nfix_slot, Acc& a,
+                                      u32 lane, int stat_edges, int stat_visits) {
     const u64 e = warp_sum64(a.edges), v = warp_sum64(a.visits);
     const u64 nf = warp_sum64(a.nfix);
     if (!MULTI) {
@@ -375,7 +375,7 @@ __device__ __forceinline__ void flush(const RoundParams& P, u32 slot, Acc& a, u3
                 if (d != kInf64) atomicMin(&P.ivar[0].minD[slot], d);
                 if (t != kInf64) atomicMin(&P.ivar[0].thr[slot], t);
             }
-            if (nf) atomicAdd(&P.ivar[0].nfix[slot], (u32)nf);
+            if (nf) atomicAdd(&P.ivar[0].nfix[nfix_slot], (u32)nf);
         }
     }
     if (lane == 0) {
@@ -609,9 +609,10 @@ __device__ __forceinline__ void relax_issue(const RoundParams& P,
 // whose D was infinite is newly discovered and joins the active set.
 template <bool MULTI, class L>
 __device__ __forceinline__ void relax_consume(const RoundParams& P, u32 cur, Acc& a, WarpQueue& q,
-                                              Pend& pd, u32 lane) {
+                                              WarpQueue& qf, Pend& pd, u32 lane) {
     if (!pd.any) return;
     pd.any = false;
+    const u32 nxt = cur ^ 1u;
 #pragma unroll
     for (u32 i = 0; i < kBI; ++i) {
         const bool ok = pd.cand[i] < pd.old[i];
@@ -643,12 +644,29 @@ __device__ __forceinline__ void relax_consume(const RoundParams& P, u32 cur, Acc
             }
             put_hub(P, &P.ctl->AHpk[cur], P.L.AH[cur], P.L.AC[cur], pd.gy[i], deg);
         }
+        if (P.lc) {
+            // Label-correcting: a target whose D changed is relaxed again in
+            // the next round (once, however often it changed in this one).
+            const u32 r = P.ctl->round;
+            const bool chg = ok && atomicExch(&P.chg[pd.gy[i]], r) != r;
+            u64 odeg = 0;
+            if (chg) {
+                const InstDesc& d = MULTI ? P.idesc[pd.inst[i]] : P.g;
+                odeg = d.out_off[pd.yl[i] + 1] - d.out_off[pd.yl[i]];
+                if (MULTI) atomicAdd(&P.ivar[pd.inst[i]].nfix[nxt], 1u);
+                else a.nfix++;
+            }
+            const bool fs = chg && odeg <= P.hub;
+            wq_push(P, qf, &P.ctl->nFS[nxt], P.L.FS[nxt], fs, pd.gy[i], lane);
+            if (chg && !fs) put_hub(P, &P.ctl->FHpk[nxt], P.L.FH[nxt], P.L.FC[nxt], pd.gy[i], odeg);
+        }
     }
 }
 
 template <bool MULTI, class L>
 __device__ void relax_small(const RoundParams& P, WarpStage<typename L::RSlot>& st, u32 t,
-                            u32 nfs, u32 cur, u32 lane, Acc& a, WarpQueue& q, Pend& pd) {
+                            u32 nfs, u32 cur, u32 lane, Acc& a, WarpQueue& q, WarpQueue& qf,
+                            Pend& pd) {
     const u32 idx = t * 32 + lane;
     const bool valid = idx < nfs;
     u32 g = 0, xloc = 0, inst = 0, deg = 0;
@@ -664,7 +682,9 @@ __device__ void relax_small(const RoundParams& P, WarpStage<typename L::RSlot>& 
         deg = (u32)(d.out_off[xloc + 1] - b);
         typename L::Rec* rx = L::rec(P) + g;
         rx->cf[cur ^ 1] = rx->cf[cur];              // keep both copies "fixed"
-        dx = L::ld_dc(rx, cur).y & kCMask;          // C = D for a fixed vertex
+        // Label-setting: C = D for a fixed vertex.  Label-correcting: the
+        // distance at the start of this relaxation step.
+        dx = P.lc ? P.snap[g] : (L::ld_dc(rx, cur).y & kCMask);
         a.visits++;
     }
     Tile tl = make_tile(st, deg, (u64)(adj + b), lane);
@@ -675,7 +695,7 @@ __device__ void relax_small(const RoundParams& P, WarpStage<typename L::RSlot>& 
             issue_dc<MULTI, L>(P, st, as, ds, min(kB, tl.total - bb * kB), cur, gbase, true, lane);
         },
         [&](u32 bb, u32 as, u32 ds) {
-            relax_consume<MULTI, L>(P, cur, a, q, pd, lane);
+            relax_consume<MULTI, L>(P, cur, a, q, qf, pd, lane);
             relax_issue<MULTI, L>(P, st, as, ds, min(kB, tl.total - bb * kB), cur, true, dx, xloc,
                                   gbase, inst, a, pd, lane);
         });
@@ -683,7 +703,7 @@ __device__ void relax_small(const RoundParams& P, WarpStage<typename L::RSlot>& 
 
 template <bool MULTI, class L>
 __device__ void relax_hub(const RoundParams& P, WarpStage<typename L::RSlot>& st, u32 c, u32 nfh,
-                          u32 cur, u32 lane, Acc& a, WarpQueue& q, Pend& pd) {
+                          u32 cur, u32 lane, Acc& a, WarpQueue& q, WarpQueue& qf, Pend& pd) {
     const uint2* FH = P.L.FH[cur];
     const uint2 ent = FH[hub_entry(P, FH, P.L.FC[cur], nfh, c)];
     const u32 g = ent.x, k = c - ent.y;
@@ -694,7 +714,7 @@ __device__ void relax_hub(const RoundParams& P, WarpStage<typename L::RSlot>& st
     const u64 cb = b + (u64)k * P.chunk;
     const u64 ce = umin64(cb + P.chunk, e_end);
     typename L::Rec* rx = L::rec(P) + g;
-    const u64 dx = L::ld_dc(rx, cur).y & kCMask;
+    const u64 dx = P.lc ? P.snap[g] : (L::ld_dc(rx, cur).y & kCMask);
     if (k == 0 && lane == 0) {
         rx->cf[cur ^ 1] = rx->cf[cur];
         a.visits++;
@@ -707,7 +727,7 @@ __device__ void relax_hub(const RoundParams& P, WarpStage<typename L::RSlot>& st
             issue_dc<MULTI, L>(P, st, as, ds, min(kB, n - bb * kB), cur, d.base, false, lane);
         },
         [&](u32 bb, u32 as, u32 ds) {
-            relax_consume<MULTI, L>(P, cur, a, q, pd, lane);
+            relax_consume<MULTI, L>(P, cur, a, q, qf, pd, lane);
             relax_issue<MULTI, L>(P, st, as, ds, min(kB, n - bb * kB), cur, false, dx, xloc,
                                   d.base, inst, a, pd, lane);
         });
@@ -715,7 +735,7 @@ __device__ void relax_hub(const RoundParams& P, WarpStage<typename L::RSlot>& st
 
 template <class L>
 constexpr size_t relax_smem() {
-    return sizeof(WarpStage<typename L::RSlot>) * kWarps + sizeof(u32) * kWarps * kQCap;
+    return sizeof(WarpStage<typename L::RSlot>) * kWarps + 2 * sizeof(u32) * kWarps * kQCap;
 }
 template <class L>
 constexpr size_t cupdate_smem() {
@@ -735,21 +755,26 @@ __device__ void relax_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
 
     if (blockIdx.x == 0) {
         // Open the slots of round r + 1 (last read in round r - 1).
+        // (Label-correcting: this relaxation appends the next frontier, so
+        // its lists and counts were cleared by the previous round's end.)
         if (threadIdx.x == 0) {
             // Watchdog: every round advances ctl->round, so more loop bodies
             // than the round limit means the epilogue stopped running.
             if (++ctl->loop_iters > ctl->round_limit) ctl->status = kErrRounds;
-            ctl->nFS[nxt] = 0;
+            if (!P.lc) {
+                ctl->nFS[nxt] = 0;
+                ctl->FHpk[nxt] = 0;
+            }
             ctl->nAS[nxt] = 0;
-            ctl->FHpk[nxt] = 0;
             ctl->AHpk[nxt] = 0;
+            ctl->nFX[nxt] = 0;
             ctl->work[1] = 0;
             ctl->done_ctas = 0;
         }
         for (u32 i = threadIdx.x; i < ctl->ninst; i += blockDim.x) {
             P.ivar[i].thr[nxt] = kInf64;
             P.ivar[i].minD[nxt] = kInf64;
-            P.ivar[i].nfix[nxt] = 0;
+            if (!P.lc) P.ivar[i].nfix[nxt] = 0;
         }
     }
 
@@ -759,25 +784,38 @@ __device__ void relax_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
     const u64 fhpk = ctl->FHpk[cur];
     const u32 nfh = min((u32)(fhpk >> 32), P.L.capH), fh_chunks = (u32)fhpk;
     const u32 tiles = (nfs + 31) >> 5;
-    const u32 total = tiles + fh_chunks;
+    // Label-correcting: copy the fixed lower-bound word of the vertices
+    // fixed last round into the other parity slot (32 per item).
+    const u32 nfx = P.lc ? min(ctl->nFX[cur], P.L.capS) : 0u;
+    const u32 total = tiles + fh_chunks + ((nfx + 31) >> 5);
 
     Acc a = {kInf64, kInf64, 0, 0, 0};
     WarpQueue q = {s_q + wib * kQCap, 0};
+    WarpQueue qf = {s_q + (kWarps + wib) * kQCap, 0};   // label-correcting next frontier
     Pend pd;
     pd.any = false;
     // First item per warp is static (no atomic); the rest are pulled.
     const u32 nwarps = gridDim.x * kWarps;
     for (u32 item = blockIdx.x * kWarps + wib; item < total;) {
-        if (item < tiles) relax_small<MULTI, L>(P, s_st[wib], item, nfs, cur, lane, a, q, pd);
-        else relax_hub<MULTI, L>(P, s_st[wib], item - tiles, nfh, cur, lane, a, q, pd);
+        if (item < tiles) {
+            relax_small<MULTI, L>(P, s_st[wib], item, nfs, cur, lane, a, q, qf, pd);
+        } else if (item < tiles + fh_chunks) {
+            relax_hub<MULTI, L>(P, s_st[wib], item - tiles, nfh, cur, lane, a, q, qf, pd);
+        } else {
+            const u32 idx = (item - tiles - fh_chunks) * 32 + lane;
+            if (idx < nfx) {
+                typename L::Rec* rx = L::rec(P) + P.L.FX[cur][idx];
+                rx->cf[nxt] = rx->cf[cur];
+            }
+        }
         if (total <= nwarps) break;                // the static items were all
         u32 next = 0;
         if (lane == 0) next = atomicAdd(&ctl->work[0], 1u) + nwarps;
         item = __shfl_sync(kFull, next, 0);
     }
-    relax_consume<MULTI, L>(P, cur, a, q, pd, lane);
-    wq_flush(P, q, &ctl->nAS[cur], P.L.AS[cur], lane);
-    flush<MULTI>(P, cur, a, lane, 0, 3);
+    relax_consume<MULTI, L>(P, cur, a, q, qf, pd, lane);
+    wq_flush2(P, q, &ctl->nAS[cur], P.L.AS[cur], qf, &ctl->nFS[nxt], P.L.FS[nxt], lane);
+    flush<MULTI>(P, cur, nxt, a, lane, 0, 3);
 }
 
 template <bool MULTI, class L>
@@ -897,9 +935,12 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
         a.visits++;
     }
     __syncwarp();
-    const bool fx = valid && fix, sv = valid && !fix;
+    // Label-setting: the fixed vertices are the next frontier.  (Label-
+    // correcting: the relaxation built it; the fixed vertices go to FX.)
+    const bool fx = valid && fix && !P.lc, sv = valid && !fix;
     const bool fs = fx && odeg <= P.hub;
-    wq_push(P, qf, &P.ctl->nFS[nxt], P.L.FS[nxt], fs, g, lane);
+    if (P.lc) wq_push(P, qf, &P.ctl->nFX[nxt], P.L.FX[nxt], valid && fix, g, lane);
+    else wq_push(P, qf, &P.ctl->nFS[nxt], P.L.FS[nxt], fs, g, lane);
     if (fx && !fs) put_hub(P, &P.ctl->FHpk[nxt], P.L.FH[nxt], P.L.FC[nxt], g, odeg);
     wq_push(P, qa, &P.ctl->nAS[nxt], P.L.AS[nxt], sv, g, lane);
     if (MULTI) {
@@ -968,11 +1009,15 @@ __device__ void cup_hub(const RoundParams& P, WarpStage<typename L::CSlot>& st, 
     a.visits++;
     if (fix) {
         P.fround[g] = (int)r;
-        const u64 odeg = d.out_off[yloc + 1] - d.out_off[yloc];
-        if (odeg <= P.hub) put_small(P, P.L.FS[nxt], atomicAdd(&P.ctl->nFS[nxt], 1u), g);
-        else put_hub(P, &P.ctl->FHpk[nxt], P.L.FH[nxt], P.L.FC[nxt], g, odeg);
-        if (MULTI) atomicAdd(&P.ivar[inst].nfix[nxt], 1u);
-        else an.nfix++;
+        if (!P.lc) {
+            const u64 odeg = d.out_off[yloc + 1] - d.out_off[yloc];
+            if (odeg <= P.hub) put_small(P, P.L.FS[nxt], atomicAdd(&P.ctl->nFS[nxt], 1u), g);
+            else put_hub(P, &P.ctl->FHpk[nxt], P.L.FH[nxt], P.L.FC[nxt], g, odeg);
+            if (MULTI) atomicAdd(&P.ivar[inst].nfix[nxt], 1u);
+            else an.nfix++;
+        } else {
+            put_small(P, P.L.FX[nxt], atomicAdd(&P.ctl->nFX[nxt], 1u), g);
+        }
     } else {
         put_hub(P, &P.ctl->AHpk[nxt], P.L.AH[nxt], P.L.AC[nxt], g, ie - ib);
         fold<MULTI>(P, inst, nxt, dy, outw == kNoOutW ? P.dinf : dy + outw, an);
@@ -1010,9 +1055,21 @@ __device__ void round_epilogue(const RoundParams& P, u32 r) {
         }
     }
     if (running) atomicAdd(&s_running, running);
+    if (P.lc) {
+        // Label-correcting: the next relaxation appends the frontier after
+        // it into slot r & 1 (read for the last time in this round).
+        for (u32 i = threadIdx.x; i < ninst; i += blockDim.x) P.ivar[i].nfix[r & 1u] = 0;
+        if (threadIdx.x == 0) {
+            ctl->nFS[r & 1u] = 0;
+            ctl->FHpk[r & 1u] = 0;
+        }
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         const u32 total = s_running;
+        // Vertices fixed this round (single query): label-setting counts them
+        // in nfix, label-correcting lists them in FX.
+        if (ninst == 1) ctl->stats[4] += P.lc ? ctl->nFX[nxt] : P.ivar[0].nfix[nxt];
         ctl->running = total;
         ctl->cup_only = 0;
         ctl->round = r + 1;
@@ -1024,6 +1081,26 @@ __device__ void round_epilogue(const RoundParams& P, u32 r) {
         if (P.cond)
             cudaGraphSetConditional(P.cond, (st == kRunning && r + 1 <= ctl->stop_round) ? 1u : 0u);
     }
+}
+
+// Label-correcting: one item of the next frontier's distance snapshot (32
+// entries of the small list, then 32 of the hub list).
+template <class L>
+__device__ __forceinline__ void snap_frontier(const RoundParams& P, u32 k, u32 nxt, u32 sfs,
+                                              u32 sfh, u32 lane) {
+    const u32 fs_tiles = (sfs + 31) >> 5;
+    u32 g = 0;
+    bool ok;
+    if (k < fs_tiles) {
+        const u32 idx = k * 32 + lane;
+        ok = idx < sfs;
+        if (ok) g = P.L.FS[nxt][idx];
+    } else {
+        const u32 idx = (k - fs_tiles) * 32 + lane;
+        ok = idx < sfh;
+        if (ok) g = P.L.FH[nxt][idx].x;
+    }
+    if (ok) P.snap[g] = L::rec(P)[g].dp >> P.vbits;
 }
 
 // Steps (b) and (c) of round r over the whole active set (all CTAs).
@@ -1043,7 +1120,15 @@ __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r)
     const u64 ahpk = ctl->AHpk[cur];
     const u32 nah = min((u32)(ahpk >> 32), P.L.capH), ah_chunks = (u32)ahpk;
     const u32 tiles = (nas + 31) >> 5;
-    const u32 total = tiles + ah_chunks;
+    // Label-correcting: also record the distance of every next-frontier
+    // vertex while D is stable (its relaxation reads it next round).
+    u32 sfs = 0, sfh = 0, snap_items = 0;
+    if (P.lc) {
+        sfs = min(ctl->nFS[nxt], P.L.capS);
+        sfh = min((u32)(ctl->FHpk[nxt] >> 32), P.L.capH);
+        snap_items = ((sfs + 31) >> 5) + ((sfh + 31) >> 5);
+    }
+    const u32 total = tiles + ah_chunks + snap_items;
     u64 thr = kInf64, minD = kInf64;
     if (!MULTI) {
         thr = P.ivar[0].thr[cur];
@@ -1059,19 +1144,23 @@ __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r)
         if (item < tiles)
             cup_small<MULTI, L>(P, s_st[wib], item, nas, r, cur, lane, s_min + wib * 32, thr,
                                 minD, a, an, qf, qa);
-        else
+        else if (item < tiles + ah_chunks)
             cup_hub<MULTI, L>(P, s_st[wib], item - tiles, nah, r, cur, lane, thr, minD, a, an);
+        else
+            snap_frontier<L>(P, item - tiles - ah_chunks, nxt, sfs, sfh, lane);
         __syncwarp();
         if (total <= nwarps) break;                // the static items were all
         u32 next = 0;
         if (lane == 0) next = atomicAdd(&ctl->work[1], 1u) + nwarps;
         item = __shfl_sync(kFull, next, 0);
     }
-    wq_flush2(P, qf, &ctl->nFS[nxt], P.L.FS[nxt], qa, &ctl->nAS[nxt], P.L.AS[nxt], lane);
+    // (Label-correcting: qf carries the vertices fixed this round, to FX.)
+    if (P.lc) wq_flush2(P, qf, &ctl->nFX[nxt], P.L.FX[nxt], qa, &ctl->nAS[nxt], P.L.AS[nxt], lane);
+    else wq_flush2(P, qf, &ctl->nFS[nxt], P.L.FS[nxt], qa, &ctl->nAS[nxt], P.L.AS[nxt], lane);
     a.fmin_d = an.fmin_d;
     a.fmin_t = an.fmin_t;
     a.nfix = an.nfix;
-    flush<MULTI>(P, nxt, a, lane, 1, 2);
+    flush<MULTI>(P, nxt, nxt, a, lane, 1, 2);
 }
 
 template <bool MULTI, class L>
@@ -1283,6 +1372,7 @@ __global__ void k_start(RoundParams P, u32 first, u32 count, u32 max_rounds, u32
         L::set_c(rs, 0, kFixed);
         L::set_c(rs, 1, kFixed);
         P.fround[g] = 0;
+        if (P.snap) P.snap[g] = 0;    // label-correcting: relaxed in round 1 with D = 0
         if (target == s) {            // answered: the source is fixed
             __threadfence();
             v->status = kStopped;
@@ -1296,9 +1386,12 @@ __global__ void k_start(RoundParams P, u32 first, u32 count, u32 max_rounds, u32
         atomicAdd(&s_run, 1u);
     }
     __syncthreads();
-    if (threadIdx.x == 0 && s_run) {
-        ctl->status = kRunning;
-        ctl->running += s_run;
+    if (threadIdx.x == 0) {
+        ctl->stats[4] += count;       // the sources are fixed
+        if (s_run) {
+            ctl->status = kRunning;
+            ctl->running += s_run;
+        }
     }
 }
 

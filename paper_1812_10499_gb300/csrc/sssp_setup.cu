@@ -15,7 +15,7 @@ __device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
 // Every record of a single query: D = inf, C = 0 (Fig. SP_4 declarations).
 // Exactly one of rec (32-byte records) and recn (16-byte records) is set.
 __global__ void k_init_records(VRec* rec, VRecN* recn, int* fround, const u32* outw,
-                               const u64* in_off, u32 n) {
+                               const u64* in_off, u32 n, u32* chg) {
     for (u64 v = blockIdx.x * (u64)blockDim.x + threadIdx.x; v < n;
          v += (u64)gridDim.x * blockDim.x) {
         if (recn) {
@@ -34,6 +34,7 @@ __global__ void k_init_records(VRec* rec, VRecN* recn, int* fround, const u32* o
             rec[v] = r;
         }
         fround[v] = -1;
+        if (chg) chg[v] = 0;     // label-correcting change marks (rounds start at 1)
     }
 }
 
@@ -64,6 +65,7 @@ __global__ void k_init_records_multi(RoundParams P, u64 nrec, u32 first_page, u3
             P.rec[g] = r;
         }
         P.fround[g] = -1;
+        if (P.chg) P.chg[g] = 0;
     }
 }
 

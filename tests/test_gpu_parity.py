@@ -35,8 +35,10 @@ def gpu_solve(P, g, s, max_rounds=0, **opt):
 
 
 def assert_parity(P, g, s, mode=oracle.RULE_THR, **opt):
-    if mode == oracle.RULE_MIND:
-        opt.setdefault("rule", P.SSSP_RULE_MIND)
+    # The library's rule bits are the oracle's mode bits (minD clamp = 1,
+    # label-correcting = 2).
+    if mode != oracle.RULE_THR:
+        opt.setdefault("rule", mode)
     ref = oracle.round_r(g, s, mode=mode)
     out = gpu_solve(P, g, s, **opt)
     assert np.array_equal(out["dist"], ref.dist)
@@ -249,6 +251,67 @@ def test_single_target_query(sssp_lib, layout, loop):
         assert e.value.code == -3
     finally:
         P.sssp_destroy(h)
+
+
+LC_MODES = pytest.mark.parametrize("mode", [oracle.LABEL_CORRECT,
+                                            oracle.LABEL_CORRECT | oracle.RULE_MIND],
+                                   ids=["lc", "lc-mind"])
+
+
+@LAYOUTS
+@LC_MODES
+@pytest.mark.parametrize("loop", ["graph", "host", "persistent"])
+def test_label_correcting(sssp_lib, layout, mode, loop):
+    """SP_4 step 3 as printed: every vertex whose D changed is relaxed again
+    the next round.  Bit-exact with the oracle's label-correcting Round R on
+    random, skewed (with small hub thresholds) and grid graphs."""
+    P = sssp_lib
+    lm = {"graph": P.SSSP_LOOP_GRAPH, "host": P.SSSP_LOOP_HOST,
+          "persistent": P.SSSP_LOOP_PERSISTENT}[loop]
+    g = gg.random_graph(4096, 8, 1, 100, 1812_10499)
+    assert_parity(P, g, 0, mode=mode, layout=layout, loop_mode=lm)
+    g = gg.rmat(13, 8, 1, 255, 5)
+    s = int(np.argmax(g.out_degree()))
+    assert_parity(P, g, s, mode=mode, layout=layout, loop_mode=lm)
+    assert_parity(P, g, s, mode=mode, layout=layout, loop_mode=lm, hub_degree=8, chunk_edges=32)
+    assert_parity(P, gg.grid(60, 50, 1, 1000, 3), 0, mode=mode, layout=layout, loop_mode=lm)
+    g = gg.random_var_graph(2000, 0, 7, 1, 50, 9)                     # some unreachable
+    assert_parity(P, g, 3, mode=mode, layout=layout, loop_mode=lm)
+
+
+@LC_MODES
+def test_label_correcting_per_round_state(sssp_lib, mode, monkeypatch):
+    """The state after every round equals the oracle's (solves stopped with
+    max_rounds), with the small rounds in the cluster tail kernel too."""
+    monkeypatch.setenv("SSSP_TAIL_ITEMS", "1000000")
+    g = gg.random_var_graph(700, 1, 6, 1, 50, 12)
+    snaps = []
+    ref = oracle.round_r(g, 0, mode=mode, on_round=lambda r, thr, mD, D, C, F: snaps.append(
+        (D.copy(), C.copy(), F.copy())))
+    assert ref.rounds == len(snaps)
+    for r, (D, C, F) in enumerate(snaps, start=1):
+        out = gpu_solve(sssp_lib, g, 0, max_rounds=r, rule=mode)
+        assert out["info"]["rounds"] == r
+        assert np.array_equal(out["dist"], D), f"D after round {r}"
+        assert np.array_equal(out["lower"], C), f"C after round {r}"
+        assert np.array_equal(out["fixed_round"], F), f"fixed after round {r}"
+
+
+def test_label_correcting_batch(sssp_lib):
+    P = sssp_lib
+    o = P.sssp_options_default()
+    o.rule = P.SSSP_RULE_LABEL_CORRECTING
+    graphs = [gg.random_var_graph(n, 2, 10, 1, 500, 60 + i) for i, n in enumerate((300, 5000, 1200, 64))]
+    hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w, options=o) for g in graphs]
+    try:
+        srcs = [0, 7, 100, 5]
+        dists, rounds = P.sssp_solve_batch(hs, srcs)
+        for g, s, d, r in zip(graphs, srcs, dists, rounds):
+            ref = oracle.round_r(g, s, mode=oracle.LABEL_CORRECT)
+            assert np.array_equal(d, ref.dist) and int(r) == ref.rounds
+    finally:
+        for h in hs:
+            P.sssp_destroy(h)
 
 
 def test_kernel_launch_count(sssp_lib, monkeypatch):
