@@ -27,6 +27,7 @@ INF = np.uint64(0xFFFFFFFFFFFFFFFF)
 RULE_THR = 0
 RULE_MIND = 1
 LABEL_CORRECT = 2
+CHEAP_FIRST = 4
 
 _STATS = ("out_scanned", "in_scanned", "active_visits", "front_visits", "reached", "max_active")
 

@@ -259,12 +259,14 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
     if (s >= n || target >= (int64_t)n) return ORC_EINVAL;
     const int rule_mind = (mode & ORC_RULE_MIND) != 0;
     const int label_correct = (mode & ORC_LABEL_CORRECT) != 0;
+    const int cheap_first = (mode & ORC_CHEAP_FIRST) != 0;
     uint64_t m = row_ptr[n];
 
     uint64_t* col_ptr = (uint64_t*)malloc(sizeof(uint64_t) * ((size_t)n + 1));
     uint32_t* row = (uint32_t*)malloc(sizeof(uint32_t) * (m ? m : 1));
     uint32_t* w_in = (uint32_t*)malloc(sizeof(uint32_t) * (m ? m : 1));
     uint64_t* outW = (uint64_t*)malloc(sizeof(uint64_t) * n);
+    uint64_t* inW = (uint64_t*)malloc(sizeof(uint64_t) * n);
     uint64_t* D = dist;
     uint32_t* par = (uint32_t*)malloc(sizeof(uint32_t) * n);
     uint64_t* C = (uint64_t*)malloc(sizeof(uint64_t) * n);
@@ -277,9 +279,9 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
     uint64_t* Cn = (uint64_t*)malloc(sizeof(uint64_t) * n);
     uint8_t* changed = (uint8_t*)calloc(n, 1);
     uint32_t* list_mem[4] = {front, front2, act, act2};   /* freed at the end */
-    if (!col_ptr || !row || !w_in || !outW || !par || !C || !fr || !front || !front2 ||
+    if (!col_ptr || !row || !w_in || !outW || !inW || !par || !C || !fr || !front || !front2 ||
         !front_d || !act || !act2 || !Cn || !changed) {
-        free(col_ptr); free(row); free(w_in); free(outW); free(par); free(C); free(fr);
+        free(col_ptr); free(row); free(w_in); free(outW); free(inW); free(par); free(C); free(fr);
         free(front); free(front2); free(front_d); free(act); free(act2); free(Cn); free(changed);
         return ORC_ENOMEM;
     }
@@ -291,6 +293,12 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
         uint64_t mw = ORC_INF;
         for (uint64_t k = row_ptr[u]; k < row_ptr[u + 1]; ++k) mw = min_u64(mw, w[k]);
         outW[u] = mw;
+    }
+    /* inWeight[y] = min in-edge weight (SP_2, Sec. IV). */
+    for (uint32_t y = 0; y < n; ++y) {
+        uint64_t mw = ORC_INF;
+        for (uint64_t k = col_ptr[y]; k < col_ptr[y + 1]; ++k) mw = min_u64(mw, w_in[k]);
+        inW[y] = mw;
     }
 
     uint64_t st[ORC_NSTATS];
@@ -344,6 +352,10 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
             uint32_t y = act[i];
             uint64_t self = rule_mind ? minD : min_u64(D[y], thr);
             uint64_t best = ORC_INF;
+            if (cheap_first && (D[y] <= sat_add(minD, inW[y]) || D[y] <= thr)) {
+                Cn[i] = D[y];            /* fixed without reading the in-edges */
+                continue;
+            }
             st[ORC_ST_IN_SCANNED] += col_ptr[y + 1] - col_ptr[y];
             for (uint64_t k = col_ptr[y]; k < col_ptr[y + 1]; ++k) {
                 uint32_t x = row[k];
@@ -390,7 +402,7 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
     if (rounds_out) *rounds_out = r;
     if (stats) memcpy(stats, st, sizeof(st));
 
-    free(col_ptr); free(row); free(w_in); free(outW); free(par); free(C); free(fr);
+    free(col_ptr); free(row); free(w_in); free(outW); free(inW); free(par); free(C); free(fr);
     free(list_mem[0]); free(list_mem[1]); free(front_d); free(list_mem[2]); free(list_mem[3]);
     free(Cn); free(changed);
     return ORC_OK;

@@ -371,3 +371,26 @@ def test_single_target_query_is_the_full_run_cut_at_the_targets_round():
     if len(unreach):
         res = oracle.round_r(g, 0, target=int(unreach[0]))
         assert res.rounds == full.rounds and np.array_equal(res.dist, full.dist)
+
+
+# ------------------------------------- cheaper fixing rules first (SP_2 / Lemma 8)
+
+@pytest.mark.parametrize("base", [oracle.RULE_THR, oracle.RULE_MIND, oracle.LABEL_CORRECT])
+def test_cheap_rules_first_change_only_the_scan_count(base):
+    """The in-version rule D[y] <= minD + inWeight[y] and D[y] <= threshold
+    imply Eq. (1)'s bound reaches D[y]; fixing such y without reading its
+    in-edges leaves every state and round count unchanged and scans fewer
+    in-edges.  A vertex the cheap rules fix is one the full rule fixes in
+    the same round."""
+    for g, s in ((gg.rmat(12, 8, 1, 255, 4), 0), (gg.random_var_graph(3000, 1, 9, 1, 60, 8), 2),
+                 (gg.grid(40, 30, 1, 50, 1), 0)):
+        if g.out_degree()[s] == 0:
+            s = int(np.argmax(g.out_degree()))
+        a = oracle.round_r(g, s, mode=base)
+        b = oracle.round_r(g, s, mode=base | oracle.CHEAP_FIRST)
+        assert np.array_equal(a.dist, b.dist) and np.array_equal(a.parent, b.parent)
+        assert np.array_equal(a.C, b.C) and np.array_equal(a.fixed_round, b.fixed_round)
+        assert a.rounds == b.rounds
+        for k in ("out_scanned", "active_visits", "front_visits", "reached"):
+            assert a.stats[k] == b.stats[k]
+        assert b.stats["in_scanned"] < a.stats["in_scanned"]
