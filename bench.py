@@ -39,7 +39,8 @@ METRIC = "SSSP GTEPS and % HBM roofline at 1 GB300; batched queries/s and p99 vs
 # Per-vertex state layout of the round kernels (SSSP_LAYOUT_*).
 LAYOUTS = {"auto": 0, "wide": 1, "compact": 2}
 # Round rule (SSSP_RULE_* bits): threshold clamp, minD clamp, label-correcting.
-RULES = {"thr": 0, "mind": 1, "lc": 2, "lc-mind": 3}
+RULES = {"thr": 0, "mind": 1, "lc": 2, "lc-mind": 3, "thr-cheap": 4, "mind-cheap": 5,
+         "lc-cheap": 6}
 
 # Algorithmic bytes (what the round must move, at element size):
 #   per out-edge scanned by k_relax: 8 B {target, w} + 8 B target D word;
@@ -693,7 +694,7 @@ def main():
     ap.add_argument("--config", default="rmat22")
     ap.add_argument("--loop", default="graph", choices=["persistent", "graph", "host"])
     ap.add_argument("--layout", default="auto", choices=list(LAYOUTS))
-    ap.add_argument("--rule", default="thr", choices=list(RULES))
+    ap.add_argument("--rule", default="thr-cheap", choices=list(RULES))
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=150.0)

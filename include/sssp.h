@@ -73,6 +73,12 @@ extern "C" {
  * may stay unfixed: fixed_round -1 for a reachable vertex is possible).
  * Not available for the server (sssp_serve_submit returns SSSP_E_INVAL). */
 #define SSSP_RULE_LABEL_CORRECTING 2u
+/* Flag OR-ed into the rule: before scanning the in-edges of an active y, fix
+ * y at once when D[y] <= minD + inWeight[y] (the in-version rule of SP_2,
+ * Sec. IV, inWeight = least in-edge weight) or D[y] <= threshold (Lemma 8).
+ * Both imply that Eq. (1) gives C[y] = D[y], so every output is unchanged;
+ * only in_scanned (the in-edges actually read) drops. */
+#define SSSP_RULE_CHEAP_FIRST 4u
 
 /* How the rounds are sequenced.  All modes give identical results. */
 #define SSSP_LOOP_GRAPH      0u  /* two kernels per round in a CUDA graph with a device-side

@@ -25,6 +25,7 @@ SSSP_PENDING = 1
 SSSP_RULE_THRESHOLD = 0
 SSSP_RULE_MIND = 1
 SSSP_RULE_LABEL_CORRECTING = 2
+SSSP_RULE_CHEAP_FIRST = 4
 SSSP_LOOP_GRAPH = 0
 SSSP_LOOP_HOST = 1
 SSSP_LOOP_PERSISTENT = 2

@@ -260,6 +260,7 @@ int init_single_context(sssp_graph* h) {
     P.g.in_off = h->in_off;
     P.g.in_adj = h->in_adj;
     P.g.outw = h->narrow ? h->outw_pack : h->outw;
+    P.g.inw = h->inw;
     P.g.base = 0;
     P.g.n = h->n;
     P.g.source = 0;
@@ -277,6 +278,7 @@ int init_single_context(sssp_graph* h) {
     P.chunk = h->opt.chunk_edges;
     P.rule = h->opt.rule & SSSP_RULE_MIND;
     P.lc = (h->opt.rule & SSSP_RULE_LABEL_CORRECTING) ? 1u : 0u;
+    P.cheap = (h->opt.rule & SSSP_RULE_CHEAP_FIRST) ? 1u : 0u;
     if (P.lc) {
         RC(c.pool.get(&P.snap, h->n));
         RC(c.pool.get(&P.chg, h->n));
@@ -468,6 +470,9 @@ int create_impl(sssp_graph* h, u32 n, u64 m, const u64* row_ptr, const u32* col,
     }
     k_outw<<<h->grid, kThreads, 0, h->stream>>>(h->out_off, h->out_adj, n, h->outw);
     CK(cudaGetLastError());
+    RC(gp.get(&h->inw, n));   // inWeight: the same reduction over the in-edges
+    k_outw<<<h->grid, kThreads, 0, h->stream>>>(h->in_off, h->in_adj, n, h->inw);
+    CK(cudaGetLastError());
     if (h->narrow) {
         RC(gp.get(&h->outw_pack, n));
         k_pack_outw<<<h->grid, kThreads, 0, h->stream>>>(h->outw, h->in_off, n, h->opt.hub_degree,
@@ -585,6 +590,7 @@ int ensure_batch(sssp_graph* h0, u64 nrec, u32 nslots, u32 npages, u64 capH, u64
     P.chunk = h0->opt.chunk_edges;
     P.rule = h0->opt.rule & SSSP_RULE_MIND;
     P.lc = (h0->opt.rule & SSSP_RULE_LABEL_CORRECTING) ? 1u : 0u;
+    P.cheap = (h0->opt.rule & SSSP_RULE_CHEAP_FIRST) ? 1u : 0u;
     if (P.lc) {
         RC(c->pool.get(&P.snap, nrec));
         RC(c->pool.get(&P.chg, nrec));
@@ -646,13 +652,13 @@ int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist
     P.rec = narrow ? nullptr : c.rec_store;
     P.recn = narrow ? reinterpret_cast<VRecN*>(c.rec_store) : nullptr;
     P.g = InstDesc{g[0]->out_off, g[0]->out_adj, g[0]->in_off, g[0]->in_adj,
-                   narrow ? g[0]->outw_pack : g[0]->outw, 0, g[0]->n, sources[0]};
+                   narrow ? g[0]->outw_pack : g[0]->outw, g[0]->inw, 0, g[0]->n, sources[0]};
     u64 page = 0;
     for (u32 i = 0; i < k; ++i) {
         const sssp_graph* gi = g[i];
         c.h_desc[i] = InstDesc{gi->out_off, gi->out_adj, gi->in_off, gi->in_adj,
-                               narrow ? gi->outw_pack : gi->outw, page << kPageShift, gi->n,
-                               sources[i]};
+                               narrow ? gi->outw_pack : gi->outw, gi->inw, page << kPageShift,
+                               gi->n, sources[i]};
         const u64 np = ((u64)gi->n + (1u << kPageShift) - 1) >> kPageShift;
         for (u64 p = 0; p < np; ++p) c.h_pages[page + p] = i;
         page += np;
@@ -723,7 +729,7 @@ int sssp_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t*
     if (o.hub_degree == 0) o.hub_degree = kDefaultHub;
     if (o.chunk_edges == 0) o.chunk_edges = kDefaultChunk;
     if (o.block_threads == 0) o.block_threads = kThreads;
-    if ((o.rule & ~(SSSP_RULE_MIND | SSSP_RULE_LABEL_CORRECTING)) != 0 ||
+    if ((o.rule & ~(SSSP_RULE_MIND | SSSP_RULE_LABEL_CORRECTING | SSSP_RULE_CHEAP_FIRST)) != 0 ||
         o.loop_mode > SSSP_LOOP_PERSISTENT || o.chunk_edges % 32 != 0 ||
         o.layout > SSSP_LAYOUT_COMPACT ||
         o.hub_degree > (1u << 20) || o.chunk_edges > (1u << 20) ||

@@ -53,6 +53,7 @@ struct InstDesc {
     const u64* in_off;      // CSC offsets, n + 1
     const uint2* in_adj;    // {source, weight}
     const u32* outw;        // min out-weight per vertex
+    const u32* inw;         // min in-weight per vertex (kNoOutW: none), for the cheap rules
     u64 base;               // global record index of local vertex 0
     u32 n;
     u32 source;
@@ -143,7 +144,8 @@ struct RoundParams {
     u32 lc;                     // 1: label-correcting relaxation (SP_4 step 3 as printed):
                                 // the frontier is every vertex whose D changed in the
                                 // previous round's relaxation
-    u32 pad3;
+    u32 cheap;                  // 1: fix y without scanning its in-edges when
+                                // D[y] <= minD + inWeight[y] or D[y] <= threshold
     unsigned long long* snap;   // label-correcting: distance of each frontier vertex at
                                 // the start of the relaxation (written the round before)
     u32* chg;                   // label-correcting: last round in which D changed

@@ -210,6 +210,7 @@ struct sssp_graph {
     uint2* in_adj = nullptr;
     u32* outw = nullptr;
     u32* outw_pack = nullptr;        // compact layout: outWeight | in-hub flag (k_pack_outw)
+    u32* inw = nullptr;              // inWeight: min in-edge weight (kNoOutW: none)
     cudaStream_t stream = nullptr;   // internal stream for setup and host-pointer solves
     int grid = 0;
     int grid_solve = 0;

@@ -108,7 +108,7 @@ extern "C" int sssp_solve_noalloc(uint32_t n, const uint64_t* out_off, const uin
     P.L.capC = 0;   // no chunk maps here: hub chunks find their vertex by search
     P.g = InstDesc{reinterpret_cast<const u64*>(out_off), reinterpret_cast<const uint2*>(out_adj),
                    reinterpret_cast<const u64*>(in_off), reinterpret_cast<const uint2*>(in_adj),
-                   outw, 0, n, source};
+                   outw, nullptr, 0, n, source};
     P.dinf = dinf;
     P.vbits = vbits;
     P.hub = kDefaultHub;

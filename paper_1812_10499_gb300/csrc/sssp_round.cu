@@ -851,6 +851,14 @@ __device__ __forceinline__ u64 seg_min(u64 v, u32 brk, u32 lane) {
     return v;
 }
 
+// The cheaper fixing rules tried before the in-edge scan: SP_2's in-version
+// rule D[y] <= minD + inWeight[y] (Sec. IV) and D[y] <= threshold (Lemma 8).
+// Each implies that Eq. (1) gives C[y] = D[y]: a fixed in-neighbour x gives
+// D[x] + w >= D[y], an unfixed one lb(x) + w >= minD + inWeight[y].
+__device__ __forceinline__ bool cheap_rules_fix(u64 dy, u32 inw, u64 thr, u64 minD) {
+    return (inw != kNoOutW && dy <= minD + inw) || dy <= thr;
+}
+
 // Decision for one active vertex after its Eq. (1) minimum m is known.
 __device__ __forceinline__ u64 decide(const RoundParams& P, u64 dy, u64 cy, u64 m, u64 thr,
                                       u64 minD, bool& fix) {
@@ -869,6 +877,7 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
     const bool valid = idx < nas;
     u32 g = 0, yloc = 0, inst = 0, deg = 0, outw = kNoOutW;
     u64 gbase = 0, ib = 0, dy = 0, cy = 0, thr = thr0, minD = minD0, odeg = 0;
+    bool cheap_fix = false;
     const uint2* in_adj = P.g.in_adj;
     typename L::Rec* rec = L::rec(P);
     if (valid) {
@@ -889,6 +898,10 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
         dy = v.x >> P.vbits;
         cy = v.y & kCMask;
         outw = outw_of<L>(d, rec + g, yloc);
+        if (P.cheap) {
+            cheap_fix = cheap_rules_fix(dy, d.inw[yloc], thr, minD);
+            if (cheap_fix) deg = 0;                 // its in-edges are not read
+        }
     }
     smin[lane] = kInf64;
     const typename L::Bounds bd = L::bounds(thr, minD);
@@ -929,7 +942,9 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
 
     bool fix = false;
     if (valid) {
-        const u64 cn = decide(P, dy, cy, smin[lane], thr, minD, fix);
+        u64 cn = dy;
+        if (cheap_fix) fix = true;
+        else cn = decide(P, dy, cy, smin[lane], thr, minD, fix);
         L::set_c(rec + g, nxt, cn | (fix ? kFixed : 0ull));
         if (fix) P.fround[g] = (int)r;
         a.visits++;
@@ -973,7 +988,12 @@ __device__ void cup_hub(const RoundParams& P, WarpStage<typename L::CSlot>& st, 
     const u64 ce = umin64(cb + P.chunk, ie);
     const typename L::Bounds bd = L::bounds(thr, minD);
     typename L::Term tv = L::kTermInf;
-    const u32 n = ce > cb ? (u32)(ce - cb) : 0u;
+    // Cheaper rules first: every chunk of y takes the same decision.
+    bool cheap_fix = false;
+    if (P.cheap)
+        cheap_fix = cheap_rules_fix(L::ld_dc(L::rec(P) + g, cur).x >> P.vbits, d.inw[yloc], thr,
+                                    minD);
+    const u32 n = (ce > cb && !cheap_fix) ? (u32)(ce - cb) : 0u;
     run_pipeline(
         (n + kB - 1) / kB,
         [&](u32 b, u32 s) { issue_range_adj(st, s, d.in_adj, cb + b * kB, ce, lane); },
@@ -990,7 +1010,7 @@ __device__ void cup_hub(const RoundParams& P, WarpStage<typename L::CSlot>& st, 
         });
     const u64 val = warp_min64((u64)tv);
     if (lane != 0) return;
-    a.edges += ce - cb;
+    a.edges += n;
     atomicMin(&P.L.hubmin[lo], val);
     __threadfence();
     if (atomicAdd(&P.L.hubcnt[lo], 1u) != nch - 1) return;
@@ -1003,8 +1023,9 @@ __device__ void cup_hub(const RoundParams& P, WarpStage<typename L::CSlot>& st, 
     const u64 dy = v.x >> P.vbits;
     const u64 cy = v.y & kCMask;
     const u32 outw = outw_of<L>(d, ry, yloc);
-    bool fix;
-    const u64 cn = decide(P, dy, cy, m, thr, minD, fix);
+    bool fix = true;
+    u64 cn = dy;
+    if (!cheap_fix) cn = decide(P, dy, cy, m, thr, minD, fix);
     L::set_c(ry, nxt, cn | (fix ? kFixed : 0ull));
     a.visits++;
     if (fix) {

@@ -147,7 +147,7 @@ int admit(sssp_server* s) {
             c.h_pages[first + p] = slot;
         }
         const sssp_graph* g = q->g;
-        c.h_desc[slot] = InstDesc{g->out_off, g->out_adj, g->in_off, g->in_adj, g->outw,
+        c.h_desc[slot] = InstDesc{g->out_off, g->out_adj, g->in_off, g->in_adj, g->outw, g->inw,
                                   (u64)first << kPageShift, g->n, q->source};
         CK(cudaMemcpyAsync((void*)(c.P.idesc + slot), c.h_desc + slot, sizeof(InstDesc),
                            cudaMemcpyHostToDevice, s->stream));

@@ -314,6 +314,23 @@ def test_label_correcting_batch(sssp_lib):
             P.sssp_destroy(h)
 
 
+@LAYOUTS
+@pytest.mark.parametrize("base", [oracle.RULE_THR, oracle.RULE_MIND, oracle.LABEL_CORRECT],
+                         ids=["thr", "mind", "lc"])
+def test_cheap_rules_first(sssp_lib, layout, base):
+    """Cheaper fixing rules before the in-edge scan: bit-exact with the
+    oracle in the same mode, counters included (fewer in-edges read)."""
+    P = sssp_lib
+    mode = base | oracle.CHEAP_FIRST
+    assert_parity(P, gg.random_graph(4096, 8, 1, 100, 1812_10499), 0, mode=mode, layout=layout)
+    g = gg.rmat(13, 8, 1, 255, 6)
+    s = int(np.argmax(g.out_degree()))
+    assert_parity(P, g, s, mode=mode, layout=layout)
+    assert_parity(P, g, s, mode=mode, layout=layout, hub_degree=8, chunk_edges=32)
+    assert_parity(P, gg.grid(50, 40, 1, 100, 2), 0, mode=mode, layout=layout,
+                  loop_mode=P.SSSP_LOOP_PERSISTENT)
+
+
 def test_kernel_launch_count(sssp_lib, monkeypatch):
     """The solve reports the kernels it launched: four start/output kernels
     plus the round kernels of its loop mode."""
