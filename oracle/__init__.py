@@ -28,6 +28,7 @@ RULE_THR = 0
 RULE_MIND = 1
 LABEL_CORRECT = 2
 CHEAP_FIRST = 4
+ALL_UNFIXED = 8
 
 _STATS = ("out_scanned", "in_scanned", "active_visits", "front_visits", "reached", "max_active")
 

@@ -260,6 +260,7 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
     const int rule_mind = (mode & ORC_RULE_MIND) != 0;
     const int label_correct = (mode & ORC_LABEL_CORRECT) != 0;
     const int cheap_first = (mode & ORC_CHEAP_FIRST) != 0;
+    const int all_unfixed = (mode & ORC_ALL_UNFIXED) != 0;
     uint64_t m = row_ptr[n];
 
     uint64_t* col_ptr = (uint64_t*)malloc(sizeof(uint64_t) * ((size_t)n + 1));
@@ -277,12 +278,14 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
     uint32_t* act = (uint32_t*)malloc(sizeof(uint32_t) * n);
     uint32_t* act2 = (uint32_t*)malloc(sizeof(uint32_t) * n);
     uint64_t* Cn = (uint64_t*)malloc(sizeof(uint64_t) * n);
+    uint64_t* Cu = (uint64_t*)malloc(sizeof(uint64_t) * n);   /* undiscovered (ablation) */
     uint8_t* changed = (uint8_t*)calloc(n, 1);
     uint32_t* list_mem[4] = {front, front2, act, act2};   /* freed at the end */
     if (!col_ptr || !row || !w_in || !outW || !inW || !par || !C || !fr || !front || !front2 ||
-        !front_d || !act || !act2 || !Cn || !changed) {
+        !front_d || !act || !act2 || !Cn || !Cu || !changed) {
         free(col_ptr); free(row); free(w_in); free(outW); free(inW); free(par); free(C); free(fr);
-        free(front); free(front2); free(front_d); free(act); free(act2); free(Cn); free(changed);
+        free(front); free(front2); free(front_d); free(act); free(act2); free(Cn); free(Cu);
+        free(changed);
         return ORC_ENOMEM;
     }
     orc_transpose(n, row_ptr, col, w, col_ptr, row, w_in);
@@ -368,6 +371,25 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
             }
             Cn[i] = max_u64(C[y], max_u64(self, best));
         }
+        /* Ablation: the same bound for every undiscovered vertex (D = infinity,
+         * so its own clamp is the threshold, or minD with the minD rule). */
+        if (all_unfixed) {
+            for (uint32_t y = 0; y < n; ++y) {
+                if (fr[y] >= 0 || D[y] != ORC_INF) continue;
+                uint64_t best = ORC_INF;
+                st[ORC_ST_IN_SCANNED] += col_ptr[y + 1] - col_ptr[y];
+                for (uint64_t k = col_ptr[y]; k < col_ptr[y + 1]; ++k) {
+                    uint32_t x = row[k];
+                    uint64_t lb;
+                    if (rule_mind)
+                        lb = (fr[x] >= 0) ? C[x] : max_u64(C[x], minD);
+                    else
+                        lb = max_u64(C[x], min_u64(D[x], thr));
+                    best = min_u64(best, sat_add(lb, w_in[k]));
+                }
+                Cu[y] = max_u64(C[y], max_u64(rule_mind ? minD : thr, best));
+            }
+        }
 
         /* Step 4: apply C, fix C = D, split into next frontier / active. */
         uint64_t nf2 = 0, na2 = 0;
@@ -383,6 +405,9 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
                 act2[na2++] = y;
             }
         }
+        if (all_unfixed)
+            for (uint32_t y = 0; y < n; ++y)
+                if (fr[y] < 0 && D[y] == ORC_INF) C[y] = Cu[y];
         if (label_correct) nf2 = nchg;
         { uint32_t* t = front; front = front2; front2 = t; }
         { uint32_t* t = act; act = act2; act2 = t; }
@@ -404,7 +429,7 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
 
     free(col_ptr); free(row); free(w_in); free(outW); free(inW); free(par); free(C); free(fr);
     free(list_mem[0]); free(list_mem[1]); free(front_d); free(list_mem[2]); free(list_mem[3]);
-    free(Cn); free(changed);
+    free(Cn); free(Cu); free(changed);
     return ORC_OK;
 }
 

@@ -38,6 +38,8 @@
 #define ORC_RULE_THR      0u  /* clamp C by min(D, threshold)  (Lemmas 7-8)   */
 #define ORC_RULE_MIND     1u  /* clamp C by minD, fix D <= threshold (Fig. SP_4 steps 2, 4) */
 #define ORC_LABEL_CORRECT 2u  /* relax from every vertex whose D changed (SP_4 step 3) */
+#define ORC_ALL_UNFIXED   8u  /* ablation: step 4 also raises C of undiscovered vertices (Fig. SP_4
+                                 step 4 "for all unfixed"); they are never fixed (D = infinity) */
 #define ORC_CHEAP_FIRST   4u  /* before scanning y's in-edges, fix y at once when
                                  D[y] <= minD + inWeight[y] (the in-version rule of SP_2,
                                  Sec. IV) or D[y] <= threshold (Lemma 8); both imply

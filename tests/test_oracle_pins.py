@@ -394,3 +394,29 @@ def test_cheap_rules_first_change_only_the_scan_count(base):
         for k in ("out_scanned", "active_visits", "front_visits", "reached"):
             assert a.stats[k] == b.stats[k]
         assert b.stats["in_scanned"] < a.stats["in_scanned"]
+
+
+# ------------------------------------------- ablation: C for all unfixed vertices
+
+def test_all_unfixed_ablation_is_sound_and_never_slower_in_rounds():
+    """Raising C of undiscovered vertices too (step 4 "for all unfixed") keeps
+    every lower bound valid (C <= cost <= D after every round, distances the
+    textbook ones) and fixes no later: never more rounds than the active-only
+    update."""
+    for g, s in ((gg.rmat(12, 16, 1, 255, 3), None), (gg.random_graph(800, 6, 1, 50, 4), 0),
+                 (gg.grid(20, 15, 1, 100, 5), 0), (gg.dag(16, 64, 6, 3, 1, 100, 6), 0)):
+        if s is None:
+            s = int(np.argmax(g.out_degree()))
+        cost, _ = oracle.dijkstra(g, s)
+        for base in (oracle.RULE_THR, oracle.RULE_MIND):
+            checks = []
+
+            def cb(r, thr, mD, D, C, F):
+                finite = cost != INF
+                checks.append(bool(np.all(C[finite] <= cost[finite]) and np.all(cost <= D)))
+
+            a = oracle.round_r(g, s, mode=base)
+            b = oracle.round_r(g, s, mode=base | oracle.ALL_UNFIXED, on_round=cb)
+            assert all(checks)
+            assert np.array_equal(b.dist, cost)
+            assert b.rounds <= a.rounds
