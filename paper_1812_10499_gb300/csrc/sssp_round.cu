@@ -589,7 +589,11 @@ __device__ __forceinline__ void relax_issue(const RoundParams& P,
         pd.inst[i] = oi;
         if (!v.fixed(cur) && cand < v.d()) {
             pd.cand[i] = cand;
-            pd.old[i] = atomicMin(&rec[pd.gy[i]].dp, cand);
+            // The old value is needed only to detect a first discovery (staged D
+            // infinite) or, label-correcting, a change; otherwise the atomic is a
+            // reduction whose result the warp never waits for.
+            if (P.lc || v.d() == kInf64) pd.old[i] = atomicMin(&rec[pd.gy[i]].dp, cand);
+            else atomicMin(&rec[pd.gy[i]].dp, cand);
             if (L::kNarrow) {
                 const InstDesc& d = MULTI ? P.idesc[oi] : P.g;
                 pd.ow[i] = d.outw[e.x];
@@ -604,9 +608,13 @@ __device__ __forceinline__ void relax_issue(const RoundParams& P,
     pd.any = true;
 }
 
-// Consumes a pending batch: successful relaxations fold the target's D and
-// D + outWeight into the minima of the round (Lemmas 7 and 8); a target
-// whose D was infinite is newly discovered and joins the active set.
+// Consumes a pending batch.  Every candidate that was issued folds its
+// distance and distance + outWeight of the target into the minima of the
+// round (Lemmas 7 and 8): the minimum over candidates into an active y is
+// D[y] after the relaxation or more, and D[y] itself is folded (by its own
+// winning candidate, or as a survivor of the previous round), so the minima
+// are exact without knowing which candidate won.  A target whose D was
+// infinite is newly discovered and joins the active set.
 template <bool MULTI, class L>
 __device__ __forceinline__ void relax_consume(const RoundParams& P, u32 cur, Acc& a, WarpQueue& q,
                                               WarpQueue& qf, Pend& pd, u32 lane) {
@@ -615,10 +623,11 @@ __device__ __forceinline__ void relax_consume(const RoundParams& P, u32 cur, Acc
     const u32 nxt = cur ^ 1u;
 #pragma unroll
     for (u32 i = 0; i < kBI; ++i) {
-        const bool ok = pd.cand[i] < pd.old[i];
+        const bool issued = pd.cand[i] != 0;            // candidates are never 0
+        const bool ok = pd.cand[i] < pd.old[i];         // old = 0 unless returned
         const bool fresh = ok && pd.old[i] == kInf64;
         bool hub = false;
-        if (ok) {
+        if (issued) {
             u32 ow = pd.ow[i];
             bool none;
             if (L::kNarrow) {
