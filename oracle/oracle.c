@@ -226,6 +226,26 @@ int orc_floyd_warshall(uint32_t n, const uint64_t* row_ptr, const uint32_t* col,
 
 /* ----------------------------------------------------------------- Round R */
 
+/* Eq. (1)'s minimum for vertex y over its in-edges (x, y) of lb(x) + w,
+ * reading the C of the previous round:
+ *   lb(x) = max(C[x], min(D[x], threshold))          (Lemmas 7 and 8)
+ *   lb(x) = C[x] if x is fixed, else max(C[x], minD)  (minD rule, SP_4 step 4). */
+static uint64_t eq1_min(uint32_t y, const uint64_t* col_ptr, const uint32_t* row,
+                        const uint32_t* w_in, const uint64_t* C, const uint64_t* D,
+                        const int32_t* fr, uint64_t thr, uint64_t minD, int rule_mind) {
+    uint64_t best = ORC_INF;
+    for (uint64_t k = col_ptr[y]; k < col_ptr[y + 1]; ++k) {
+        uint32_t x = row[k];
+        uint64_t lb;
+        if (rule_mind)
+            lb = (fr[x] >= 0) ? C[x] : max_u64(C[x], minD);
+        else
+            lb = max_u64(C[x], min_u64(D[x], thr));
+        best = min_u64(best, sat_add(lb, w_in[k]));
+    }
+    return best;
+}
+
 int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* w,
               uint32_t s, uint32_t mode, int64_t target,
               uint64_t* dist, uint32_t* parent, uint64_t* C_out, int32_t* fixed_round,
@@ -360,15 +380,7 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
                 continue;
             }
             st[ORC_ST_IN_SCANNED] += col_ptr[y + 1] - col_ptr[y];
-            for (uint64_t k = col_ptr[y]; k < col_ptr[y + 1]; ++k) {
-                uint32_t x = row[k];
-                uint64_t lb;
-                if (rule_mind)
-                    lb = (fr[x] >= 0) ? C[x] : max_u64(C[x], minD);
-                else
-                    lb = max_u64(C[x], min_u64(D[x], thr));
-                best = min_u64(best, sat_add(lb, w_in[k]));
-            }
+            best = eq1_min(y, col_ptr, row, w_in, C, D, fr, thr, minD, rule_mind);
             Cn[i] = max_u64(C[y], max_u64(self, best));
         }
         /* Ablation: the same bound for every undiscovered vertex (D = infinity,
@@ -376,17 +388,8 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
         if (all_unfixed) {
             for (uint32_t y = 0; y < n; ++y) {
                 if (fr[y] >= 0 || D[y] != ORC_INF) continue;
-                uint64_t best = ORC_INF;
                 st[ORC_ST_IN_SCANNED] += col_ptr[y + 1] - col_ptr[y];
-                for (uint64_t k = col_ptr[y]; k < col_ptr[y + 1]; ++k) {
-                    uint32_t x = row[k];
-                    uint64_t lb;
-                    if (rule_mind)
-                        lb = (fr[x] >= 0) ? C[x] : max_u64(C[x], minD);
-                    else
-                        lb = max_u64(C[x], min_u64(D[x], thr));
-                    best = min_u64(best, sat_add(lb, w_in[k]));
-                }
+                const uint64_t best = eq1_min(y, col_ptr, row, w_in, C, D, fr, thr, minD, rule_mind);
                 Cu[y] = max_u64(C[y], max_u64(rule_mind ? minD : thr, best));
             }
         }

@@ -33,8 +33,8 @@ MUTANTS = {
         "Cn[i] = max_u64(C[y], max_u64(self, best)); C[y] = Cn[i];"),
     "self clamp ignores D": ("uint64_t self = rule_mind ? minD : min_u64(D[y], thr);",
                              "uint64_t self = rule_mind ? minD : thr;"),
-    "in-edge weight from out-array": ("best = min_u64(best, sat_add(lb, w_in[k]));",
-                                      "best = min_u64(best, sat_add(lb, w[k]));"),
+    "in-edge weight of the wrong edge": ("best = min_u64(best, sat_add(lb, w_in[k]));",
+                                         "best = min_u64(best, sat_add(lb, w_in[col_ptr[y]]));"),
     "outWeight is a max": ("mw = min_u64(mw, w[k]);", "mw = max_u64(mw, w[k]);"),
     "fix on C >= D - 1": ("int fix = (Cn[i] == D[y])", "int fix = (Cn[i] + 1 >= D[y])"),
     "dijkstra relaxes from target": ("uint64_t nd = dist[j] + w[k];",
