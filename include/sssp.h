@@ -335,6 +335,15 @@ uint64_t sssp_num_edges(sssp_handle h);
 int sssp_solve_to(sssp_handle h, uint32_t source, uint32_t target, uint64_t* dist_target,
                   uint32_t* rounds_out);
 
+/* Self-test of the device-side wait limit (failure detection without a
+ * fault): launches the persistent kernel's grid barrier over four CTAs of
+ * which one never arrives; the other three must give up after timeout_ms
+ * (1..10000), flag the timeout and exit, leaving the context usable.  Returns
+ * SSSP_E_DEVICE_TIMEOUT when the limit worked (the expected result),
+ * SSSP_E_INTERNAL if the wait ended otherwise, SSSP_E_CUDA on a CUDA error,
+ * SSSP_E_INVAL for a timeout out of range.  Uses the current device. */
+int sssp_selftest_barrier_timeout(uint32_t timeout_ms);
+
 /* State layout the handle's single-query solves run with:
  * SSSP_LAYOUT_WIDE or SSSP_LAYOUT_COMPACT (0 for a NULL handle). */
 uint32_t sssp_layout(sssp_handle h);

@@ -125,6 +125,7 @@ def load(path: str = LIB_PATH):
         "sssp_num_vertices": (u32, [vp]),
         "sssp_num_edges": (u64, [vp]),
         "sssp_layout": (u32, [vp]),
+        "sssp_selftest_barrier_timeout": (c_int, [u32]),
         "sssp_solve_to": (c_int, [vp, u32, u32, ctypes.POINTER(u64), ctypes.POINTER(u32)]),
     }
     for name, (res, args) in sig.items():
@@ -270,6 +271,12 @@ def sssp_solve_to(h: int, source: int, target: int):
     _check(load().sssp_solve_to(h, source, target, ctypes.byref(d), ctypes.byref(r)),
            "sssp_solve_to")
     return int(d.value), int(r.value)
+
+
+def sssp_selftest_barrier_timeout(timeout_ms: int = 200) -> int:
+    """Status of the device-wait self-test (SSSP_E_DEVICE_TIMEOUT = -6 when the
+    wait limit worked)."""
+    return load().sssp_selftest_barrier_timeout(timeout_ms)
 
 
 def sssp_layout(h: int) -> int:

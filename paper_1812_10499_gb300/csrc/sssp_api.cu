@@ -806,6 +806,34 @@ int sssp_solve_to(sssp_handle h, uint32_t source, uint32_t target, uint64_t* dis
     return SSSP_OK;
 }
 
+int sssp_selftest_barrier_timeout(uint32_t timeout_ms) {
+    if (timeout_ms == 0 || timeout_ms > 10000) return SSSP_E_INVAL;
+    Ctl* ctl = nullptr;
+    CK(cudaMalloc(&ctl, sizeof(Ctl)));
+    int rc = SSSP_OK;
+    cudaError_t e = cudaMemset(ctl, 0, sizeof(Ctl));
+    if (e == cudaSuccess) {
+        RoundParams P{};
+        P.ctl = ctl;
+        P.barrier_ns = (unsigned long long)timeout_ms * 1000000ull;
+        u32 absent = 1;
+        void* args[] = {&P, &absent};
+        // Four co-resident CTAs of one warp; CTA 1 never arrives.
+        e = cudaLaunchCooperativeKernel(barrier_selftest_fn(), dim3(4), dim3(32), args, 0, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    Ctl h{};
+    if (e == cudaSuccess) e = cudaMemcpy(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        rc = SSSP_E_CUDA;
+    } else {
+        rc = (h.error & 4u) ? SSSP_E_DEVICE_TIMEOUT : SSSP_E_INTERNAL;
+    }
+    cudaFree(ctl);
+    return rc;
+}
+
 uint32_t sssp_layout(sssp_handle h) {
     return h ? (h->narrow ? SSSP_LAYOUT_COMPACT : SSSP_LAYOUT_WIDE) : 0u;
 }

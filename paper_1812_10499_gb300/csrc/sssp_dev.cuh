@@ -150,6 +150,8 @@ struct RoundParams {
                                 // the start of the relaxation (written the round before)
     u32* chg;                   // label-correcting: last round in which D changed
     unsigned long long cond;    // cudaGraphConditionalHandle of the device loop, 0 = none
+    unsigned long long barrier_ns;  // wait limit of the persistent kernel's grid barrier
+                                    // (0 = the default, 20 s)
     u64* trace;                 // persistent kernel: globaltimer at launch, then at the end of
                                 // every phase (2 per round); nullable
 };

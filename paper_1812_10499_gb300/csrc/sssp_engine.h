@@ -19,6 +19,7 @@ const void* relax_fn(bool multi, bool narrow);
 const void* cupdate_fn(bool multi, bool narrow);
 const void* solve_fn(bool multi, bool narrow);
 const void* tail_fn(bool multi, bool narrow);
+const void* barrier_selftest_fn();
 u32 tail_cluster_ctas();
 size_t solve_smem_bytes(bool narrow);
 int solve_blocks_per_sm(int threads);

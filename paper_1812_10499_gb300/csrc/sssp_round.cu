@@ -1235,6 +1235,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ bool grid_barrier(const RoundParams& P, bool epilogue, u32 r) {
     __shared__ u32 s_last, s_gen;
     Ctl* ctl = P.ctl;
+    const unsigned long long lim = P.barrier_ns ? P.barrier_ns : kBarrierTimeoutNs;
     __syncthreads();
     if (threadIdx.x == 0) {
         s_gen = ld_volatile(&ctl->bar_gen);
@@ -1255,7 +1256,7 @@ __device__ bool grid_barrier(const RoundParams& P, bool epilogue, u32 r) {
     } else if (threadIdx.x == 0) {
         const unsigned long long t0 = global_ns();
         while (ld_volatile(&ctl->bar_gen) == s_gen) {
-            if (global_ns() - t0 > kBarrierTimeoutNs) {
+            if (global_ns() - t0 > lim) {
                 atomicOr(&ctl->error, 4u);
                 break;
             }
@@ -1265,6 +1266,13 @@ __device__ bool grid_barrier(const RoundParams& P, bool epilogue, u32 r) {
     }
     __syncthreads();
     return (ld_volatile(&ctl->error) & 4u) == 0;
+}
+
+// Self-test of the barrier's wait limit: CTA `absent` never arrives, so the
+// others must give up after P.barrier_ns, set ctl->error bit 4 and return.
+__global__ void k_barrier_selftest(RoundParams P, u32 absent) {
+    if (blockIdx.x == absent) return;
+    grid_barrier(P, false, 0);
 }
 
 // All rounds of the running queries in one launch: relax phase, barrier,
@@ -1440,6 +1448,8 @@ const void* solve_fn(bool multi, bool narrow) {
     if (multi) return narrow ? (const void*)k_solve<true, NarrowL> : (const void*)k_solve<true, WideL>;
     return narrow ? (const void*)k_solve<false, NarrowL> : (const void*)k_solve<false, WideL>;
 }
+const void* barrier_selftest_fn() { return (const void*)k_barrier_selftest; }
+
 const void* tail_fn(bool multi, bool narrow) {
     if (multi) return narrow ? (const void*)k_tail<true, NarrowL> : (const void*)k_tail<true, WideL>;
     return narrow ? (const void*)k_tail<false, NarrowL> : (const void*)k_tail<false, WideL>;

@@ -107,6 +107,11 @@ def test_layout_option_checked_on_the_host(lib):
     assert lib.sssp_layout(None) == 0
 
 
+def test_selftest_argument_checked_on_the_host(lib):
+    assert lib.sssp_selftest_barrier_timeout(0) == -1
+    assert lib.sssp_selftest_barrier_timeout(20000) == -1
+
+
 def test_null_handles(lib):
     assert lib.sssp_solve(None, 0, None, None) == -1
     assert lib.sssp_solve_ex(None, 0, None, None) == -1

@@ -350,6 +350,22 @@ def test_kernel_launch_count(sssp_lib, monkeypatch):
     assert 4 + 3 <= tail["kernel_launches"] <= 4 + 3 * 2
 
 
+def test_device_wait_limit_without_a_fault(sssp_lib):
+    """Failure detection on the GPU without a fault: the persistent kernel's
+    grid barrier is run with one CTA that never arrives; the others give up
+    after the limit, flag it and exit; the host reads SSSP_E_DEVICE_TIMEOUT
+    and the context keeps working."""
+    import time
+    P = sssp_lib
+    t0 = time.perf_counter()
+    rc = P.sssp_selftest_barrier_timeout(200)
+    dt = time.perf_counter() - t0
+    assert rc == -6
+    assert 0.15 < dt < 10.0
+    assert_parity(P, gg.random_graph(4096, 8, 1, 100, 1812_10499), 0,
+                  loop_mode=P.SSSP_LOOP_PERSISTENT)
+
+
 def test_layout_selection(sssp_lib):
     """The automatic layout is compact exactly when n * max weight < 2^31 - 1;
     a graph whose distances need more than 31 bits solves with wide records,
