@@ -284,10 +284,18 @@ def sssp_layout(h: int) -> int:
     return load().sssp_layout(h)
 
 
-def sssp_solve(h: int, source: int):
-    """Returns (dist u64[n], rounds)."""
+def sssp_solve(h: int, source: int, out: np.ndarray | None = None):
+    """Returns (dist u64[n], rounds).  out: a C-contiguous u64[n] array to
+    write the distances into (reused across calls, it saves allocating and
+    first-touching n * 8 bytes of host memory per call)."""
     lib = load()
-    dist = np.empty(lib.sssp_num_vertices(h), dtype=np.uint64)
+    n = lib.sssp_num_vertices(h)
+    if out is None:
+        dist = np.empty(n, dtype=np.uint64)
+    else:
+        if out.dtype != np.uint64 or out.shape != (n,) or not out.flags.c_contiguous:
+            raise SsspError(-1, "sssp_solve: out must be a contiguous u64[n] array")
+        dist = out
     rounds = ctypes.c_uint32(0)
     _check(lib.sssp_solve(h, source, _ptr(dist), ctypes.byref(rounds)), "sssp_solve")
     return dist, int(rounds.value)

@@ -408,6 +408,31 @@ def test_solve_and_solve_device(sssp_lib):
         P.sssp_destroy(h)
 
 
+def test_host_outputs_and_reused_output_array(sssp_lib):
+    """Host outputs of sssp_solve_ex, and sssp_solve writing into a caller's
+    reused array, equal the oracle's on consecutive calls."""
+    P = sssp_lib
+    g = gg.rmat(13, 16, 1, 255, 21)
+    s = int(np.argmax(g.out_degree()))
+    ref = oracle.round_r(g, s)
+    h = P.sssp_create(g.n, g.row_ptr, g.col, g.w)
+    out_arr = np.full(g.n, 7, dtype=np.uint64)
+    try:
+        for _ in range(2):
+            out = P.sssp_solve_ex(h, s, parent=True, fixed_round=True, lower=True)
+            assert np.array_equal(out["dist"], ref.dist)
+            assert np.array_equal(out["parent"], ref.parent)
+            assert np.array_equal(out["fixed_round"], ref.fixed_round)
+            assert np.array_equal(out["lower"], ref.C)
+            d, r = P.sssp_solve(h, s, out=out_arr)
+            assert d is out_arr
+            assert np.array_equal(d, ref.dist) and r == ref.rounds
+        with pytest.raises(P.SsspError):
+            P.sssp_solve(h, s, out=np.zeros(g.n, dtype=np.int32))
+    finally:
+        P.sssp_destroy(h)
+
+
 def test_given_csc_and_torch_allocator(sssp_lib):
     torch = pytest.importorskip("torch")
     P = sssp_lib
