@@ -542,6 +542,7 @@ struct Pend {
     u32 ow[kBI];                    // target outWeight (compact: | in-hub flag in bit 31)
     u32 deg[kBI];                   // target in-degree (wide layout)
     u32 inst[kBI];                  // target's query (multi-query mode)
+    u32 r;                          // the round (label-correcting change marks)
     bool any;                       // a batch is pending (warp-uniform)
 };
 
@@ -656,8 +657,7 @@ __device__ __forceinline__ void relax_consume(const RoundParams& P, u32 cur, Acc
         if (P.lc) {
             // Label-correcting: a target whose D changed is relaxed again in
             // the next round (once, however often it changed in this one).
-            const u32 r = P.ctl->round;
-            const bool chg = ok && atomicExch(&P.chg[pd.gy[i]], r) != r;
+            const bool chg = ok && atomicExch(&P.chg[pd.gy[i]], pd.r) != pd.r;
             u64 odeg = 0;
             if (chg) {
                 const InstDesc& d = MULTI ? P.idesc[pd.inst[i]] : P.g;
@@ -803,6 +803,7 @@ __device__ void relax_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
     WarpQueue qf = {s_q + (kWarps + wib) * kQCap, 0};   // label-correcting next frontier
     Pend pd;
     pd.any = false;
+    pd.r = r;
     // First item per warp is static (no atomic); the rest are pulled.
     const u32 nwarps = gridDim.x * kWarps;
     for (u32 item = blockIdx.x * kWarps + wib; item < total;) {
@@ -1085,15 +1086,6 @@ __device__ void round_epilogue(const RoundParams& P, u32 r) {
         }
     }
     if (running) atomicAdd(&s_running, running);
-    if (P.lc) {
-        // Label-correcting: the next relaxation appends the frontier after
-        // it into slot r & 1 (read for the last time in this round).
-        for (u32 i = threadIdx.x; i < ninst; i += blockDim.x) P.ivar[i].nfix[r & 1u] = 0;
-        if (threadIdx.x == 0) {
-            ctl->nFS[r & 1u] = 0;
-            ctl->FHpk[r & 1u] = 0;
-        }
-    }
     __syncthreads();
     if (threadIdx.x == 0) {
         const u32 total = s_running;
@@ -1145,6 +1137,15 @@ __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r)
     const u32 cur = r & 1u, nxt = cur ^ 1u;
     const u32 lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->work[0] = 0;
+    if (P.lc && blockIdx.x == 0) {
+        // Label-correcting: the next relaxation appends the frontier after it
+        // into slot cur, whose frontier this round's relaxation has consumed.
+        for (u32 i = threadIdx.x; i < ctl->ninst; i += blockDim.x) P.ivar[i].nfix[cur] = 0;
+        if (threadIdx.x == 0) {
+            ctl->nFS[cur] = 0;
+            ctl->FHpk[cur] = 0;
+        }
+    }
 
     const u32 nas = min(ctl->nAS[cur], P.L.capS);
     const u64 ahpk = ctl->AHpk[cur];
@@ -1336,10 +1337,34 @@ __device__ __forceinline__ u32 tail_cup_fits(const RoundParams& P, u32 r) {
     return ai <= P.tail_items ? 1u : 0u;
 }
 
+// Whether a single query goes on to round r + 1 in the tail kernel: the
+// decision of the end-of-round epilogue (a round that fixed or, label-
+// correcting, changed nothing ends the query; so do the target and the round
+// limits) and the frontier's size check.  Every input is final once round r's
+// lower-bound phase has passed a cluster barrier and is written by no step of
+// round r + 1, so CTAs that already started its relaxation (which appends to
+// the active lists: their size is checked after it, tail_cup_fits) cannot
+// change another CTA's decision.
+__device__ __forceinline__ bool tail_next_single(const RoundParams& P, u32 r) {
+    const InstVar* v = P.ivar;
+    const Ctl* ctl = P.ctl;
+    const u32 nxt = (r & 1u) ^ 1u;
+    if (ld_volatile(&v->nfix[nxt]) == 0) return false;
+    const u32 tgt = v->target;
+    if (tgt != kNoTarget && *(volatile const int*)&P.fround[P.g.base + tgt] >= 0) return false;
+    if (v->max_rounds != 0 && r - v->start_round + 1 >= v->max_rounds) return false;
+    if (r + 1 > ctl->round_limit || r + 1 > ld_volatile(&ctl->stop_round)) return false;
+    const u32 fi = ((ld_volatile(&ctl->nFS[nxt]) + 31) >> 5) + (u32)ld_volatile(&ctl->FHpk[nxt]);
+    return fi <= P.tail_items;
+}
+
 // Launched as one cluster of kTailCTAs CTAs.  Every CTA takes the same
-// number of cluster barriers: the loop decision is written by CTA 0 before
-// a barrier and read by all after it, and nothing writes it again before
-// every CTA has passed the next barrier.
+// number of cluster barriers: each loop decision is either computed by every
+// CTA from the same values, final at the barrier before it, or (several
+// queries) written by CTA 0 before a barrier and read by all after it.  CTA 0
+// alone writes the end-of-round state; with a single query the other CTAs
+// start the next relaxation meanwhile, which reads none of that state (the
+// round number is passed along, not read back).
 template <bool MULTI, class L>
 __global__ void __launch_bounds__(256, 1) k_tail(RoundParams P) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
@@ -1347,14 +1372,12 @@ __global__ void __launch_bounds__(256, 1) k_tail(RoundParams P) {
     const bool lead = blockIdx.x == 0;
     if (lead && threadIdx.x == 0) ctl->tail_go = tail_decide(P);
     cluster_sync_all();
-    for (;;) {
-        if (ld_volatile(&ctl->tail_go) == 0) break;
-        const u32 r = ld_volatile(&ctl->round);
+    bool go = ld_volatile(&ctl->tail_go) != 0;
+    u32 r = ld_volatile(&ctl->round);
+    while (go) {
         relax_phase<MULTI, L>(P, s_dyn, r);
         cluster_sync_all();
-        if (lead && threadIdx.x == 0) ctl->tail_go = tail_cup_fits(P, r);
-        cluster_sync_all();
-        if (ld_volatile(&ctl->tail_go) == 0) {
+        if (!tail_cup_fits(P, r)) {
             // The relaxation grew the active set: the full grid finishes
             // the round (its relax launch is skipped).
             if (lead && threadIdx.x == 0) ctl->cup_only = 1;
@@ -1362,19 +1385,27 @@ __global__ void __launch_bounds__(256, 1) k_tail(RoundParams P) {
         }
         cupdate_phase<MULTI, L>(P, s_dyn, r);
         cluster_sync_all();
-        if (lead) {
-            round_epilogue(P, r);
-            if (threadIdx.x == 0) ctl->tail_go = tail_decide(P);
+        if (!MULTI) {
+            go = tail_next_single(P, r);
+            if (lead) round_epilogue(P, r);
+            ++r;
+        } else {
+            if (lead) {
+                round_epilogue(P, r);
+                if (threadIdx.x == 0) ctl->tail_go = tail_decide(P);
+            }
+            cluster_sync_all();
+            go = ld_volatile(&ctl->tail_go) != 0;
+            r = ld_volatile(&ctl->round);
         }
-        cluster_sync_all();
     }
     // The device loop goes on while rounds remain (the epilogue's setting
     // is overridden here because the tail kernel ends the loop body).
     if (lead && threadIdx.x == 0 && P.cond) {
         const u32 st = ld_volatile(&ctl->status);
-        const u32 r = ld_volatile(&ctl->round);
+        const u32 rr = ld_volatile(&ctl->round);
         cudaGraphSetConditional(P.cond,
-                                (st == kRunning && r <= ld_volatile(&ctl->stop_round)) ? 1u : 0u);
+                                (st == kRunning && rr <= ld_volatile(&ctl->stop_round)) ? 1u : 0u);
     }
 }
 
