@@ -1,0 +1,54 @@
+"""The benchmark's contract on the host: the reference arm (the oracle, no
+GPU) prints one JSON line with the keys the driver reads, and the traffic
+figure of a committed ncu summary is withheld once the kernels' sources no
+longer match the ones it was captured from."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--config", "random4096", "--steps", "3", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e", "impl"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["unit"] == "GTEPS" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["vs_baseline"] is None
+
+
+def test_traffic_withheld_when_the_kernels_changed(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    sha = bench.kernel_source_sha256()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "k_cupdate_x.md").write_text(
+        f"kernel_source_sha256: {sha}\ntraffic_bytes_per_launch: 123\n")
+    (prof / "k_relax_x.md").write_text(
+        "kernel_source_sha256: 00\ntraffic_bytes_per_launch: 456\n")
+    (tmp_path / "paper_1812_10499_gb300").symlink_to(os.path.join(ROOT, "paper_1812_10499_gb300"))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_traffic("k_cupdate", "x")[0] == 123.0
+    t, why = bench.measured_traffic("k_relax", "x")
+    assert t is None and "stale" in why
+    assert bench.measured_traffic("k_cupdate", "missing") == (None, None)
+
+
+def test_algorithmic_bytes_per_unit():
+    sys.path.insert(0, ROOT)
+    import bench
+    info = {"out_scanned": 10, "front_visits": 2, "in_scanned": 100, "active_visits": 3}
+    assert bench.alg_bytes(info) == (16 * 10 + 36 * 2, 24 * 100 + 48 * 3)
