@@ -29,6 +29,7 @@ RULE_MIND = 1
 LABEL_CORRECT = 2
 CHEAP_FIRST = 4
 ALL_UNFIXED = 8
+DELTA = 16
 
 _STATS = ("out_scanned", "in_scanned", "active_visits", "front_visits", "reached", "max_active")
 
@@ -63,6 +64,9 @@ def _bind(lib):
     lib.orc_round.restype = c_int
     lib.orc_round.argtypes = [u32, vp, vp, vp, u32, u32, ctypes.c_int64, vp, vp, vp, vp, vp, vp,
                               ROUND_CB, vp]
+    lib.orc_round_delta.restype = c_int
+    lib.orc_round_delta.argtypes = [u32, vp, vp, vp, u32, u32, ctypes.c_int64, u64, vp, vp, vp,
+                                    vp, vp, vp, ROUND_CB, vp]
     lib.orc_prune.restype = c_int
     lib.orc_prune.argtypes = [u32, vp, vp, u32, vp]
     for f in (lib.orc_sp1, lib.orc_sp2):
@@ -151,12 +155,13 @@ class RoundResult:
 
 
 def round_r(g, s: int, mode: int = RULE_THR, on_round=None, lib=None,
-            target: int | None = None) -> RoundResult:
+            target: int | None = None, delta: int | None = None) -> RoundResult:
     """Sequential Round R (the SP_3/SP_4 round; see oracle.c).
 
     on_round(round, thr, minD, D, C, fixed_round) is called after every round
     with numpy views of the state (valid only during the call).  target: stop
-    after the round that fixes this vertex (single-target query)."""
+    after the round that fixes this vertex (single-target query).  delta:
+    windowed relaxation (ORC_DELTA) with this window width; None = off."""
     lib = lib or load()
     rp, col, w = _csr(g)
     n = g.n
@@ -175,10 +180,18 @@ def round_r(g, s: int, mode: int = RULE_THR, on_round=None, lib=None,
         cb = ROUND_CB(_cb)
     else:
         cb = ROUND_CB()
-    _check(lib.orc_round(n, rp.ctypes.data, col.ctypes.data, w.ctypes.data, s, mode,
-                         -1 if target is None else int(target), dist.ctypes.data,
-                         parent.ctypes.data, C.ctypes.data, fr.ctypes.data,
-                         ctypes.byref(rounds), stats.ctypes.data, cb, None), "round")
+    if delta is None:
+        rc = lib.orc_round(n, rp.ctypes.data, col.ctypes.data, w.ctypes.data, s, mode,
+                           -1 if target is None else int(target), dist.ctypes.data,
+                           parent.ctypes.data, C.ctypes.data, fr.ctypes.data,
+                           ctypes.byref(rounds), stats.ctypes.data, cb, None)
+    else:
+        rc = lib.orc_round_delta(n, rp.ctypes.data, col.ctypes.data, w.ctypes.data, s,
+                                 mode | DELTA, -1 if target is None else int(target), int(delta),
+                                 dist.ctypes.data, parent.ctypes.data, C.ctypes.data,
+                                 fr.ctypes.data, ctypes.byref(rounds), stats.ctypes.data, cb,
+                                 None)
+    _check(rc, "round")
     return RoundResult(dist, parent, C, fr, int(rounds.value),
                        {k: int(v) for k, v in zip(_STATS, stats)})
 

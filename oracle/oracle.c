@@ -250,6 +250,15 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
               uint32_t s, uint32_t mode, int64_t target,
               uint64_t* dist, uint32_t* parent, uint64_t* C_out, int32_t* fixed_round,
               uint32_t* rounds_out, uint64_t* stats, orc_round_cb cb, void* ctx) {
+    if (mode & ORC_DELTA) return ORC_EINVAL;   /* needs a window: orc_round_delta */
+    return orc_round_delta(n, row_ptr, col, w, s, mode, target, 0, dist, parent, C_out,
+                           fixed_round, rounds_out, stats, cb, ctx);
+}
+
+int orc_round_delta(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* w,
+                    uint32_t s, uint32_t mode, int64_t target, uint64_t delta,
+                    uint64_t* dist, uint32_t* parent, uint64_t* C_out, int32_t* fixed_round,
+                    uint32_t* rounds_out, uint64_t* stats, orc_round_cb cb, void* ctx) {
     /*
      * One round of the parallel SP_3/SP_4 scheme, done one vertex at a time
      * on a snapshot (Sec. VI, SP_4 steps 1-5, label-setting as in SP_3):
@@ -275,12 +284,24 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
      * changed in the previous round's step 1 (SP_4 step 3 relaxes all
      * discovered vertices; a vertex whose D is unchanged has nothing new to
      * relax), each with the D it had at the start of the step.
+     *
+     * ORC_DELTA (a reading of Sec. I's remark that Delta-stepping can be
+     * combined with the lower bounds): a vertex is "pending" while its D has
+     * changed since it last relaxed.  After step 4 the next frontier is every
+     * pending vertex that is fixed, plus every pending active vertex with
+     * D < minD + delta (minD of this round, saturating): the window plays the
+     * part of Delta-stepping's current bucket.  Vertices outside the window
+     * wait, so the loop runs while the frontier or the active set is
+     * non-empty.  delta = 0 is the label-setting round exactly; a large
+     * delta relaxes every changed vertex as ORC_LABEL_CORRECT does.
      */
     if (s >= n || target >= (int64_t)n) return ORC_EINVAL;
     const int rule_mind = (mode & ORC_RULE_MIND) != 0;
     const int label_correct = (mode & ORC_LABEL_CORRECT) != 0;
     const int cheap_first = (mode & ORC_CHEAP_FIRST) != 0;
     const int all_unfixed = (mode & ORC_ALL_UNFIXED) != 0;
+    const int windowed = (mode & ORC_DELTA) != 0;
+    if (windowed && label_correct) return ORC_EINVAL;
     uint64_t m = row_ptr[n];
 
     uint64_t* col_ptr = (uint64_t*)malloc(sizeof(uint64_t) * ((size_t)n + 1));
@@ -335,7 +356,7 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
     uint32_t r = 0;
     if (target == (int64_t)s) nf = 0;   /* the source is fixed before round 1 */
 
-    while (nf > 0) {
+    while (nf > 0 || (windowed && na > 0)) {
         r++;
         st[ORC_ST_FRONT_VISITS] += nf;
 
@@ -356,6 +377,7 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
                     D[y] = nd;
                     par[y] = x;
                     if (label_correct && !changed[y]) { changed[y] = 1; front2[nchg++] = y; }
+                    if (windowed) changed[y] = 1;          /* pending */
                 }
             }
         }
@@ -396,6 +418,7 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
 
         /* Step 4: apply C, fix C = D, split into next frontier / active. */
         uint64_t nf2 = 0, na2 = 0;
+        const uint64_t window = sat_add(minD, delta);
         for (uint64_t i = 0; i < na; ++i) {
             uint32_t y = act[i];
             C[y] = Cn[i];
@@ -403,9 +426,10 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
             if (fix) {
                 C[y] = D[y];
                 fr[y] = (int32_t)r;
-                if (!label_correct) front2[nf2++] = y;
+                if (windowed ? changed[y] : !label_correct) front2[nf2++] = y;
             } else {
                 act2[na2++] = y;
+                if (windowed && changed[y] && D[y] < window) front2[nf2++] = y;
             }
         }
         if (all_unfixed)

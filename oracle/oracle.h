@@ -45,6 +45,8 @@
                                  Sec. IV) or D[y] <= threshold (Lemma 8); both imply
                                  Cn[y] = D[y], so only in_scanned changes */
 
+#define ORC_DELTA        16u  /* windowed relaxation (orc_round_delta only): see oracle.c */
+
 /* Per-round statistics written by orc_round (array of ORC_NSTATS u64). */
 #define ORC_ST_OUT_SCANNED   0  /* out-edges scanned in relax steps          */
 #define ORC_ST_IN_SCANNED    1  /* in-edges scanned in C-update steps        */
@@ -93,6 +95,14 @@ int orc_round(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const ui
               uint32_t s, uint32_t mode, int64_t target,
               uint64_t* dist, uint32_t* parent, uint64_t* C_out, int32_t* fixed_round,
               uint32_t* rounds_out, uint64_t* stats, orc_round_cb cb, void* ctx);
+
+/* orc_round with ORC_DELTA allowed in mode: delta is the width of the window
+ * of distances above minD whose changed vertices relax before they are fixed
+ * (ignored without ORC_DELTA; ORC_DELTA with ORC_LABEL_CORRECT is invalid). */
+int orc_round_delta(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* w,
+                    uint32_t s, uint32_t mode, int64_t target, uint64_t delta,
+                    uint64_t* dist, uint32_t* parent, uint64_t* C_out, int32_t* fixed_round,
+                    uint32_t* rounds_out, uint64_t* stats, orc_round_cb cb, void* ctx);
 
 /* Sec. III pre-processing: iteratively delete non-source vertices with no
  * in-edges.  removed[v] = 1 for deleted vertices. */

@@ -48,6 +48,12 @@ MUTANTS = {
         "            for (uint32_t k = 0; k < n; ++k) {"),
     "sp1 forgets pred decrement": ("pred[y]--;", ""),
     "transpose stores target as source": ("row[at] = u;", "row[at] = col[k];"),
+    "window bound not strict": ("if (windowed && changed[y] && D[y] < window)",
+                                "if (windowed && changed[y] && D[y] <= window)"),
+    "window above the threshold": ("const uint64_t window = sat_add(minD, delta);",
+                                   "const uint64_t window = sat_add(thr, delta);"),
+    "windowed frontier drops fixed vertices": ("if (windowed ? changed[y] : !label_correct)",
+                                               "if (windowed ? 0 : !label_correct)"),
     "heap compares wrong way": ("if (h->key[a] != h->key[b]) return h->key[a] < h->key[b];",
                                 "if (h->key[a] != h->key[b]) return h->key[a] > h->key[b];"),
 }
@@ -69,6 +75,13 @@ def battery(lib):
             d1, o1 = oracle.sp1(g, e["source"], lib=lib)
             assert d1.tolist() == e["dist"] and o1["outer"] == e["sp1_outer"]
             assert o1["inserts"] == e["sp1_inserts"]
+    for name in ("window9", "window10"):
+        e = ex[name]
+        g = gg.from_edges(e["n"], e["edges"])
+        r = oracle.round_r(g, e["source"], lib=lib, delta=e["delta"])
+        assert r.dist.tolist() == e["dist"]
+        assert r.fixed_round.tolist() == e["fixed_round"]
+        assert r.rounds == e["rounds"]
     for n, d, wmax, seed in pins.SMALL_CASES[::2]:
         g = pins.random_small(n, d, wmax, seed)
         ref = pins.brute_force_dist(g, 0) if n <= 8 else oracle.bellman_ford(g, 0)

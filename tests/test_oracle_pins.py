@@ -167,7 +167,7 @@ def test_transpose_is_the_same_edge_multiset():
 
 # ---------------------------------------------------- Round R invariants
 
-def check_round_invariants(g, s, mode=oracle.RULE_THR, lib=None):
+def check_round_invariants(g, s, mode=oracle.RULE_THR, lib=None, delta=None):
     cost, _ = oracle.dijkstra(g, s, lib=lib)
     seen = []
 
@@ -183,12 +183,13 @@ def check_round_invariants(g, s, mode=oracle.RULE_THR, lib=None):
         assert np.all(C[unf] < D[unf])
         seen.append(int(np.count_nonzero(F == r)))
 
-    r = oracle.round_r(g, s, mode=mode, on_round=on_round, lib=lib)
+    r = oracle.round_r(g, s, mode=mode, on_round=on_round, lib=lib, delta=delta)
     reach = cost != INF
     assert np.array_equal(r.dist, cost)
     assert np.array_equal(r.fixed_round >= 0, reach)
-    # every round but the last fixes at least one vertex
-    assert all(c >= 1 for c in seen[:-1]) and seen[-1] == 0
+    # every round but the last fixes at least one vertex (windowed: the last
+    # round may fix vertices that have nothing left to relax)
+    assert all(c >= 1 for c in seen[:-1]) and (delta is not None or seen[-1] == 0)
     assert r.rounds == len(seen) <= max(1, int(reach.sum()))
     assert r.stats["reached"] == int(reach.sum())
     # parent edges are tight and come from vertices fixed earlier
@@ -200,7 +201,12 @@ def check_round_invariants(g, s, mode=oracle.RULE_THR, lib=None):
         ws = [int(g.w[k]) for k in range(int(g.row_ptr[p]), int(g.row_ptr[p + 1]))
               if int(g.col[k]) == v]
         assert ws and int(cost[p]) + min(ws) == int(cost[v])
-        assert r.fixed_round[p] < r.fixed_round[v]
+        # (windowed: p may relax before it is fixed, and it is then fixed in
+        # v's round at the latest -- v's bound needs lb(p) = D[p])
+        if delta is None:
+            assert r.fixed_round[p] < r.fixed_round[v]
+        else:
+            assert r.fixed_round[p] <= r.fixed_round[v]
     return r
 
 
@@ -420,3 +426,88 @@ def test_all_unfixed_ablation_is_sound_and_never_slower_in_rounds():
             assert all(checks)
             assert np.array_equal(b.dist, cost)
             assert b.rounds <= a.rounds
+
+
+# ------------------------------------------- windowed relaxation (Delta-stepping)
+
+def window_graphs():
+    """Graphs of every shape the windowed mode meets: random, skewed (hubs),
+    grids, layered DAGs, some unreachable vertices, multi-edges."""
+    out = [(gg.random_graph(600, 6, 1, 50, 21), 0), (gg.grid(24, 18, 1, 1000, 22), 0),
+           (gg.dag(12, 40, 5, 3, 1, 300, 23), 0), (gg.random_var_graph(500, 0, 7, 1, 90, 24), 3),
+           (gg.from_edges(4, [(0, 1, 2), (0, 1, 1), (1, 2, 5), (0, 2, 9), (2, 3, 1)]), 0)]
+    g = gg.rmat(11, 12, 1, 255, 25)
+    out.append((g, int(np.argmax(g.out_degree()))))
+    return out
+
+
+@pytest.mark.parametrize("variant", ["window9", "window10"])
+def test_windowed_hand_derived_trace(variant):
+    """The window bound is minD + delta, strict: on the hand-derived example
+    delta = 9 keeps v3 waiting (the label-setting run, 4 rounds) and delta =
+    10 lets it relax one round before it is fixed (3 rounds)."""
+    ex = worked_example()[variant]
+    g = gg.from_edges(ex["n"], ex["edges"])
+    r = oracle.round_r(g, ex["source"], delta=ex["delta"])
+    assert r.dist.tolist() == ex["dist"]
+    assert r.fixed_round.tolist() == ex["fixed_round"]
+    assert r.parent.tolist() == ex["parent"]
+    assert r.rounds == ex["rounds"]
+    for k in ("out_scanned", "front_visits", "active_visits"):
+        assert r.stats[k] == ex[k]
+
+
+@pytest.mark.parametrize("base", [oracle.RULE_THR, oracle.RULE_MIND, oracle.CHEAP_FIRST,
+                                  oracle.RULE_MIND | oracle.CHEAP_FIRST],
+                         ids=["thr", "mind", "cheap", "mind-cheap"])
+def test_windowed_zero_is_the_label_setting_round(base):
+    """delta = 0: no active vertex is below minD, so only fixed vertices
+    relax, each once -- the label-setting round, state and counters alike."""
+    for g, s in window_graphs():
+        a = oracle.round_r(g, s, mode=base)
+        b = oracle.round_r(g, s, mode=base, delta=0)
+        for f in ("dist", "parent", "C", "fixed_round"):
+            assert np.array_equal(getattr(a, f), getattr(b, f)), f
+        assert a.rounds == b.rounds and a.stats == b.stats
+
+
+@pytest.mark.parametrize("base", [oracle.RULE_THR, oracle.RULE_MIND], ids=["thr", "mind"])
+def test_windowed_unbounded_is_label_correcting_round_by_round(base):
+    """delta above every distance: every changed vertex relaxes the next
+    round, as SP_4 step 3 prints it.  The state after each round equals the
+    label-correcting run's for as long as that runs; the windowed run then
+    goes on until the active set is empty, so every reachable vertex ends
+    fixed."""
+    for g, s in window_graphs():
+        lc, win = [], []
+        a = oracle.round_r(g, s, mode=base | oracle.LABEL_CORRECT,
+                           on_round=lambda r, t, m, D, C, F: lc.append((D.copy(), C.copy(),
+                                                                        F.copy())))
+        b = oracle.round_r(g, s, mode=base, delta=2**64 - 1,
+                           on_round=lambda r, t, m, D, C, F: win.append((D.copy(), C.copy(),
+                                                                         F.copy())))
+        assert b.rounds >= a.rounds
+        for r, (x, y) in enumerate(zip(lc, win), start=1):
+            for u, v in zip(x, y):
+                assert np.array_equal(u, v), f"round {r}"
+        cost = oracle.dijkstra(g, s)[0]
+        assert np.array_equal(b.dist, cost)
+        assert np.array_equal(b.fixed_round >= 0, cost != INF)
+
+
+@pytest.mark.parametrize("delta", [1, 6, 40, 300, 5000])
+@pytest.mark.parametrize("mode", [oracle.RULE_THR, oracle.RULE_MIND], ids=["thr", "mind"])
+def test_windowed_round_invariants(delta, mode):
+    """Any window: C <= cost <= D after every round, fixed vertices at their
+    cost, textbook distances, tight parent edges, every reachable vertex
+    fixed, every round but the last fixes something."""
+    for n, d, wmax, seed in SMALL_CASES[::3]:
+        check_round_invariants(random_small(n, d, wmax, seed), 0, mode, delta=delta)
+    for g, s in window_graphs():
+        check_round_invariants(g, s, mode, delta=delta)
+
+
+def test_windowed_and_label_correcting_do_not_combine():
+    g = gg.random_graph(50, 3, 1, 9, 1)
+    with pytest.raises(RuntimeError):
+        oracle.round_r(g, 0, mode=oracle.LABEL_CORRECT, delta=5)
