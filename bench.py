@@ -38,9 +38,21 @@ SEED = 1812_10499
 METRIC = "SSSP GTEPS and % HBM roofline at 1 GB300; batched queries/s and p99 vs plain loop"
 # Per-vertex state layout of the round kernels (SSSP_LAYOUT_*).
 LAYOUTS = {"auto": 0, "wide": 1, "compact": 2}
-# Round rule (SSSP_RULE_* bits): threshold clamp, minD clamp, label-correcting.
+# Round rule (SSSP_RULE_* bits): threshold clamp, minD clamp, label-correcting,
+# cheaper rules first, windowed relaxation (window width --delta).
 RULES = {"thr": 0, "mind": 1, "lc": 2, "lc-mind": 3, "thr-cheap": 4, "mind-cheap": 5,
-         "lc-cheap": 6}
+         "lc-cheap": 6, "thr-win": 16, "mind-win": 17, "thr-cheap-win": 20}
+
+
+def window_delta(g, delta):
+    """Window width of the windowed rules: the given one, else the choice for
+    uniformly random weights that Sec. I quotes for Delta-stepping (Delta of
+    the order of 1 / maximum degree for weights in [0, 1]), scaled to the
+    weight range: max weight / maximum out-degree, at least 1."""
+    if delta is not None:
+        return int(delta)
+    dmax = max(1, int(np.max(g.out_degree())))
+    return max(1, int(round(int(np.max(g.w)) / dmax)))
 
 # Algorithmic bytes (what the round must move, at element size):
 #   per out-edge scanned by k_relax: 8 B {target, w} + 8 B target D word;
@@ -247,6 +259,10 @@ def run_ours(args):
                      "host": P.SSSP_LOOP_HOST}[args.loop]
     opt.layout = LAYOUTS[args.layout]
     opt.rule = RULES[args.rule]
+    delta = None
+    if opt.rule & P.SSSP_RULE_WINDOWED:
+        delta = window_delta(g, args.delta)
+        opt.delta = delta
     h = P.sssp_create(g.n, g.row_ptr, g.col, g.w, options=opt)
     layout = {P.SSSP_LAYOUT_WIDE: "wide 32 B records",
               P.SSSP_LAYOUT_COMPACT: "compact 16 B records"}[P.sssp_layout(h)]
@@ -366,7 +382,7 @@ def run_ours(args):
         "data": "synthetic (seeded generator)",
         "config": {"workload": desc, "n": g.n, "m": g.m, "sources": sources,
                    "rounds": rounds, "m_reach_per_step": m_reach, "state_layout": layout,
-                   "rule": args.rule,
+                   "rule": args.rule, **({"delta": delta} if delta is not None else {}),
                    "l2": "inputs larger than L2 (CSR+CSC+state > 1 GB)",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "kernel": kernel, "achieved": dom_gbs, "peak": peak,
@@ -695,6 +711,8 @@ def main():
     ap.add_argument("--loop", default="graph", choices=["persistent", "graph", "host"])
     ap.add_argument("--layout", default="auto", choices=list(LAYOUTS))
     ap.add_argument("--rule", default="thr-cheap", choices=list(RULES))
+    ap.add_argument("--delta", type=int, default=None,
+                    help="window width of the windowed rules (default: max weight / mean degree)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=150.0)

@@ -79,6 +79,19 @@ extern "C" {
  * Both imply that Eq. (1) gives C[y] = D[y], so every output is unchanged;
  * only in_scanned (the in-edges actually read) drops. */
 #define SSSP_RULE_CHEAP_FIRST 4u
+/* Flag OR-ed into the rule: windowed relaxation, a combination of the lower
+ * bounds with Delta-stepping (Sec. I notes that the two can be combined).
+ * Delta-stepping's current bucket becomes a window of width
+ * sssp_options.delta above minD: after step (c) the next frontier is every
+ * vertex whose D changed since it last relaxed and that is either fixed now
+ * or still active with D < minD + delta.  The loop runs while a frontier or
+ * an active vertex is left.  delta = 0 gives exactly the default
+ * label-setting round; a delta above every distance relaxes every changed
+ * vertex as SSSP_RULE_LABEL_CORRECTING does (but every reachable vertex is
+ * fixed in the end).  Distances are the same; rounds, work and fixing
+ * rounds depend on delta.  Not combinable with SSSP_RULE_LABEL_CORRECTING;
+ * not available for the server. */
+#define SSSP_RULE_WINDOWED 16u
 
 /* How the rounds are sequenced.  All modes give identical results. */
 #define SSSP_LOOP_GRAPH      0u  /* two kernels per round in a CUDA graph with a device-side
@@ -126,6 +139,8 @@ typedef struct sssp_options {
     sssp_alloc_fn alloc;     /* NULL = cudaMalloc                                          */
     sssp_free_fn free;       /* NULL = cudaFree                                            */
     void* alloc_ctx;
+    uint64_t delta;          /* window width of SSSP_RULE_WINDOWED, in weight units
+                                (0 = the label-setting round)                              */
 } sssp_options;
 
 /* Fills *opt with the defaults described above. */

@@ -26,6 +26,7 @@ SSSP_RULE_THRESHOLD = 0
 SSSP_RULE_MIND = 1
 SSSP_RULE_LABEL_CORRECTING = 2
 SSSP_RULE_CHEAP_FIRST = 4
+SSSP_RULE_WINDOWED = 16
 SSSP_LOOP_GRAPH = 0
 SSSP_LOOP_HOST = 1
 SSSP_LOOP_PERSISTENT = 2
@@ -43,7 +44,8 @@ class sssp_options(ctypes.Structure):
                 ("hub_degree", ctypes.c_uint32), ("chunk_edges", ctypes.c_uint32),
                 ("block_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
                 ("device", ctypes.c_int32), ("layout", ctypes.c_uint32),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+                ("delta", ctypes.c_uint64)]
 
 
 class sssp_solve_args(ctypes.Structure):

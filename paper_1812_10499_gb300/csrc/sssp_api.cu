@@ -279,7 +279,9 @@ int init_single_context(sssp_graph* h) {
     P.rule = h->opt.rule & SSSP_RULE_MIND;
     P.lc = (h->opt.rule & SSSP_RULE_LABEL_CORRECTING) ? 1u : 0u;
     P.cheap = (h->opt.rule & SSSP_RULE_CHEAP_FIRST) ? 1u : 0u;
-    if (P.lc) {
+    P.win = (h->opt.rule & SSSP_RULE_WINDOWED) ? 1u : 0u;
+    P.delta = h->opt.delta;
+    if (P.lc || P.win) {
         RC(c.pool.get(&P.snap, h->n));
         RC(c.pool.get(&P.chg, h->n));
         RC(c.pool.get(&P.L.FX[0], h->n));
@@ -591,7 +593,9 @@ int ensure_batch(sssp_graph* h0, u64 nrec, u32 nslots, u32 npages, u64 capH, u64
     P.rule = h0->opt.rule & SSSP_RULE_MIND;
     P.lc = (h0->opt.rule & SSSP_RULE_LABEL_CORRECTING) ? 1u : 0u;
     P.cheap = (h0->opt.rule & SSSP_RULE_CHEAP_FIRST) ? 1u : 0u;
-    if (P.lc) {
+    P.win = (h0->opt.rule & SSSP_RULE_WINDOWED) ? 1u : 0u;
+    P.delta = h0->opt.delta;
+    if (P.lc || P.win) {
         RC(c->pool.get(&P.snap, nrec));
         RC(c->pool.get(&P.chg, nrec));
         RC(c->pool.get(&P.L.FX[0], nrec));
@@ -617,7 +621,8 @@ int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist
     for (u32 i = 0; i < k; ++i) {
         if (!g[i] || !dist[i]) return SSSP_E_INVAL;
         if (g[i]->device != h0->device || g[i]->opt.hub_degree != h0->opt.hub_degree ||
-            g[i]->opt.chunk_edges != h0->opt.chunk_edges || g[i]->opt.rule != h0->opt.rule)
+            g[i]->opt.chunk_edges != h0->opt.chunk_edges || g[i]->opt.rule != h0->opt.rule ||
+            g[i]->opt.delta != h0->opt.delta)
             return SSSP_E_INVAL;
         if (sources[i] >= g[i]->n) return SSSP_E_SOURCE_RANGE;
         vbits = std::max(vbits, std::max<u32>(1, bits_for((u64)g[i]->n - 1)));
@@ -729,7 +734,9 @@ int sssp_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t*
     if (o.hub_degree == 0) o.hub_degree = kDefaultHub;
     if (o.chunk_edges == 0) o.chunk_edges = kDefaultChunk;
     if (o.block_threads == 0) o.block_threads = kThreads;
-    if ((o.rule & ~(SSSP_RULE_MIND | SSSP_RULE_LABEL_CORRECTING | SSSP_RULE_CHEAP_FIRST)) != 0 ||
+    if ((o.rule & ~(SSSP_RULE_MIND | SSSP_RULE_LABEL_CORRECTING | SSSP_RULE_CHEAP_FIRST |
+                    SSSP_RULE_WINDOWED)) != 0 ||
+        ((o.rule & SSSP_RULE_LABEL_CORRECTING) && (o.rule & SSSP_RULE_WINDOWED)) ||
         o.loop_mode > SSSP_LOOP_PERSISTENT || o.chunk_edges % 32 != 0 ||
         o.layout > SSSP_LAYOUT_COMPACT ||
         o.hub_degree > (1u << 20) || o.chunk_edges > (1u << 20) ||

@@ -146,9 +146,15 @@ struct RoundParams {
                                 // previous round's relaxation
     u32 cheap;                  // 1: fix y without scanning its in-edges when
                                 // D[y] <= minD + inWeight[y] or D[y] <= threshold
-    unsigned long long* snap;   // label-correcting: distance of each frontier vertex at
-                                // the start of the relaxation (written the round before)
-    u32* chg;                   // label-correcting: last round in which D changed
+    u32 win;                    // 1: windowed relaxation (Delta-stepping's bucket as a
+                                // window over D): an active vertex whose D changed since
+                                // it last relaxed relaxes while D < minD + delta
+    u64 delta;                  // the window's width (windowed relaxation)
+    unsigned long long* snap;   // label-correcting / windowed: distance of each frontier
+                                // vertex at the start of the relaxation (written the round
+                                // before)
+    u32* chg;                   // label-correcting: last round in which D changed;
+                                // windowed: nonzero while D changed since the last relaxation
     unsigned long long cond;    // cudaGraphConditionalHandle of the device loop, 0 = none
     unsigned long long barrier_ns;  // wait limit of the persistent kernel's grid barrier
                                     // (0 = the default, 20 s)

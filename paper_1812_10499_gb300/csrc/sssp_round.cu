@@ -332,6 +332,17 @@ __device__ __forceinline__ void wq_flush2(const RoundParams& P, WarpQueue& q1, u
     q2.cnt = 0;
 }
 
+// Appends g (where pred holds) to a small list with one atomic per warp.
+__device__ __forceinline__ void warp_append(const RoundParams& P, u32* counter, u32* list,
+                                            bool pred, u32 g, u32 lane) {
+    const u32 mask = __ballot_sync(kFull, pred);
+    if (mask == 0) return;
+    u32 base = 0;
+    if (lane == 0) base = atomicAdd(counter, __popc(mask));
+    base = __shfl_sync(kFull, base, 0);
+    if (pred) put_small(P, list, base + __popc(mask & ((1u << lane) - 1u)), g);
+}
+
 // Accumulators a thread carries through one phase.
 struct Acc {
     u64 fmin_d, fmin_t;     // folds of minD / threshold (single-query mode)
@@ -590,6 +601,9 @@ __device__ __forceinline__ void relax_issue(const RoundParams& P,
         pd.inst[i] = oi;
         if (!v.fixed(cur) && cand < v.d()) {
             pd.cand[i] = cand;
+            // Windowed: D[y] changes this round (it ends at most cand, below the
+            // D staged during this phase), so y must relax again.
+            if (P.win) P.chg[pd.gy[i]] = 1u;
             // The old value is needed only to detect a first discovery (staged D
             // infinite) or, label-correcting, a change; otherwise the atomic is a
             // reduction whose result the warp never waits for.
@@ -691,9 +705,9 @@ __device__ void relax_small(const RoundParams& P, WarpStage<typename L::RSlot>& 
         deg = (u32)(d.out_off[xloc + 1] - b);
         typename L::Rec* rx = L::rec(P) + g;
         rx->cf[cur ^ 1] = rx->cf[cur];              // keep both copies "fixed"
-        // Label-setting: C = D for a fixed vertex.  Label-correcting: the
-        // distance at the start of this relaxation step.
-        dx = P.lc ? P.snap[g] : (L::ld_dc(rx, cur).y & kCMask);
+        // Label-setting: C = D for a fixed vertex.  Label-correcting and
+        // windowed: the distance at the start of this relaxation step.
+        dx = (P.lc || P.win) ? P.snap[g] : (L::ld_dc(rx, cur).y & kCMask);
         a.visits++;
     }
     Tile tl = make_tile(st, deg, (u64)(adj + b), lane);
@@ -723,7 +737,7 @@ __device__ void relax_hub(const RoundParams& P, WarpStage<typename L::RSlot>& st
     const u64 cb = b + (u64)k * P.chunk;
     const u64 ce = umin64(cb + P.chunk, e_end);
     typename L::Rec* rx = L::rec(P) + g;
-    const u64 dx = P.lc ? P.snap[g] : (L::ld_dc(rx, cur).y & kCMask);
+    const u64 dx = (P.lc || P.win) ? P.snap[g] : (L::ld_dc(rx, cur).y & kCMask);
     if (k == 0 && lane == 0) {
         rx->cf[cur ^ 1] = rx->cf[cur];
         a.visits++;
@@ -793,9 +807,9 @@ __device__ void relax_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
     const u64 fhpk = ctl->FHpk[cur];
     const u32 nfh = min((u32)(fhpk >> 32), P.L.capH), fh_chunks = (u32)fhpk;
     const u32 tiles = (nfs + 31) >> 5;
-    // Label-correcting: copy the fixed lower-bound word of the vertices
-    // fixed last round into the other parity slot (32 per item).
-    const u32 nfx = P.lc ? min(ctl->nFX[cur], P.L.capS) : 0u;
+    // Label-correcting and windowed: copy the fixed lower-bound word of the
+    // vertices fixed last round into the other parity slot (32 per item).
+    const u32 nfx = (P.lc || P.win) ? min(ctl->nFX[cur], P.L.capS) : 0u;
     const u32 total = tiles + fh_chunks + ((nfx + 31) >> 5);
 
     Acc a = {kInf64, kInf64, 0, 0, 0};
@@ -867,6 +881,13 @@ __device__ __forceinline__ u64 seg_min(u64 v, u32 brk, u32 lane) {
 // D[x] + w >= D[y], an unfixed one lb(x) + w >= minD + inWeight[y].
 __device__ __forceinline__ bool cheap_rules_fix(u64 dy, u32 inw, u64 thr, u64 minD) {
     return (inw != kNoOutW && dy <= minD + inw) || dy <= thr;
+}
+
+// Windowed relaxation: the bound below which a changed active vertex relaxes
+// before it is fixed (minD of this round + delta, saturating).
+__device__ __forceinline__ u64 win_limit(u64 minD, u64 delta) {
+    const u64 l = minD + delta;
+    return l < minD ? kInf64 : l;
 }
 
 // Decision for one active vertex after its Eq. (1) minimum m is known.
@@ -962,7 +983,19 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
     __syncwarp();
     // Label-setting: the fixed vertices are the next frontier.  (Label-
     // correcting: the relaxation built it; the fixed vertices go to FX.)
-    const bool fx = valid && fix && !P.lc, sv = valid && !fix;
+    // Windowed: the fixed vertices and, while D < minD + delta, the
+    // survivors -- each only if its D changed since it last relaxed; the
+    // fixed vertices also go to FX.
+    bool fx = valid && fix && !P.lc;
+    const bool sv = valid && !fix;
+    if (P.win) {
+        fx = valid && P.chg[g] != 0 && (fix || dy < win_limit(minD, P.delta));
+        if (fx) {
+            P.chg[g] = 0;
+            P.snap[g] = dy;
+        }
+        warp_append(P, &P.ctl->nFX[nxt], P.L.FX[nxt], valid && fix, g, lane);
+    }
     const bool fs = fx && odeg <= P.hub;
     if (P.lc) wq_push(P, qf, &P.ctl->nFX[nxt], P.L.FX[nxt], valid && fix, g, lane);
     else wq_push(P, qf, &P.ctl->nFS[nxt], P.L.FS[nxt], fs, g, lane);
@@ -1038,21 +1071,37 @@ __device__ void cup_hub(const RoundParams& P, WarpStage<typename L::CSlot>& st, 
     if (!cheap_fix) cn = decide(P, dy, cy, m, thr, minD, fix);
     L::set_c(ry, nxt, cn | (fix ? kFixed : 0ull));
     a.visits++;
+    // The next frontier and FX as in cup_small.
+    bool front = fix && !P.lc;
     if (fix) {
         P.fround[g] = (int)r;
-        if (!P.lc) {
-            const u64 odeg = d.out_off[yloc + 1] - d.out_off[yloc];
-            if (odeg <= P.hub) put_small(P, P.L.FS[nxt], atomicAdd(&P.ctl->nFS[nxt], 1u), g);
-            else put_hub(P, &P.ctl->FHpk[nxt], P.L.FH[nxt], P.L.FC[nxt], g, odeg);
-            if (MULTI) atomicAdd(&P.ivar[inst].nfix[nxt], 1u);
-            else an.nfix++;
-        } else {
-            put_small(P, P.L.FX[nxt], atomicAdd(&P.ctl->nFX[nxt], 1u), g);
-        }
+        if (P.lc || P.win) put_small(P, P.L.FX[nxt], atomicAdd(&P.ctl->nFX[nxt], 1u), g);
     } else {
         put_hub(P, &P.ctl->AHpk[nxt], P.L.AH[nxt], P.L.AC[nxt], g, ie - ib);
         fold<MULTI>(P, inst, nxt, dy, outw == kNoOutW ? P.dinf : dy + outw, an);
     }
+    if (P.win) {
+        front = P.chg[g] != 0 && (fix || dy < win_limit(minD, P.delta));
+        if (front) {
+            P.chg[g] = 0;
+            P.snap[g] = dy;
+        }
+    }
+    if (front) {
+        const u64 odeg = d.out_off[yloc + 1] - d.out_off[yloc];
+        if (odeg <= P.hub) put_small(P, P.L.FS[nxt], atomicAdd(&P.ctl->nFS[nxt], 1u), g);
+        else put_hub(P, &P.ctl->FHpk[nxt], P.L.FH[nxt], P.L.FC[nxt], g, odeg);
+        if (MULTI) atomicAdd(&P.ivar[inst].nfix[nxt], 1u);
+        else an.nfix++;
+    }
+}
+
+// Whether query v has rounds left after round r (nxt = the parity of round
+// r + 1): a next frontier (counted in nfix) or, windowed, active vertices
+// that wait outside the window (their D was folded into minD[nxt]).
+__device__ __forceinline__ bool has_next(const RoundParams& P, const InstVar* v, u32 nxt) {
+    if (ld_volatile(&v->nfix[nxt]) != 0) return true;
+    return P.win && ld_volatile(&v->minD[nxt]) != kInf64;
 }
 
 // End of round r, run by the last CTA: retire finished queries, advance the
@@ -1070,7 +1119,7 @@ __device__ void round_epilogue(const RoundParams& P, u32 r) {
         if (ld_volatile(&v->status) != kRunning) continue;
         const u32 nr = r - v->start_round + 1;
         const u32 tgt = v->target;
-        if (ld_volatile(&v->nfix[nxt]) == 0) {
+        if (!has_next(P, v, nxt)) {
             v->rounds = nr;
             v->status = kDone;
         } else if (tgt != kNoTarget &&
@@ -1090,8 +1139,8 @@ __device__ void round_epilogue(const RoundParams& P, u32 r) {
     if (threadIdx.x == 0) {
         const u32 total = s_running;
         // Vertices fixed this round (single query): label-setting counts them
-        // in nfix, label-correcting lists them in FX.
-        if (ninst == 1) ctl->stats[4] += P.lc ? ctl->nFX[nxt] : P.ivar[0].nfix[nxt];
+        // in nfix, label-correcting and windowed relaxation list them in FX.
+        if (ninst == 1) ctl->stats[4] += (P.lc || P.win) ? ctl->nFX[nxt] : P.ivar[0].nfix[nxt];
         ctl->running = total;
         ctl->cup_only = 0;
         ctl->round = r + 1;
@@ -1349,7 +1398,7 @@ __device__ __forceinline__ bool tail_next_single(const RoundParams& P, u32 r) {
     const InstVar* v = P.ivar;
     const Ctl* ctl = P.ctl;
     const u32 nxt = (r & 1u) ^ 1u;
-    if (ld_volatile(&v->nfix[nxt]) == 0) return false;
+    if (!has_next(P, v, nxt)) return false;
     const u32 tgt = v->target;
     if (tgt != kNoTarget && *(volatile const int*)&P.fround[P.g.base + tgt] >= 0) return false;
     if (v->max_rounds != 0 && r - v->start_round + 1 >= v->max_rounds) return false;

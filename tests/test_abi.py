@@ -107,6 +107,26 @@ def test_layout_option_checked_on_the_host(lib):
     assert lib.sssp_layout(None) == 0
 
 
+def test_rule_bits_checked_on_the_host(lib):
+    import paper_1812_10499_gb300 as P
+    rp = np.array([0, 1, 1], dtype=np.uint64)
+    col = np.array([1], dtype=np.uint32)
+    wa = np.array([3], dtype=np.uint32)
+
+    def create(rule, delta=0):
+        o = P.sssp_options_default()
+        o.rule = rule
+        o.delta = delta
+        h = ctypes.c_void_p()
+        return lib.sssp_create(2, 1, rp.ctypes.data, col.ctypes.data, wa.ctypes.data, None,
+                               None, None, ctypes.byref(o), ctypes.byref(h))
+    # An unknown bit, and windowed with label-correcting relaxation.
+    assert create(8) == -1
+    assert create(P.SSSP_RULE_WINDOWED | P.SSSP_RULE_LABEL_CORRECTING, 5) == -1
+    # The options structure carries the window width after alloc_ctx.
+    assert P.sssp_options.delta.offset == P.sssp_options.alloc_ctx.offset + 8
+
+
 def test_selftest_argument_checked_on_the_host(lib):
     assert lib.sssp_selftest_barrier_timeout(0) == -1
     assert lib.sssp_selftest_barrier_timeout(20000) == -1

@@ -34,12 +34,15 @@ def gpu_solve(P, g, s, max_rounds=0, **opt):
         P.sssp_destroy(h)
 
 
-def assert_parity(P, g, s, mode=oracle.RULE_THR, **opt):
+def assert_parity(P, g, s, mode=oracle.RULE_THR, delta=None, **opt):
     # The library's rule bits are the oracle's mode bits (minD clamp = 1,
-    # label-correcting = 2).
-    if mode != oracle.RULE_THR:
+    # label-correcting = 2, cheaper rules first = 4, windowed = 16).
+    if delta is not None:
+        opt.setdefault("rule", mode | P.SSSP_RULE_WINDOWED)
+        opt.setdefault("delta", delta)
+    elif mode != oracle.RULE_THR:
         opt.setdefault("rule", mode)
-    ref = oracle.round_r(g, s, mode=mode)
+    ref = oracle.round_r(g, s, mode=mode, delta=delta)
     out = gpu_solve(P, g, s, **opt)
     assert np.array_equal(out["dist"], ref.dist)
     assert np.array_equal(out["parent"], ref.parent)
@@ -308,6 +311,83 @@ def test_label_correcting_batch(sssp_lib):
         dists, rounds = P.sssp_solve_batch(hs, srcs)
         for g, s, d, r in zip(graphs, srcs, dists, rounds):
             ref = oracle.round_r(g, s, mode=oracle.LABEL_CORRECT)
+            assert np.array_equal(d, ref.dist) and int(r) == ref.rounds
+    finally:
+        for h in hs:
+            P.sssp_destroy(h)
+
+
+@LAYOUTS
+@pytest.mark.parametrize("loop", ["graph", "host", "persistent"])
+@pytest.mark.parametrize("delta", [0, 3, 40, 2**64 - 1], ids=["d0", "d3", "d40", "dinf"])
+def test_windowed(sssp_lib, layout, loop, delta):
+    """Windowed relaxation (the lower bounds with a Delta-stepping window):
+    bit-exact with the oracle -- state, round count and counters -- on
+    random, skewed (small hub thresholds too), grid, layered and partly
+    unreachable graphs, from the label-setting end (delta 0) to the
+    label-correcting end."""
+    P = sssp_lib
+    lm = {"graph": P.SSSP_LOOP_GRAPH, "host": P.SSSP_LOOP_HOST,
+          "persistent": P.SSSP_LOOP_PERSISTENT}[loop]
+    kw = dict(delta=delta, layout=layout, loop_mode=lm)
+    assert_parity(P, gg.random_graph(4096, 8, 1, 100, 1812_10499), 0, **kw)
+    g = gg.rmat(13, 8, 1, 255, 5)
+    s = int(np.argmax(g.out_degree()))
+    assert_parity(P, g, s, **kw)
+    assert_parity(P, g, s, hub_degree=8, chunk_edges=32, **kw)
+    assert_parity(P, gg.grid(60, 50, 1, 1000, 3), 0, **kw)
+    assert_parity(P, gg.dag(10, 200, 6, 3, 1, 300, 4), 0, **kw)
+    assert_parity(P, gg.random_var_graph(2000, 0, 7, 1, 50, 9), 3, **kw)
+
+
+@LAYOUTS
+@pytest.mark.parametrize("variant", ["window9", "window10"])
+def test_windowed_hand_derived_trace(sssp_lib, layout, variant):
+    ex = worked_example()[variant]
+    g = gg.from_edges(ex["n"], ex["edges"])
+    out, _ = assert_parity(sssp_lib, g, ex["source"], delta=ex["delta"], layout=layout)
+    assert out["info"]["rounds"] == ex["rounds"]
+    assert out["fixed_round"].tolist() == ex["fixed_round"]
+
+
+@pytest.mark.parametrize("base", [oracle.RULE_THR, oracle.RULE_MIND, oracle.CHEAP_FIRST],
+                         ids=["thr", "mind", "cheap"])
+@pytest.mark.parametrize("tail", ["cluster", "grid"])
+def test_windowed_per_round_state(sssp_lib, base, tail, monkeypatch):
+    """The state after every round equals the oracle's (solves stopped with
+    max_rounds), with every round in the cluster tail kernel or none."""
+    monkeypatch.setenv("SSSP_TAIL_ITEMS", "1000000" if tail == "cluster" else "0")
+    g = gg.random_var_graph(700, 1, 6, 1, 50, 12)
+    for delta in (5, 60):
+        snaps = []
+        ref = oracle.round_r(g, 0, mode=base, delta=delta,
+                             on_round=lambda r, thr, mD, D, C, F: snaps.append(
+                                 (D.copy(), C.copy(), F.copy())))
+        assert ref.rounds == len(snaps)
+        for r, (D, C, F) in enumerate(snaps, start=1):
+            out = gpu_solve(sssp_lib, g, 0, max_rounds=r, rule=base | sssp_lib.SSSP_RULE_WINDOWED,
+                            delta=delta)
+            assert out["info"]["rounds"] == r
+            assert np.array_equal(out["dist"], D), f"D after round {r}"
+            assert np.array_equal(out["lower"], C), f"C after round {r}"
+            assert np.array_equal(out["fixed_round"], F), f"fixed after round {r}"
+
+
+def test_windowed_batch(sssp_lib):
+    """Several graphs in one batched launch, windowed: each equals its own
+    oracle run (distances and round count)."""
+    P = sssp_lib
+    o = P.sssp_options_default()
+    o.rule = P.SSSP_RULE_WINDOWED
+    o.delta = 120
+    graphs = [gg.random_var_graph(n, 2, 10, 1, 500, 70 + i) for i, n in enumerate((300, 5000, 1200, 64))]
+    graphs.append(gg.grid(40, 30, 1, 1000, 75))
+    hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w, options=o) for g in graphs]
+    try:
+        srcs = [0, 7, 100, 5, 0]
+        dists, rounds = P.sssp_solve_batch(hs, srcs)
+        for g, s, d, r in zip(graphs, srcs, dists, rounds):
+            ref = oracle.round_r(g, s, delta=120)
             assert np.array_equal(d, ref.dist) and int(r) == ref.rounds
     finally:
         for h in hs:
