@@ -356,7 +356,7 @@ def run_ours(args):
 
     # ---- end to end through the public host API (dist copied to host)
     e2e_steps = max(1, min(args.steps, 10))
-    host_out = [np.empty(g.n, dtype=np.uint64)]
+    host_out = [P.host_empty(g.n)]           # page-locked: the copy is one DMA
     torch.cuda.synchronize()
     if dist:
         dist.barrier()

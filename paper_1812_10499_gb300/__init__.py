@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -123,6 +124,8 @@ def load(path: str = LIB_PATH):
         "sssp_solve_noalloc": (c_int, [u32, vp, vp, vp, vp, u32, u32, vp,
                                        ctypes.POINTER(u32), vp]),
         "sssp_destroy": (None, [vp]),
+        "sssp_host_alloc": (c_int, [ctypes.c_size_t, ctypes.POINTER(vp)]),
+        "sssp_host_free": (None, [vp]),
         "sssp_strerror": (ctypes.c_char_p, [c_int]),
         "sssp_num_vertices": (u32, [vp]),
         "sssp_num_edges": (u64, [vp]),
@@ -222,6 +225,20 @@ def sssp_destroy(h: int):
     if h:
         load().sssp_destroy(h)
         _keepalive.pop(h, None)
+
+
+def host_empty(n: int, dtype=np.uint64) -> np.ndarray:
+    """An uninitialised numpy array of n elements in page-locked host memory
+    (sssp_host_alloc), freed when the array is collected.  Passed as the
+    `out` of sssp_solve it takes the distances by DMA every solve."""
+    lib = load()
+    dt = np.dtype(dtype)
+    nbytes = max(1, int(n) * dt.itemsize)
+    p = ctypes.c_void_p()
+    _check(lib.sssp_host_alloc(nbytes, ctypes.byref(p)), "sssp_host_alloc")
+    buf = (ctypes.c_char * nbytes).from_address(p.value)
+    weakref.finalize(buf, lib.sssp_host_free, p.value)
+    return np.frombuffer(buf, dtype=dt, count=int(n))
 
 
 def sssp_profile(h: int, enable: bool) -> dict:

@@ -792,6 +792,21 @@ void sssp_destroy(sssp_handle h) {
     delete h;
 }
 
+int sssp_host_alloc(size_t bytes, void** out) {
+    if (!out || bytes == 0) return SSSP_E_INVAL;
+    *out = nullptr;
+    if (cudaHostAlloc(out, bytes, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();   // clear the runtime's last-error state
+        *out = nullptr;
+        return SSSP_E_NOMEM;
+    }
+    return SSSP_OK;
+}
+
+void sssp_host_free(void* p) {
+    if (p) cudaFreeHost(p);
+}
+
 uint32_t sssp_num_vertices(sssp_handle h) { return h ? h->n : 0; }
 uint64_t sssp_num_edges(sssp_handle h) { return h ? h->m : 0; }
 int sssp_solve_to(sssp_handle h, uint32_t source, uint32_t target, uint64_t* dist_target,

@@ -127,6 +127,13 @@ def test_rule_bits_checked_on_the_host(lib):
     assert P.sssp_options.delta.offset == P.sssp_options.alloc_ctx.offset + 8
 
 
+def test_host_alloc_arguments_checked_on_the_host(lib):
+    p = ctypes.c_void_p()
+    assert lib.sssp_host_alloc(0, ctypes.byref(p)) == -1
+    assert lib.sssp_host_alloc(64, None) == -1
+    lib.sssp_host_free(None)
+
+
 def test_selftest_argument_checked_on_the_host(lib):
     assert lib.sssp_selftest_barrier_timeout(0) == -1
     assert lib.sssp_selftest_barrier_timeout(20000) == -1

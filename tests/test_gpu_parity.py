@@ -513,6 +513,26 @@ def test_host_outputs_and_reused_output_array(sssp_lib):
         P.sssp_destroy(h)
 
 
+def test_page_locked_output_array(sssp_lib):
+    """host_empty gives a page-locked array; solves into it (reused across
+    calls) equal solves into a pageable one."""
+    P = sssp_lib
+    g = gg.rmat(12, 8, 1, 255, 31)
+    h = P.sssp_create(g.n, g.row_ptr, g.col, g.w)
+    try:
+        pinned = P.host_empty(g.n)
+        assert pinned.dtype == np.uint64 and pinned.shape == (g.n,)
+        for s in (0, 5, 77):
+            ref = oracle.round_r(g, s).dist
+            d1, _ = P.sssp_solve(h, s, out=pinned)
+            assert d1 is pinned
+            assert np.array_equal(pinned, ref)
+            assert np.array_equal(P.sssp_solve(h, s, out=np.empty(g.n, np.uint64))[0], ref)
+        del pinned, d1
+    finally:
+        P.sssp_destroy(h)
+
+
 def test_given_csc_and_torch_allocator(sssp_lib):
     torch = pytest.importorskip("torch")
     P = sssp_lib
