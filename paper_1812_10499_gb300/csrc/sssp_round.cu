@@ -343,6 +343,16 @@ __device__ __forceinline__ void warp_append(const RoundParams& P, u32* counter, 
     if (pred) put_small(P, list, base + __popc(mask & ((1u << lane) - 1u)), g);
 }
 
+// The static first work item of warp wib of this CTA.  Items are dealt
+// round-robin over the CTAs, starting with CTA 1 and ending with CTA 0: a
+// small list spreads over many SMs, and CTA 0 -- which runs the end-of-round
+// epilogue right before the cluster tail kernel's next relaxation -- gets an
+// item only when every other CTA has one.
+__device__ __forceinline__ u32 static_item(u32 wib) {
+    const u32 rank = blockIdx.x == 0 ? gridDim.x - 1 : blockIdx.x - 1;
+    return wib * gridDim.x + rank;
+}
+
 // Accumulators a thread carries through one phase.
 struct Acc {
     u64 fmin_d, fmin_t;     // folds of minD / threshold (single-query mode)
@@ -820,7 +830,7 @@ __device__ void relax_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
     pd.r = r;
     // First item per warp is static (no atomic); the rest are pulled.
     const u32 nwarps = gridDim.x * kWarps;
-    for (u32 item = blockIdx.x * kWarps + wib; item < total;) {
+    for (u32 item = static_item(wib); item < total;) {
         if (item < tiles) {
             relax_small<MULTI, L>(P, s_st[wib], item, nfs, cur, lane, a, q, qf, pd);
         } else if (item < tiles + fh_chunks) {
@@ -1220,7 +1230,7 @@ __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r)
     WarpQueue qf = {s_qf + wib * kQCap, 0}, qa = {s_qa + wib * kQCap, 0};
     // First item per warp is static (no atomic); the rest are pulled.
     const u32 nwarps = gridDim.x * kWarps;
-    for (u32 item = blockIdx.x * kWarps + wib; item < total;) {
+    for (u32 item = static_item(wib); item < total;) {
         if (item < tiles)
             cup_small<MULTI, L>(P, s_st[wib], item, nas, r, cur, lane, s_min + wib * 32, thr,
                                 minD, a, an, qf, qa);
@@ -1398,13 +1408,19 @@ __device__ __forceinline__ bool tail_next_single(const RoundParams& P, u32 r) {
     const InstVar* v = P.ivar;
     const Ctl* ctl = P.ctl;
     const u32 nxt = (r & 1u) ^ 1u;
-    if (!has_next(P, v, nxt)) return false;
+    // Every load first (one memory round trip), then the decision.
     const u32 tgt = v->target;
-    if (tgt != kNoTarget && *(volatile const int*)&P.fround[P.g.base + tgt] >= 0) return false;
+    const u32 nfix = ld_volatile(&v->nfix[nxt]);
+    const u64 mind = ld_volatile(&v->minD[nxt]);
+    const int tfix = tgt != kNoTarget ? *(volatile const int*)&P.fround[P.g.base + tgt] : -1;
+    const u32 stop = ld_volatile(&ctl->stop_round);
+    const u32 nfs = ld_volatile(&ctl->nFS[nxt]);
+    const u64 fhpk = ld_volatile(&ctl->FHpk[nxt]);
+    if (nfix == 0 && !(P.win && mind != kInf64)) return false;   // has_next
+    if (tfix >= 0) return false;
     if (v->max_rounds != 0 && r - v->start_round + 1 >= v->max_rounds) return false;
-    if (r + 1 > ctl->round_limit || r + 1 > ld_volatile(&ctl->stop_round)) return false;
-    const u32 fi = ((ld_volatile(&ctl->nFS[nxt]) + 31) >> 5) + (u32)ld_volatile(&ctl->FHpk[nxt]);
-    return fi <= P.tail_items;
+    if (r + 1 > ctl->round_limit || r + 1 > stop) return false;
+    return ((nfs + 31) >> 5) + (u32)fhpk <= P.tail_items;
 }
 
 // Launched as one cluster of kTailCTAs CTAs.  Every CTA takes the same
