@@ -699,14 +699,14 @@ __device__ __forceinline__ void relax_consume(const RoundParams& P, u32 cur, Acc
 template <bool MULTI, class L>
 __device__ void relax_small(const RoundParams& P, WarpStage<typename L::RSlot>& st, u32 t,
                             u32 nfs, u32 cur, u32 lane, Acc& a, WarpQueue& q, WarpQueue& qf,
-                            Pend& pd) {
+                            Pend& pd, bool has_pre, u32 gpre) {
     const u32 idx = t * 32 + lane;
     const bool valid = idx < nfs;
     u32 g = 0, xloc = 0, inst = 0, deg = 0;
     u64 gbase = 0, b = 0, dx = 0;
     const uint2* adj = P.g.out_adj;
     if (valid) {
-        g = P.L.FS[cur][idx];
+        g = has_pre ? gpre : P.L.FS[cur][idx];
         const InstDesc& d = desc_of<MULTI>(P, g, inst);
         gbase = d.base;
         adj = d.out_adj;
@@ -785,6 +785,11 @@ __device__ void relax_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
     Ctl* ctl = P.ctl;
     const u32 cur = r & 1u, nxt = cur ^ 1u;
     const u32 lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    // The static item's small-list entry, loaded beside the list counts (one
+    // memory round trip fewer); it is used only if the item is a small tile.
+    const u32 item0 = static_item(wib);
+    const u32 pidx = item0 * 32 + lane;
+    const u32 gpre = pidx < P.L.capS ? P.L.FS[cur][pidx] : 0u;
 
     if (blockIdx.x == 0) {
         // Open the slots of round r + 1 (last read in round r - 1).
@@ -830,9 +835,10 @@ __device__ void relax_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
     pd.r = r;
     // First item per warp is static (no atomic); the rest are pulled.
     const u32 nwarps = gridDim.x * kWarps;
-    for (u32 item = static_item(wib); item < total;) {
+    for (u32 item = item0; item < total;) {
         if (item < tiles) {
-            relax_small<MULTI, L>(P, s_st[wib], item, nfs, cur, lane, a, q, qf, pd);
+            relax_small<MULTI, L>(P, s_st[wib], item, nfs, cur, lane, a, q, qf, pd,
+                                  item == item0, gpre);
         } else if (item < tiles + fh_chunks) {
             relax_hub<MULTI, L>(P, s_st[wib], item - tiles, nfh, cur, lane, a, q, qf, pd);
         } else {
@@ -912,7 +918,7 @@ __device__ __forceinline__ u64 decide(const RoundParams& P, u64 dy, u64 cy, u64 
 template <bool MULTI, class L>
 __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st, u32 t, u32 nas,
                           u32 r, u32 cur, u32 lane, u64* smin, u64 thr0, u64 minD0, Acc& a,
-                          Acc& an, WarpQueue& qf, WarpQueue& qa) {
+                          Acc& an, WarpQueue& qf, WarpQueue& qa, bool has_pre, u32 gpre) {
     const u32 nxt = cur ^ 1u;
     const u32 idx = t * 32 + lane;
     const bool valid = idx < nas;
@@ -922,7 +928,7 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
     const uint2* in_adj = P.g.in_adj;
     typename L::Rec* rec = L::rec(P);
     if (valid) {
-        g = P.L.AS[cur][idx];
+        g = has_pre ? gpre : P.L.AS[cur][idx];
         const InstDesc& d = desc_of<MULTI>(P, g, inst);
         gbase = d.base;
         in_adj = d.in_adj;
@@ -1195,6 +1201,11 @@ __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r)
     Ctl* ctl = P.ctl;
     const u32 cur = r & 1u, nxt = cur ^ 1u;
     const u32 lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    // The static item's small-list entry, loaded beside the list counts (as
+    // in relax_phase).
+    const u32 item0 = static_item(wib);
+    const u32 pidx = item0 * 32 + lane;
+    const u32 gpre = pidx < P.L.capS ? P.L.AS[cur][pidx] : 0u;
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->work[0] = 0;
     if (P.lc && blockIdx.x == 0) {
         // Label-correcting: the next relaxation appends the frontier after it
@@ -1230,10 +1241,10 @@ __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r)
     WarpQueue qf = {s_qf + wib * kQCap, 0}, qa = {s_qa + wib * kQCap, 0};
     // First item per warp is static (no atomic); the rest are pulled.
     const u32 nwarps = gridDim.x * kWarps;
-    for (u32 item = static_item(wib); item < total;) {
+    for (u32 item = item0; item < total;) {
         if (item < tiles)
             cup_small<MULTI, L>(P, s_st[wib], item, nas, r, cur, lane, s_min + wib * 32, thr,
-                                minD, a, an, qf, qa);
+                                minD, a, an, qf, qa, item == item0, gpre);
         else if (item < tiles + ah_chunks)
             cup_hub<MULTI, L>(P, s_st[wib], item - tiles, nah, r, cur, lane, thr, minD, a, an);
         else
