@@ -176,9 +176,10 @@ def peaks():
 
 
 def kernel_source_sha256():
-    """sha256 over the round kernels' sources (layout header, then kernels)."""
+    """sha256 over the round kernels' sources and launch defaults (layout
+    header, kernels, engine header with the default hub and chunk sizes)."""
     h = hashlib.sha256()
-    for f in ("sssp_dev.cuh", "sssp_round.cu"):
+    for f in ("sssp_dev.cuh", "sssp_round.cu", "sssp_engine.h"):
         h.update(open(os.path.join(ROOT, "paper_1812_10499_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 

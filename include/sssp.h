@@ -129,7 +129,7 @@ typedef struct sssp_options {
     uint32_t loop_mode;      /* SSSP_LOOP_*                                                */
     uint32_t hub_degree;     /* vertices of degree > hub_degree are split into chunks
                                 processed by many warps (0 = library default, 256)         */
-    uint32_t chunk_edges;    /* edges per hub chunk (0 = default 512, must be a multiple
+    uint32_t chunk_edges;    /* edges per hub chunk (0 = default 1024, must be a multiple
                                 of 32)                                                     */
     uint32_t block_threads;  /* threads per CTA of the round kernels (0 = 256)             */
     uint32_t ctas_per_sm;    /* CTAs per SM of the round kernels (0 = from occupancy)      */

@@ -57,7 +57,7 @@ namespace engine {
 constexpr u32 kThreads = 256;
 constexpr u32 kPageShift = 10;
 constexpr u32 kDefaultHub = 256;
-constexpr u32 kDefaultChunk = 512;
+constexpr u32 kDefaultChunk = 1024;
 constexpr u32 kDefaultTailItems = 512;
 
 #define CK(call)                                       \
