@@ -52,3 +52,19 @@ def test_algorithmic_bytes_per_unit():
     import bench
     info = {"out_scanned": 10, "front_visits": 2, "in_scanned": 100, "active_visits": 3}
     assert bench.alg_bytes(info) == (16 * 10 + 36 * 2, 24 * 100 + 48 * 3)
+
+
+def test_window_width_default_and_rule_bits():
+    """The windowed rules take --delta, else max weight / maximum out-degree
+    (at least 1); their rule bits are the library's."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import graphgen as gg
+    import paper_1812_10499_gb300 as P
+    g = gg.grid(40, 30, 1, 10000, 1)                       # max out-degree 4
+    assert bench.window_delta(g, None) == round(int(g.w.max()) / 4)
+    assert bench.window_delta(g, 77) == 77
+    assert bench.window_delta(gg.rmat(12, 16, 1, 255, 2), None) == 1   # hubs: window 1
+    for name in ("thr-win", "mind-win", "thr-cheap-win"):
+        assert bench.RULES[name] & P.SSSP_RULE_WINDOWED
+        assert not bench.RULES[name] & P.SSSP_RULE_LABEL_CORRECTING
