@@ -175,12 +175,39 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def _code_only(text):
+    """C/C++ source with comments removed and whitespace runs collapsed (string
+    and character literals kept as they are)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            i = text.find("\n", i)
+            i = n if i < 0 else i
+        elif text.startswith("/*", i):
+            i = text.find("*/", i + 2)
+            i = n if i < 0 else i + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_sha256():
-    """sha256 over the round kernels' sources and launch defaults (layout
-    header, kernels, engine header with the default hub and chunk sizes)."""
+    """sha256 over the code (comments and layout ignored) of the round kernels'
+    sources and launch defaults: layout header, kernels, engine header with the
+    default hub and chunk sizes."""
     h = hashlib.sha256()
     for f in ("sssp_dev.cuh", "sssp_round.cu", "sssp_engine.h"):
-        h.update(open(os.path.join(ROOT, "paper_1812_10499_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_1812_10499_gb300", "csrc", f)).read()
+        h.update(_code_only(text).encode())
     return h.hexdigest()
 
 

@@ -68,3 +68,16 @@ def test_window_width_default_and_rule_bits():
     for name in ("thr-win", "mind-win", "thr-cheap-win"):
         assert bench.RULES[name] & P.SSSP_RULE_WINDOWED
         assert not bench.RULES[name] & P.SSSP_RULE_LABEL_CORRECTING
+
+
+def test_kernel_hash_ignores_comments_and_layout():
+    """The profiles' source hash follows the code only: comments and spacing
+    do not change it, a code token does; literals are kept whole."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = "int f(int x) {  // add one\n    return x + 1; /* done */ }\n"
+    b = "int f(int x) {\n  return x + 1;\n}\n"
+    assert bench._code_only(a) == bench._code_only(b) == "int f(int x) { return x + 1; }"
+    assert bench._code_only("return x + 2;") != bench._code_only("return x + 1;")
+    assert bench._code_only('const char* s = "a // b /* c */";') == 'const char* s = "a // b /* c */";'
+    assert bench._code_only("char q = '\"'; // x") == "char q = '\"';"
