@@ -1408,13 +1408,15 @@ __device__ __forceinline__ u32 tail_cup_fits(const RoundParams& P, u32 r) {
 }
 
 // Whether a single query goes on to round r + 1 in the tail kernel: the
-// decision of the end-of-round epilogue (a round that fixed or, label-
-// correcting, changed nothing ends the query; so do the target and the round
-// limits) and the frontier's size check.  Every input is final once round r's
-// lower-bound phase has passed a cluster barrier and is written by no step of
-// round r + 1, so CTAs that already started its relaxation (which appends to
-// the active lists: their size is checked after it, tail_cup_fits) cannot
-// change another CTA's decision.
+// decision of the end-of-round epilogue (a round that leaves no next frontier
+// -- and, windowed, no active vertex -- ends the query; so do the target and
+// the round limits) and the frontier's size check.  Every input is final once
+// round r's lower-bound phase has passed a cluster barrier and is written by no
+// step of round r + 1, so CTAs that already started its relaxation (which
+// appends to the active lists: their size is checked after it, tail_cup_fits)
+// cannot change another CTA's decision.  The one exception, minD of round r + 1
+// (the relaxation folds its candidates into it), is read only when the next
+// frontier is empty, and then round r + 1 relaxes nothing.
 __device__ __forceinline__ bool tail_next_single(const RoundParams& P, u32 r) {
     const InstVar* v = P.ivar;
     const Ctl* ctl = P.ctl;
