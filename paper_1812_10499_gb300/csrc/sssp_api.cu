@@ -519,6 +519,18 @@ void destroy_impl(sssp_graph* h) {
     h->stream = nullptr;
 }
 
+// The device address of a page-locked host allocation mapped into the
+// device's address space, or nullptr (pageable memory, or not mapped).
+u64* mapped_device_ptr(void* host) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    return static_cast<u64*>(at.devicePointer);
+}
+
 int read_status(Context& c, cudaStream_t st, u32 ninst) {
     CK(cudaMemcpyAsync(c.h_ctl, c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(c.h_ivar, c.P.ivar, sizeof(InstVar) * ninst, cudaMemcpyDeviceToHost, st));
@@ -873,7 +885,11 @@ int sssp_solve_ex(sssp_handle h, uint32_t source, const sssp_solve_args* args,
     Context& c = h->single;
     u64* const a_dist = reinterpret_cast<u64*>(a.dist);
     u64* const a_lower = reinterpret_cast<u64*>(a.lower);
-    u64* dist_dev = a.dev ? a_dist : (a_dist ? c.stage : nullptr);
+    // A page-locked, device-mapped host array (sssp_host_alloc) takes the
+    // distances straight from the output kernel; any other host array gets
+    // them by a copy from device scratch.
+    u64* const dist_mapped = (!a.dev && a_dist) ? mapped_device_ptr(a_dist) : nullptr;
+    u64* dist_dev = a.dev ? a_dist : (dist_mapped ? dist_mapped : (a_dist ? c.stage : nullptr));
     // Host outputs other than dist go through device scratch in the lists
     // (free after the solve): parent / fround use FS, lower uses AS.
     u32* parent_dev = a.parent ? (a.dev ? a.parent : c.P.L.FS[0]) : nullptr;
@@ -884,10 +900,12 @@ int sssp_solve_ex(sssp_handle h, uint32_t source, const sssp_solve_args* args,
     if (a.lower && !a.dev) RC(tmp.get(&lower_dev, h->n));
     int rc = enqueue_single(h, source, a.max_rounds, st, dist_dev, parent_dev, fround_dev, lower_dev,
                             a.has_target ? a.target : kNoTarget);
-    if (rc == SSSP_OK) rc = read_status(c, st, 1);
+    // The host copies go on the stream before the status read, so that one
+    // synchronisation covers the solve, the outputs and the status (outputs
+    // are unspecified when the solve fails).
     if (rc == SSSP_OK && !a.dev) {
         cudaError_t e = cudaSuccess;
-        if (a.dist)
+        if (a.dist && !dist_mapped)
             e = cudaMemcpyAsync(a.dist, dist_dev, sizeof(u64) * h->n, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && a.parent)
             e = cudaMemcpyAsync(a.parent, parent_dev, sizeof(u32) * h->n, cudaMemcpyDeviceToHost, st);
@@ -896,12 +914,13 @@ int sssp_solve_ex(sssp_handle h, uint32_t source, const sssp_solve_args* args,
                                 cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && a.lower)
             e = cudaMemcpyAsync(a.lower, lower_dev, sizeof(u64) * h->n, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             rc = SSSP_E_CUDA;
         }
     }
+    if (rc == SSSP_OK) rc = read_status(c, st, 1);
+    else cudaStreamSynchronize(st);   // nothing enqueued may outlive the scratch below
     tmp.release();
     if (rc != SSSP_OK) return rc;
     const InstVar& v = c.h_ivar[0];
