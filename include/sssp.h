@@ -334,10 +334,10 @@ int sssp_solve_noalloc(uint32_t n, const uint64_t* out_off, const uint32_t* out_
 /* Releases a graph and its device memory.  NULL is ignored. */
 void sssp_destroy(sssp_handle h);
 
-/* Page-locked host memory for outputs that are copied every solve (dist_out
- * of sssp_solve and friends): the device writes it by DMA at the host link's
- * rate, while a pageable destination is staged through the driver's bounce
- * buffers.  bytes > 0 (else SSSP_E_INVAL); *out receives the pointer, owned
+/* Page-locked host memory, mapped into the device's address space, for
+ * outputs written every solve: given as the dist_out of sssp_solve /
+ * sssp_solve_ex, it is written directly by the output kernel (no device
+ * staging, no copy); a pageable destination gets a copy from device scratch.  bytes > 0 (else SSSP_E_INVAL); *out receives the pointer, owned
  * by the caller until sssp_host_free.  SSSP_E_NOMEM when the allocation
  * fails.  sssp_host_free(NULL) is ignored. */
 int sssp_host_alloc(size_t bytes, void** out);
