@@ -337,9 +337,10 @@ void sssp_destroy(sssp_handle h);
 /* Page-locked host memory, mapped into the device's address space, for
  * outputs written every solve: given as the dist_out of sssp_solve /
  * sssp_solve_ex, it is written directly by the output kernel (no device
- * staging, no copy); a pageable destination gets a copy from device scratch.  bytes > 0 (else SSSP_E_INVAL); *out receives the pointer, owned
- * by the caller until sssp_host_free.  SSSP_E_NOMEM when the allocation
- * fails.  sssp_host_free(NULL) is ignored. */
+ * staging, no copy); a pageable destination gets a copy from device scratch.
+ * bytes > 0 (else SSSP_E_INVAL); *out receives the pointer, owned by the
+ * caller until sssp_host_free.  SSSP_E_NOMEM when the allocation fails.
+ * sssp_host_free(NULL) is ignored. */
 int sssp_host_alloc(size_t bytes, void** out);
 void sssp_host_free(void* p);
 
