@@ -23,6 +23,18 @@ LIB_PATH = os.path.join(_HERE, "libsssp.so")
 
 SSSP_OK = 0
 SSSP_PENDING = 1
+SSSP_E_INVAL = -1
+SSSP_E_ZERO_WEIGHT = -2
+SSSP_E_SOURCE_RANGE = -3
+SSSP_E_OVERFLOW = -4
+SSSP_E_NOMEM = -5
+SSSP_E_DEVICE_TIMEOUT = -6
+SSSP_E_CUDA = -7
+SSSP_E_ROUND_LIMIT = -8
+SSSP_E_BUSY = -9
+SSSP_E_NOT_FOUND = -10
+SSSP_E_INTERNAL = -11
+SSSP_E_NOALLOC_LIMIT = -12
 SSSP_RULE_THRESHOLD = 0
 SSSP_RULE_MIND = 1
 SSSP_RULE_LABEL_CORRECTING = 2

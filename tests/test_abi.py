@@ -155,3 +155,18 @@ def test_product_fails_loudly_without_the_library(tmp_path):
             P.load(str(tmp_path / "missing.so"))
     finally:
         P._lib = saved
+
+
+def test_binding_constants_match_the_header():
+    """Every #define of include/sssp.h with a plain integer value has the
+    same value in the Python binding."""
+    import paper_1812_10499_gb300 as P
+    text = open(HEADER).read()
+    defs = re.findall(r"^#define (SSSP_\w+)\s+\(?(-?\d+)u?\)?", text, flags=re.M)
+    assert len(defs) > 20
+    for name, val in defs:
+        if hasattr(P, name):
+            assert getattr(P, name) == int(val), name
+    for name in ("SSSP_E_INVAL", "SSSP_E_SOURCE_RANGE", "SSSP_RULE_WINDOWED", "SSSP_LAYOUT_COMPACT",
+                 "SSSP_LOOP_PERSISTENT", "SSSP_PENDING"):
+        assert hasattr(P, name), name

@@ -151,3 +151,41 @@ def test_serve_alone_and_in_the_mix(sssp_lib):
         P.sssp_serve_close(server)
         for h in hs:
             P.sssp_destroy(h)
+
+
+def test_rule_mismatches_are_rejected(sssp_lib):
+    """The server runs the default rule only; a batch needs one rule and one
+    window for all its graphs.  Both refuse other handles with SSSP_E_INVAL
+    before any work is queued."""
+    P = sssp_lib
+    g = gg.random_var_graph(300, 2, 6, 1, 50, 3)
+
+    def make(rule=0, delta=0):
+        o = P.sssp_options_default()
+        o.rule = rule
+        o.delta = delta
+        return P.sssp_create(g.n, g.row_ptr, g.col, g.w, options=o)
+
+    hd = make()
+    hw = make(P.SSSP_RULE_WINDOWED, 40)
+    hw2 = make(P.SSSP_RULE_WINDOWED, 41)
+    hl = make(P.SSSP_RULE_LABEL_CORRECTING)
+    server = P.sssp_serve_open(budget_bytes=16 << 20, max_slots=2)
+    try:
+        out = np.zeros(g.n, dtype=np.uint64)
+        for h in (hw, hl):
+            with pytest.raises(P.SsspError) as e:
+                P.sssp_serve_submit(server, h, 0, out)
+            assert e.value.code == P.SSSP_E_INVAL
+        for pair in ((hw, hd), (hw, hw2), (hl, hw)):
+            with pytest.raises(P.SsspError) as e:
+                P.sssp_solve_batch(list(pair), [0, 0])
+            assert e.value.code == P.SSSP_E_INVAL
+        # the same handles alone, and a batch of one kind, still solve correctly
+        d, r = P.sssp_solve_batch([hw, hw], [0, 5])
+        assert np.array_equal(d[0], oracle.round_r(g, 0, delta=40).dist)
+        assert int(r[1]) == oracle.round_r(g, 5, delta=40).rounds
+    finally:
+        P.sssp_serve_close(server)
+        for h in (hd, hw, hw2, hl):
+            P.sssp_destroy(h)
