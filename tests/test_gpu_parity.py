@@ -341,6 +341,37 @@ def test_windowed(sssp_lib, layout, loop, delta):
 
 
 @LAYOUTS
+def test_windowed_single_target(sssp_lib, layout):
+    """Windowed relaxation stopped at the round that fixes a target: the
+    state and counters equal the oracle's windowed single-target run."""
+    P = sssp_lib
+    g = gg.random_var_graph(3000, 0, 8, 1, 200, 43)
+    delta = 60
+    full = oracle.round_r(g, 0, delta=delta)
+    reach = np.flatnonzero(full.fixed_round >= 0)
+    unreach = np.flatnonzero(full.fixed_round < 0)
+    order = reach[np.argsort(full.fixed_round[reach], kind="stable")]
+    targets = [0, int(order[1]), int(order[len(order) // 2]), int(order[-1]), int(unreach[0])]
+    h = P.sssp_create(g.n, g.row_ptr, g.col, g.w,
+                      options=make_opts(P, layout=layout, rule=P.SSSP_RULE_WINDOWED, delta=delta))
+    try:
+        for t in targets:
+            ref = oracle.round_r(g, 0, target=t, delta=delta)
+            out = P.sssp_solve_ex(h, 0, parent=True, fixed_round=True, lower=True, target=t)
+            for k, v in (("dist", ref.dist), ("parent", ref.parent),
+                         ("fixed_round", ref.fixed_round), ("lower", ref.C)):
+                assert np.array_equal(out[k], v), (t, k)
+            info = out["info"]
+            assert info["rounds"] == ref.rounds
+            # a run that reaches the end of the loop counts as finished
+            assert info["finished"] == (1 if ref.rounds == full.rounds else 0)
+            for k in ("out_scanned", "in_scanned", "active_visits", "front_visits"):
+                assert info[k] == ref.stats[k], (t, k)
+    finally:
+        P.sssp_destroy(h)
+
+
+@LAYOUTS
 @pytest.mark.parametrize("variant", ["window9", "window10"])
 def test_windowed_hand_derived_trace(sssp_lib, layout, variant):
     ex = worked_example()[variant]
