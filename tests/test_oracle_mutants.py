@@ -52,6 +52,8 @@ MUTANTS = {
                                 "if (windowed && changed[y] && D[y] <= window)"),
     "window above the threshold": ("const uint64_t window = sat_add(minD, delta);",
                                    "const uint64_t window = sat_add(thr, delta);"),
+    "windowed improvement not marked pending": ("if (windowed) changed[y] = 1;",
+                                                "if (windowed) changed[y] = 0;"),
     "windowed frontier drops fixed vertices": ("if (windowed ? changed[y] : !label_correct)",
                                                "if (windowed ? 0 : !label_correct)"),
     "heap compares wrong way": ("if (h->key[a] != h->key[b]) return h->key[a] < h->key[b];",
