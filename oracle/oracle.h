@@ -21,6 +21,10 @@
  *                       weights; hand-derived worked-example trace (3 rounds).
  *                       Round counts on general graphs: parity unpinned
  *                       beyond those invariants (the paper prints none).
+ *   orc_round_delta     pinned: delta = 0 equals orc_round; an unbounded delta
+ *                       equals ORC_LABEL_CORRECT round by round; hand-derived
+ *                       window9 / window10 traces (the strict minD + delta
+ *                       bound); per-round invariants for several deltas.
  *   orc_sp1 / orc_sp2   pinned: distances; heap-op claims of Theorems 2-3.
  *   orc_transpose       pinned: edge multiset equality.
  */
