@@ -170,10 +170,13 @@ int sssp_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t*
                 const uint32_t* w_in, const sssp_options* opt, sssp_handle* out);
 
 /* Single-source shortest paths from `source` (Sec. VI, rounds until no vertex
- * is left to explore).  dist_out: host u64[n], written on success.
- * rounds_out (nullable): number of rounds executed (relaxation steps,
- * including the last one that finds nothing new).  Blocks until done.
- * Errors: SSSP_E_INVAL, SSSP_E_SOURCE_RANGE, SSSP_E_ROUND_LIMIT, SSSP_E_CUDA. */
+ * is left to explore).  dist_out: host u64[n], written on success (an array
+ * from sssp_host_alloc is written directly by the device, any other through
+ * a copy).  rounds_out (nullable): number of rounds executed (relaxation
+ * steps, including the last one that finds nothing new).  Blocks until done.
+ * Errors: SSSP_E_INVAL, SSSP_E_SOURCE_RANGE, SSSP_E_ROUND_LIMIT,
+ * SSSP_E_DEVICE_TIMEOUT (a bounded device wait of the persistent loop gave
+ * up), SSSP_E_INTERNAL (a device-side guard tripped), SSSP_E_CUDA. */
 int sssp_solve(sssp_handle h, uint32_t source, uint64_t* dist_out, uint32_t* rounds_out);
 
 /* Same as sssp_solve, but dist_dev is a device u64[n] and the work is
@@ -204,7 +207,9 @@ typedef struct sssp_solve_args {
 
 typedef struct sssp_solve_info {
     uint32_t rounds;         /* rounds executed                                            */
-    uint32_t finished;       /* 1 if no vertex was left to explore                          */
+    uint32_t finished;       /* 1 if the rounds ran to completion: no frontier left (and,
+                                windowed, no active vertex); 0 if stopped by max_rounds or
+                                a target                                                   */
     uint64_t reached;        /* vertices fixed (reachable, source included)                */
     uint64_t out_scanned;    /* out-edges scanned by step (a)                              */
     uint64_t in_scanned;     /* in-edges scanned by step (b)                               */
