@@ -81,3 +81,18 @@ def test_kernel_hash_ignores_comments_and_layout():
     assert bench._code_only("return x + 2;") != bench._code_only("return x + 1;")
     assert bench._code_only('const char* s = "a // b /* c */";') == 'const char* s = "a // b /* c */";'
     assert bench._code_only("char q = '\"'; // x") == "char q = '\"';"
+
+
+def test_cpu_baseline_legs():
+    """The CPU legs time the oracle as it stands: Dijkstra on one thread, and
+    Round R one query per core in spawned processes that build their own
+    graphs from the seeds."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import graphgen as gg
+    g = gg.random_graph(2000, 6, 1, 50, 5)
+    gteps, used, secs = bench.cpu_dijkstra_gteps(g, [0, 1, 2], 60.0)
+    assert gteps > 0 and used == 3 and secs > 0
+    tasks = [(1500 + 10 * i, 7000 + i, i) for i in range(6)]
+    qps, done, busy, cores = bench.cpu_queries_per_s(tasks, 120.0, cores=2)
+    assert done == 6 and cores == 2 and busy > 0 and qps > 0
