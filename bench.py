@@ -286,33 +286,29 @@ def cpu_dijkstra_gteps(g, sources, budget_s):
 
 # CPU baseline of the batched workloads: the oracle's Round R, one query per
 # host core.  Workers are spawned (the parent has a CUDA context) and build
-# their graphs from the seeds, so no graph is pickled.
-_CPU_GRAPH = None
-
-
-def _cpu_worker_init(shared_rmat_seed):
-    """Pool initialiser: the graph all queries share (64 sources on one R-MAT
-    scale 18 graph) is generated once per worker, outside the timed work."""
-    global _CPU_GRAPH
-    if shared_rmat_seed is not None:
-        import graphgen as gg
-        _CPU_GRAPH = gg.rmat(18, 16, 1, 255, shared_rmat_seed)
+# their graphs from the seeds, so no graph is pickled.  A task is
+# ("var", n, seed, source) for a graph of the batched distribution or
+# ("rmat", scale, seed, source); R-MAT graphs are kept per worker.
+_CPU_RMAT = {}
 
 
 def _cpu_query(task):
-    """One query: (n, graph seed, source) of a batch graph, or (None, None,
-    source) on the shared graph.  Returns the oracle's seconds (generation
-    excluded)."""
+    """One query on the oracle; returns its seconds (generation excluded)."""
     import graphgen as gg
     import oracle
-    n, gseed, s = task
-    g = _CPU_GRAPH if n is None else gg.random_var_graph(n, 4, 16, 1, 1000, gseed)
+    kind, size, gseed, s = task
+    if kind == "var":
+        g = gg.random_var_graph(size, 4, 16, 1, 1000, gseed)
+    else:
+        g = _CPU_RMAT.get((size, gseed))
+        if g is None:
+            g = _CPU_RMAT[(size, gseed)] = gg.rmat(size, 16, 1, 255, gseed)
     t0 = time.perf_counter()
     oracle.round_r(g, s)
     return time.perf_counter() - t0
 
 
-def cpu_queries_per_s(tasks, budget_s, shared_rmat_seed=None, cores=None):
+def cpu_queries_per_s(tasks, budget_s, cores=None):
     """Queries/s of the oracle over all host cores: queries completed within
     about budget_s seconds of wall time, divided by their oracle time per
     core.  Returns (queries/s, queries done, oracle seconds, cores)."""
@@ -320,7 +316,7 @@ def cpu_queries_per_s(tasks, budget_s, shared_rmat_seed=None, cores=None):
     cores = cores or os.cpu_count() or 1
     ctx = mp.get_context("spawn")
     done, busy = 0, 0.0
-    with ctx.Pool(cores, initializer=_cpu_worker_init, initargs=(shared_rmat_seed,)) as pool:
+    with ctx.Pool(cores) as pool:
         t0 = time.perf_counter()
         for secs in pool.imap_unordered(_cpu_query, tasks):
             done += 1
@@ -653,12 +649,11 @@ def run_batch(args):
     }
     if not args.no_cpu:
         if args.config == "batch":
-            tasks = [(g.n, (SEED + 3) * 1000 + i, s) for i, (g, s) in enumerate(zip(graphs, srcs))]
-            shared = None
+            tasks = [("var", g.n, (SEED + 3) * 1000 + i, s)
+                     for i, (g, s) in enumerate(zip(graphs, srcs))]
         else:
-            tasks = [(None, None, s) for s in srcs]
-            shared = SEED + 3
-        qps, done, busy, cores = cpu_queries_per_s(tasks, args.cpu_budget, shared)
+            tasks = [("rmat", 18, SEED + 3, s) for s in srcs]
+        qps, done, busy, cores = cpu_queries_per_s(tasks, args.cpu_budget)
         line["cpu_baseline"] = {
             "value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
             "sample": f"oracle sequential Round R, one query per core on {cores} spawned "
@@ -761,6 +756,16 @@ def run_serve(args):
                                f"{args.serve_rounds} rounds per server step"},
         "rates": results,
     }
+    if not args.no_cpu:
+        nvar = len(pool) - 2
+        tasks = [("var", pool[w].n, (SEED + 4) * 1000 + w, srcs[i]) if w < nvar
+                 else ("rmat", 20, SEED + 4 + (w - nvar), srcs[i]) for i, w in enumerate(which)]
+        qps, done, busy, cores = cpu_queries_per_s(tasks, args.cpu_budget)
+        line["cpu_baseline"] = {
+            "value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle sequential Round R on the served query mix, one query per core on "
+                      f"{cores} spawned processes, {done} of the {nq} queries ({busy:.1f} s of "
+                      f"oracle time; graph generation excluded)"}
     print(json.dumps(line), flush=True)
     for h in hs:
         P.sssp_destroy(h)

@@ -93,6 +93,7 @@ def test_cpu_baseline_legs():
     g = gg.random_graph(2000, 6, 1, 50, 5)
     gteps, used, secs = bench.cpu_dijkstra_gteps(g, [0, 1, 2], 60.0)
     assert gteps > 0 and used == 3 and secs > 0
-    tasks = [(1500 + 10 * i, 7000 + i, i) for i in range(6)]
+    tasks = [("var", 1500 + 10 * i, 7000 + i, i) for i in range(6)]
+    tasks += [("rmat", 10, 3, s) for s in (0, 1)]
     qps, done, busy, cores = bench.cpu_queries_per_s(tasks, 120.0, cores=2)
-    assert done == 6 and cores == 2 and busy > 0 and qps > 0
+    assert done == 8 and cores == 2 and busy > 0 and qps > 0
