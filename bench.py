@@ -572,6 +572,20 @@ def run_p2p(args):
                    "timing": "wall clock per synchronous call (host API, graph resident)"},
         "clocks": clk,
     }
+    if not args.no_cpu:
+        import oracle
+        done, busy = 0, 0.0
+        for s, t in pairs:                       # the oracle's single-target run, one thread
+            t0 = time.perf_counter()
+            oracle.round_r(g, s, target=t)
+            busy += time.perf_counter() - t0
+            done += 1
+            if busy >= args.cpu_budget:
+                break
+        line["cpu_baseline"] = {
+            "value": done / busy, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle sequential Round R stopped at the target, {done} of the "
+                      f"{len(pairs)} pairs, {busy:.1f} s, one thread"}
     print(json.dumps(line), flush=True)
     P.sssp_destroy(h)
 
