@@ -117,33 +117,49 @@ extern "C" int sssp_solve_noalloc(uint32_t n, const uint64_t* out_off, const uin
     P.page_shift = kPageShift;
 
     // Every call starts from cleared state: the scratch keeps the previous
-    // call's contents.  Hub reduction slots start at (infinity, 0).
-    CK(cudaMemsetAsync(P.L.hubmin, 0xFF, sizeof(u64) * n, st));
-    CK(cudaMemsetAsync(P.L.hubcnt, 0, sizeof(u32) * n, st));
-    k_outw<<<grid, kThreads, 0, st>>>(P.g.out_off, P.g.out_adj, n, outw);
-    if (narrow)   // compact kernels read outWeight with the in-hub flag (in place)
-        k_pack_outw<<<grid, kThreads, 0, st>>>(outw, P.g.in_off, n, kDefaultHub, outw);
-    k_init_records<<<grid, kThreads, 0, st>>>(P.rec, P.recn, P.fround, outw, P.g.in_off, n);
-    k_reset_ctl<<<1, 32, 0, st>>>(P.ctl, 1, n + 2);
-    CK(cudaGetLastError());
-    CK(launch_start(false, narrow, P, 0, 1, 0, st));
-    void* args[] = {&P};
-    CK(cudaLaunchCooperativeKernel(solve_fn(false, narrow), dim3(grid), dim3(kThreads), args,
-                                   solve_smem_bytes(narrow), st));
-    k_finalize<<<grid, kThreads, 0, st>>>(P.rec, P.recn, P.fround, 0, n, vbits, P.ivar,
-                                          reinterpret_cast<u64*>(dist_dev), nullptr, nullptr,
-                                          nullptr);
-    CK(cudaGetLastError());
-    // Status and round count into host stack memory (synchronous copies).
+    // call's contents.  Hub reduction slots start at (infinity, 0).  Once the
+    // first command is enqueued, a failure waits for the stream before it
+    // returns, so no kernel of a failed call still uses the scratch.
+    int rc = SSSP_OK;
+    cudaError_t e = cudaMemsetAsync(P.L.hubmin, 0xFF, sizeof(u64) * n, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.L.hubcnt, 0, sizeof(u32) * n, st);
+    if (e == cudaSuccess) {
+        k_outw<<<grid, kThreads, 0, st>>>(P.g.out_off, P.g.out_adj, n, outw);
+        if (narrow)   // compact kernels read outWeight with the in-hub flag (in place)
+            k_pack_outw<<<grid, kThreads, 0, st>>>(outw, P.g.in_off, n, kDefaultHub, outw);
+        k_init_records<<<grid, kThreads, 0, st>>>(P.rec, P.recn, P.fround, outw, P.g.in_off, n);
+        k_reset_ctl<<<1, 32, 0, st>>>(P.ctl, 1, n + 2);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_start(false, narrow, P, 0, 1, 0, st);
+    if (e == cudaSuccess) {
+        void* args[] = {&P};
+        e = cudaLaunchCooperativeKernel(solve_fn(false, narrow), dim3(grid), dim3(kThreads), args,
+                                        solve_smem_bytes(narrow), st);
+    }
+    if (e == cudaSuccess) {
+        k_finalize<<<grid, kThreads, 0, st>>>(P.rec, P.recn, P.fround, 0, n, vbits, P.ivar,
+                                              reinterpret_cast<u64*>(dist_dev), nullptr, nullptr,
+                                              nullptr);
+        e = cudaGetLastError();
+    }
+    // Status and round count into host stack memory.
     Ctl hc;
     InstVar hv;
-    CK(cudaMemcpyAsync(&hc, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&hv, P.ivar, sizeof(InstVar), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (hc.error & 4u) return SSSP_E_DEVICE_TIMEOUT;
-    if (hc.error & 8u) return SSSP_E_OVERFLOW;   // a weight above max_weight
-    if (hc.error) return SSSP_E_INTERNAL;
-    if (hv.status != kDone) return SSSP_E_ROUND_LIMIT;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&hv, P.ivar, sizeof(InstVar), cudaMemcpyDeviceToHost, st);
+    const cudaError_t es = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = es;
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return SSSP_E_CUDA;
+    }
+    if (hc.error & 4u) rc = SSSP_E_DEVICE_TIMEOUT;
+    else if (hc.error & 8u) rc = SSSP_E_OVERFLOW;   // a weight above max_weight
+    else if (hc.error) rc = SSSP_E_INTERNAL;
+    else if (hv.status != kDone) rc = SSSP_E_ROUND_LIMIT;
+    if (rc != SSSP_OK) return rc;
     if (rounds_out) *rounds_out = hv.rounds;
     return SSSP_OK;
 }

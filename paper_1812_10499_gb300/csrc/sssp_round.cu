@@ -601,7 +601,10 @@ __device__ __forceinline__ void relax_issue(const RoundParams& P,
         const uint2 e = st.adj[as][idx];
         const typename L::RSlot& v = st.dc[ds][idx];
         const u64 dd = odx + e.y;
-        if (L::kNarrow && dd >= kNarrowLimit) {    // cannot happen when n * max w fits
+        // A distance at the layout's limit cannot come from a graph whose
+        // n * max weight fits it (checked when the graph is created); it
+        // means an edge heavier than the declared maximum weight.
+        if (dd >= (L::kNarrow ? kNarrowLimit : P.dinf)) {
             atomicOr(&P.ctl->error, 8u);
             continue;
         }
