@@ -1,27 +1,34 @@
 """Benchmark of the GB300 bound-based SSSP library (Garg, arXiv 1812.10499).
 
-Default workload (one JSON line): R-MAT scale 22, edge factor 16,
-(a, b, c, d) = (.57, .19, .19, .05), duplicates and self-loops removed, w in
-[1, 255]; 8 seeded sources solved one at a time.  One step = the 8 solves.
-Metric: GTEPS = (sum over the step's solves of the out-edges of reachable
-vertices) / time.  `value` is device time with the graph resident; `e2e` is
-the same metric through the host-pointer API (sssp_solve: distances copied
-back to host memory every solve).
+Default run (one JSON line): the headline workload, R-MAT scale 22, edge
+factor 16, (a, b, c, d) = (.57, .19, .19, .05), duplicates and self-loops
+removed, w in [1, 255]; 8 seeded sources solved one at a time.  One step =
+the 8 solves.  Metric: GTEPS = (sum over the step's solves of the out-edges
+of reachable vertices) / time.  `value` is device time with the graph
+resident; `e2e` is the same metric through the host-pointer API (sssp_solve:
+distances copied back to host memory every solve).  The same line carries
+the other halves of the metric as sub-objects:
+  batched  512 independent graphs in one batched launch vs the plain loop
+  msrc     64 sources on one R-MAT scale 18 graph in one launch vs the loop
+  served   Poisson arrivals at 0.25x-4x the plain loop's capacity: served
+           queries/s and p50/p99 latency vs the plain FIFO loop
+each with its results checked against the oracle on a seeded sample and the
+oracle's own throughput on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--config rmat22|random4096|grid|dag|unitgrid|batch|msrc|serve|p2p]
+                  [--headline-only]
 
 Multi-GPU: replicas only (queries are independent); each rank solves the same
 8 sources on its own GPU, `value` sums all ranks' edges over the slowest
-rank's time ("scaling": "weak").
+rank's time ("scaling": "weak"); the batched and served sub-objects are
+measured at one GPU only.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
-import re
-import math
 import os
 import statistics
 import subprocess
@@ -36,6 +43,7 @@ sys.path.insert(0, ROOT)
 
 SEED = 1812_10499
 METRIC = "SSSP GTEPS and % HBM roofline at 1 GB300; batched queries/s and p99 vs plain loop"
+INF = np.uint64(0xFFFFFFFFFFFFFFFF)
 # Per-vertex state layout of the round kernels (SSSP_LAYOUT_*).
 LAYOUTS = {"auto": 0, "wide": 1, "compact": 2}
 # Round rule (SSSP_RULE_* bits): threshold clamp, minD clamp, label-correcting,
@@ -78,41 +86,34 @@ def dist_env():
     return ws, rank, local
 
 
-def rmat22():
-    import graphgen as gg
-    g = gg.rmat(22, 16, 1, 255, SEED + 1)
-    cand = np.flatnonzero(g.out_degree() > 0)
-    idx = gg.uniform(SEED + 1, 7, 8, 0, len(cand) - 1)
-    return g, [int(cand[int(i)]) for i in idx]
-
-
 def workload(name):
     import graphgen as gg
+    from graphgen import workloads as wl
     if name == "rmat22":
-        g, srcs = rmat22()
+        g, srcs = wl.rmat22()
         desc = ("R-MAT scale 22, edge factor 16, a/b/c/d=.57/.19/.19/.05, dedup, no self-loops, "
                 "w U[1,255], 8 seeded sources one at a time")
         return g, srcs, desc
     if name.startswith("rmat") and name[4:].isdigit():
         scale = int(name[4:])
         g = gg.rmat(scale, 16, 1, 255, SEED + 1)
-        cand = np.flatnonzero(g.out_degree() > 0)
-        idx = gg.uniform(SEED + 1, 7, 8, 0, len(cand) - 1)
-        return (g, [int(cand[int(i)]) for i in idx],
+        return (g, wl.rmat_sources(g, SEED + 1, 7, 8),
                 f"R-MAT scale {scale}, edge factor 16, w U[1,255], 8 seeded sources one at a time")
     if name == "random4096":
-        return (gg.random_graph(4096, 8, 1, 100, SEED), [0],
-                "random n=4096, 8 distinct out-edges, w U[1,100], source 0")
+        g, srcs = wl.random4096()
+        return g, srcs, "random n=4096, 8 distinct out-edges, w U[1,100], source 0"
     if name == "grid":
-        return (gg.grid(4096, 4096, 1, 10000, SEED + 2), [0],
-                "grid 4096x4096 4-neighbour bidirectional, w U[1,10000], source corner")
+        g, srcs = wl.grid4096()
+        return g, srcs, "grid 4096x4096 4-neighbour bidirectional, w U[1,10000], source corner"
     if name == "grid1024":
         return (gg.grid(1024, 1024, 1, 10000, SEED + 2), [0],
                 "grid 1024x1024 4-neighbour bidirectional, w U[1,10000], source corner")
     if name == "unitgrid":
-        return gg.grid(4096, 4096, 1, 1, SEED + 2), [0], "grid 4096x4096 all weights 1, corner"
+        g, srcs = wl.unitgrid4096()
+        return g, srcs, "grid 4096x4096 all weights 1, corner"
     if name == "dag":
-        return (gg.dag(1024, 8192, 8, 4, 1, 1000, SEED + 2), [0],
+        g, srcs = wl.dag1024()
+        return (g, srcs,
                 "layered DAG 1024 x 8192, out-degree 8 to layer+U{1..4}, w U[1,1000], source 0")
     raise ValueError(name)
 
@@ -212,21 +213,24 @@ def kernel_source_sha256():
 
 
 def measured_traffic(kernel, config):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary of this
-    workload, or None when there is none or the kernel source has changed
-    since it was captured (the summary records the source's sha256)."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{config}.md")
+    """DRAM bytes per launch of `kernel` on workload `config`, from the
+    machine-readable record of the committed ncu captures
+    (profiles/traffic.json), or None when there is none or the kernel
+    sources have changed since it was captured (each entry records the
+    sources' sha256)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        text = open(path).read()
-    except OSError:
+        with open(path) as f:
+            entries = json.load(f)
+    except (OSError, ValueError):
         return None, None
-    fields = dict(re.findall(r"^(\w+): (\S+)$", text, flags=re.M))
-    sha = kernel_source_sha256()
-    if fields.get("kernel_source_sha256") != sha or "traffic_bytes_per_launch" not in fields:
-        return None, f"profiles/{kernel}_{config}.md is stale (kernel source changed)"
-    return float(fields["traffic_bytes_per_launch"]), (
-        f"profiles/{kernel}_{config}.md: DRAM bytes per launch over one whole solve, "
-        "ncu --cache-control none")
+    e = entries.get(f"{kernel}/{config}")
+    if not e or "traffic_bytes_per_launch" not in e:
+        return None, None
+    if e.get("kernel_source_sha256") != kernel_source_sha256():
+        return None, f"profiles/traffic.json {kernel}/{config} is stale (kernel source changed)"
+    return float(e["traffic_bytes_per_launch"]), (
+        f"profiles/traffic.json {kernel}/{config}: {e.get('how', 'ncu dram__bytes')}")
 
 
 def alg_bytes(info):
@@ -277,35 +281,50 @@ def cpu_dijkstra_gteps(g, sources, budget_s):
         t0 = time.perf_counter()
         d, _ = oracle.dijkstra(g, s)
         t_tot += time.perf_counter() - t0
-        edges += int(deg[d != np.uint64(0xFFFFFFFFFFFFFFFF)].sum())
+        edges += int(deg[d != INF].sum())
         used += 1
         if t_tot >= budget_s:
             break
     return edges / t_tot / 1e9, used, t_tot
 
 
-# CPU baseline of the batched workloads: the oracle's Round R, one query per
-# host core.  Workers are spawned (the parent has a CUDA context) and build
-# their graphs from the seeds, so no graph is pickled.  A task is
-# ("var", n, seed, source) for a graph of the batched distribution or
-# ("rmat", scale, seed, source); R-MAT graphs are kept per worker.
+# Oracle runs of independent queries, one per host core.  Workers are
+# spawned (the parent has a CUDA context) and build their graphs from the
+# seeds, so no graph is pickled.  A task is ("var", n, seed, source) for a
+# graph of the batched distribution (out-degree U{4..16}, w in [1, 1000],
+# generator seed `seed`) or ("rmat", scale, seed, source) for an R-MAT graph
+# (edge factor 16, w in [1, 255]); R-MAT graphs are kept per worker.
 _CPU_RMAT = {}
+
+
+def _cpu_graph(kind, size, gseed):
+    import graphgen as gg
+    if kind == "var":
+        return gg.random_var_graph(size, 4, 16, 1, 1000, gseed)
+    g = _CPU_RMAT.get((size, gseed))
+    if g is None:
+        g = _CPU_RMAT[(size, gseed)] = gg.rmat(size, 16, 1, 255, gseed)
+    return g
 
 
 def _cpu_query(task):
     """One query on the oracle; returns its seconds (generation excluded)."""
-    import graphgen as gg
     import oracle
     kind, size, gseed, s = task
-    if kind == "var":
-        g = gg.random_var_graph(size, 4, 16, 1, 1000, gseed)
-    else:
-        g = _CPU_RMAT.get((size, gseed))
-        if g is None:
-            g = _CPU_RMAT[(size, gseed)] = gg.rmat(size, 16, 1, 255, gseed)
+    g = _cpu_graph(kind, size, gseed)
     t0 = time.perf_counter()
     oracle.round_r(g, s)
     return time.perf_counter() - t0
+
+
+def _cpu_query_result(task):
+    """One query on the oracle: (seconds, distances, rounds)."""
+    import oracle
+    kind, size, gseed, s = task
+    g = _cpu_graph(kind, size, gseed)
+    t0 = time.perf_counter()
+    r = oracle.round_r(g, s)
+    return time.perf_counter() - t0, r.dist, r.rounds
 
 
 def cpu_queries_per_s(tasks, budget_s, cores=None):
@@ -327,11 +346,30 @@ def cpu_queries_per_s(tasks, budget_s, cores=None):
     return done * cores / busy, done, busy, cores
 
 
+def oracle_sample(tasks, cores=None):
+    """The oracle on every task, one per host core: ([(seconds, distances,
+    rounds)] in task order, cores)."""
+    import multiprocessing as mp
+    cores = min(len(tasks), cores or os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        return pool.map(_cpu_query_result, tasks, chunksize=1), cores
+
+
+def sample_indices(count, seed_stream, k):
+    """k distinct seeded indices in [0, count)."""
+    import graphgen as gg
+    if k >= count:
+        return list(range(count))
+    u = gg.unit(SEED + 9, seed_stream, count)
+    return sorted(int(i) for i in np.argsort(u)[:k])
+
+
 # ------------------------------------------------------------ our arm
 
 def run_ours(args):
     import torch
     import paper_1812_10499_gb300 as P
+    from graphgen import workloads as wl
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -340,6 +378,8 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     P.load()
+    # Tunings go to a cache of this run only (the sweep runs every time).
+    P.sssp_tune_cache_open(None)
     t0 = time.time()
     g, sources, desc = workload(args.config)
     log(f"[rank {rank}] workload {args.config}: n={g.n} m={g.m} gen {time.time() - t0:.1f}s")
@@ -355,19 +395,55 @@ def run_ours(args):
     h = P.sssp_create(g.n, g.row_ptr, g.col, g.w, options=opt)
     layout = {P.SSSP_LAYOUT_WIDE: "wide 32 B records",
               P.SSSP_LAYOUT_COMPACT: "compact 16 B records"}[P.sssp_layout(h)]
-    # Edges of the reachable vertices, each counted once (the label-correcting
-    # rule scans some of them more than once).
-    outs = [P.sssp_solve_ex(h, s) for s in sources]
-    infos = [o["info"] for o in outs]
-    deg = g.out_degree()
-    m_reach = sum(int(deg[o["dist"] != np.uint64(0xFFFFFFFFFFFFFFFF)].sum()) for o in outs)
-    rounds = [i["rounds"] for i in infos]
     stream = torch.cuda.Stream()
     dd = torch.empty(g.n, dtype=torch.int64, device="cuda")
 
     def step():
         for s in sources:
             P.sssp_solve_device(h, s, dd, stream=stream)
+
+    def timed_steps(k):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    tuning = None
+    if not args.no_tune:
+        # The autotuner picks the launch shape on sources other than the
+        # timed ones; the library's default shape is timed on the step first.
+        for _ in range(args.warmup):
+            step()
+        default_t = P.sssp_get_tuning(h)
+        ms_default = timed_steps(max(1, min(args.steps, 10)))
+        tsrc = wl.rmat_sources(g, SEED + 8, 1, args.tune_sources) if g.m else [sources[0]]
+        t0 = time.perf_counter()
+        res = P.sssp_autotune(h, tsrc, reps=args.tune_reps)
+        tune_s = time.perf_counter() - t0
+        for _ in range(args.warmup):
+            step()
+        ms_tuned = timed_steps(max(1, min(args.steps, 10)))
+        tuning = {"class_key": P.sssp_graph_key(h), "default": default_t, "chosen": res["best"],
+                  "sweep": {"sources": tsrc, "evaluated": res["evaluated"],
+                            "start_ms": res["start_ms"], "best_ms": res["best_ms"],
+                            "seconds": tune_s},
+                  "step_ms_default": ms_default, "step_ms_tuned": ms_tuned,
+                  "gain": ms_default / ms_tuned,
+                  "what": "sssp_autotune: coordinate descent over hub degree x chunk size, "
+                          "cluster-tail work items, CTAs per SM; device time of passes over "
+                          "the sweep's sources (not the timed ones); the step is timed with "
+                          "the default and the chosen tuning"}
+    # Edges of the reachable vertices, each counted once (the label-correcting
+    # rule scans some of them more than once).
+    outs = [P.sssp_solve_ex(h, s) for s in sources]
+    infos = [o["info"] for o in outs]
+    deg = g.out_degree()
+    m_reach = sum(int(deg[o["dist"] != INF].sum()) for o in outs)
+    rounds = [i["rounds"] for i in infos]
 
     for _ in range(args.warmup):
         step()
@@ -390,22 +466,24 @@ def run_ours(args):
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
+    ms_local = ms
     ms, edges = reduce_over_ranks(dist, "cuda", ms, args.steps * m_reach)
     value = edges / (ms * 1e-3) / 1e9
     # Kernels launched per solve, counted by the library (start, round kernels
     # including the cluster tail kernel of every device-loop iteration, output).
     launches = args.steps * sum(i["kernel_launches"] for i in infos)
 
-    # ---- dominant kernel: launch durations with CUDA events on the solve stream
+    # ---- roofline: every kernel's launches timed with CUDA events on the
+    # solve stream, in the schedule of the timed solves (the device loop's
+    # iterations launched from the host), work counters split by kernel
     relax_b, cup_b = 0, 0
     for i in infos:
         rb, cb = alg_bytes(i)
         relax_b += rb
         cup_b += cb
+    step_bytes = relax_b + cup_b                      # one step = the 8 solves
     reps = max(1, min(args.steps, 5))
     peak, peak_kind = peaks()
-    # Phase split (device trace of the persistent kernel, or events around
-    # host-launched kernels in the other loop modes).
     P.sssp_profile(h, True)
     for _ in range(reps):
         for s in sources:
@@ -413,10 +491,26 @@ def run_ours(args):
     prof = P.sssp_profile(h, False)
     P.sssp_profile(h, True)
     P.sssp_solve_ex(h, sources[0], dist=False, stream=stream)
-    per_round = P.sssp_profile_rounds(h)
+    per_iter = P.sssp_profile_rounds(h)
     P.sssp_profile(h, False)
-    cup_gbs = cup_b * reps / (prof["cupdate_ms"] * 1e-3) / 1e9
-    relax_gbs = relax_b * reps / (prof["relax_ms"] * 1e-3) / 1e9
+    gc, tc = prof["grid_counters"], prof["tail_counters"]
+    kern = {
+        "k_cupdate": (B_IN_EDGE * gc["in_scanned"] + B_ACTIVE * gc["active_visits"],
+                      prof["cupdate_ms"], prof["cupdate_launches"]),
+        "k_relax": (B_OUT_EDGE * gc["out_scanned"] + B_FRONT * gc["front_visits"],
+                    prof["relax_ms"], prof["relax_launches"]),
+        "k_tail": (alg_bytes(tc)[0] + alg_bytes(tc)[1], prof["tail_ms"], prof["tail_launches"]),
+    }
+    kernels = {}
+    for k, (b, t_ms, n) in kern.items():
+        if n == 0 or t_ms <= 0:
+            continue
+        kernels[k] = {"launches": n, "ms": t_ms, "bytes": b,
+                      "achieved_gbs": b / (t_ms * 1e-3) / 1e9,
+                      "frac": b / (t_ms * 1e-3) / 1e9 / peak, "share": 0.0}
+    tot_ms = sum(v["ms"] for v in kernels.values())
+    for v in kernels.values():
+        v["share"] = v["ms"] / tot_ms
     if args.loop == "persistent":
         # One launch of k_solve per solve: events around each solve call.
         pairs = []
@@ -431,17 +525,22 @@ def run_ours(args):
         stream.synchronize()
         kernel = "k_solve"
         ms_per_launch = statistics.fmean(a.elapsed_time(b) for a, b in pairs)
-        bytes_per_launch = (relax_b + cup_b) / len(sources)
+        bytes_per_launch = step_bytes / len(sources)
         timing = ("CUDA events on the solve stream around each solve (one k_solve launch plus "
-                  "four small start/output kernels); phase split from the kernel's globaltimer "
-                  "trace")
+                  "four small start/output kernels)")
     else:
-        kernel = "k_cupdate"
-        ms_per_launch = prof["cupdate_ms"] / max(1, prof["cupdate_launches"])
-        bytes_per_launch = cup_b * reps / max(1, prof["cupdate_launches"])
-        timing = "CUDA events around every launch on the solve stream, host-launched rounds"
+        kernel = max(kernels, key=lambda k: kernels[k]["ms"])      # the dominant kernel
+        b, t_ms, n = kern[kernel]
+        ms_per_launch = t_ms / n
+        bytes_per_launch = b / n
+        timing = ("CUDA events around every launch on the solve stream; the host launches the "
+                  "device loop's iterations (k_relax, k_cupdate, cluster tail kernel k_tail) as "
+                  "the timed solves run them; algorithmic bytes from the work counters of the "
+                  "rounds each kernel ran")
     dom_gbs = bytes_per_launch / (ms_per_launch * 1e-3) / 1e9
     traffic, traffic_src = measured_traffic(kernel, args.config)
+    # Whole step: all algorithmic bytes of the 8 solves over the timed step.
+    step_gbs = step_bytes / (ms_local / args.steps * 1e-3) / 1e9
 
     # ---- end to end through the public host API (dist copied to host)
     e2e_steps = max(1, min(args.steps, 10))
@@ -456,6 +555,7 @@ def run_ours(args):
     t_e2e = time.perf_counter() - t0
     ms_e2e, edges_e2e = reduce_over_ranks(dist, "cuda", t_e2e * 1e3, e2e_steps * m_reach)
     e2e = edges_e2e / (ms_e2e * 1e-3) / 1e9
+    P.sssp_destroy(h)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -482,19 +582,28 @@ def run_ours(args):
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": dom_gbs / peak,
                      "traffic": traffic, "traffic_source": traffic_src,
                      "bytes_per_launch": bytes_per_launch,
-                     "ms_per_launch": ms_per_launch,
-                     "cupdate_phase_achieved": cup_gbs, "relax_phase_achieved": relax_gbs,
-                     "timing": timing,
-                     "per_round_ms_first_source": {
-                         "relax": [round(float(x), 4) for x in per_round[0]],
-                         "cupdate": [round(float(x), 4) for x in per_round[1]]}},
+                     "ms_per_launch": ms_per_launch, "timing": timing,
+                     "kernels": kernels,
+                     "step": {"bytes": step_bytes, "ms": ms_local / args.steps,
+                              "achieved": step_gbs, "frac": step_gbs / peak,
+                              "what": "algorithmic bytes of all kernels of the 8 solves over "
+                                      "the timed step (device loop, no profiling)"},
+                     "per_iteration_first_source": {
+                         "relax_ms": [round(float(x), 4) for x in per_iter[0]],
+                         "cupdate_ms": [round(float(x), 4) for x in per_iter[1]],
+                         "tail_ms": [round(float(x), 4) for x in per_iter[2]],
+                         "tail_rounds": [int(x) for x in per_iter[3]]}},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(sources),
                 "d2h_bytes_per_step": 8 * g.n * len(sources)},
         "gpu_launches": launches,
         "clocks": clk,
+        "tuning": tuning,
     }
-    P.sssp_destroy(h)
+    if args.config == "rmat22" and ws == 1 and not args.headline_only:
+        line["batched"] = batched_metrics(args, "batch")
+        line["msrc"] = batched_metrics(args, "msrc")
+        line["served"] = served_metrics(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -503,16 +612,259 @@ def run_ours(args):
 
 # ------------------------------------------------- batched / served queries
 
-def batch_graphs(count, seed, nmin=1024, nmax=262144):
-    """Independent graphs: n log-uniform in [nmin, nmax], out-degree U{4..16},
-    w ~ U[1,1000], one seeded source each."""
-    import graphgen as gg
-    u = gg.unit(seed, 1, count)
-    ns = np.round(np.exp(np.log(nmin) + u * (np.log(nmax) - np.log(nmin)))).astype(int)
-    graphs = [gg.random_var_graph(int(n), 4, 16, 1, 1000, seed * 1000 + i)
-              for i, n in enumerate(ns)]
-    srcs = [int(gg.uniform(seed, 2 + i, 1, 0, g.n - 1)[0]) for i, g in enumerate(graphs)]
-    return graphs, srcs
+def batched_metrics(args, kind):
+    """Queries/s of one lock-step batched launch against the plain loop of one
+    sssp_solve_device per query (same queries, same stream), with the results
+    of the two compared query by query, a seeded sample compared with the
+    oracle, and the oracle's queries/s on the host cores."""
+    import torch
+    import paper_1812_10499_gb300 as P
+    from graphgen import workloads as wl
+    P.load()
+    t0 = time.time()
+    if kind == "batch":
+        seed = SEED + 3
+        ns = wl.batch_sizes(args.batch_count, seed)
+        graphs = [wl.batch_graph(n, seed, i) for i, n in enumerate(ns)]
+        srcs = [wl.batch_source(seed, i, g.n) for i, g in enumerate(graphs)]
+        hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w) for g in graphs]
+        desc = (f"{len(graphs)} independent graphs, n log-uniform in [1K, 256K], out-degree "
+                f"U{{4..16}}, w U[1,1000], one seeded source each")
+        tasks = [("var", g.n, seed * 1000 + i, s) for i, (g, s) in enumerate(zip(graphs, srcs))]
+        m_total = sum(g.m for g in graphs)
+        nsample = 96
+    else:
+        g, srcs = wl.msrc_rmat18()
+        h = P.sssp_create(g.n, g.row_ptr, g.col, g.w)
+        hs = [h] * len(srcs)
+        graphs = [g] * len(srcs)
+        desc = "64 seeded sources on one R-MAT scale 18 graph (edge factor 16, w U[1,255])"
+        tasks = [("rmat", 18, SEED + 3, s) for s in srcs]
+        m_total = g.m
+        nsample = 64
+    ns = [gr.n for gr in graphs]
+    log(f"{kind} workload: {len(hs)} queries, {sum(ns)} vertices, setup {time.time() - t0:.1f}s")
+    outs_a = [torch.empty(n, dtype=torch.int64, device="cuda") for n in ns]
+    outs_b = [torch.empty(n, dtype=torch.int64, device="cuda") for n in ns]
+    st = torch.cuda.Stream()
+
+    def plain():
+        for hh, s, o in zip(hs, srcs, outs_a):
+            P.sssp_solve_device(hh, s, o, stream=st)
+
+    def batched():
+        return P.sssp_solve_batch_device(hs, srcs, outs_b, stream=st)
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        plain()
+        rounds_b = batched()
+    st.synchronize()
+    tuning = None
+    if not args.no_tune:
+        # The batch with the first graph's tuning, then the autotuner's pick
+        # (cached under the batch's class, where the batched call finds it).
+        steps_t = max(1, min(args.steps, 5))
+        ms0 = timed(batched, steps_t)
+        t0 = time.perf_counter()
+        res = P.sssp_autotune_batch(hs, srcs, reps=2)
+        tune_s = time.perf_counter() - t0
+        for _ in range(args.warmup):
+            rounds_b = batched()
+        ms1 = timed(batched, steps_t)
+        tuning = {"class_key": P.sssp_batch_key(hs), "chosen": res["best"],
+                  "sweep": {"evaluated": res["evaluated"], "start_ms": res["start_ms"],
+                            "best_ms": res["best_ms"], "seconds": tune_s},
+                  "batch_ms_default": ms0, "batch_ms_tuned": ms1, "gain": ms0 / ms1,
+                  "what": "sssp_autotune_batch on the whole batch (the timed queries)"}
+    same_plain = all(torch.equal(a, b) for a, b in zip(outs_a, outs_b))
+
+    steps = max(1, min(args.steps, 10))
+    clocks = Clocks(0)
+    clocks.start()
+    ms_b = timed(batched, steps)
+    ms_p = timed(plain, steps)
+    clk = clocks.stop()
+    q = len(hs) * steps
+    # Results: a seeded sample against the oracle (which also times it).
+    idx = sample_indices(len(tasks), 1 if kind == "batch" else 2, nsample)
+    res, cores = oracle_sample([tasks[i] for i in idx])
+    same_oracle = all(
+        np.array_equal(outs_b[i].cpu().numpy().view(np.uint64), d) and int(rounds_b[i]) == r
+        for i, (_, d, r) in zip(idx, res))
+    busy = sum(t for t, _, _ in res)
+    out = {
+        "metric": "batched SSSP queries/s vs the plain per-query loop",
+        "value": q / (ms_b * 1e-3), "unit": "queries/s", "plain_value": q / (ms_p * 1e-3),
+        "speedup": ms_p / ms_b, "identical_results": bool(same_plain and same_oracle),
+        "identical_to_plain": bool(same_plain), "identical_to_oracle_sample": bool(same_oracle),
+        "oracle_sample": len(idx), "steps": steps, "ms_per_step": ms_b / steps,
+        "plain_ms_per_step": ms_p / steps, "higher_is_better": True, "dtype": "u64",
+        "timing": "CUDA events on one stream around `steps` repetitions of the whole batch "
+                  "(one batched call) and of the plain loop (one solve per query)",
+        "config": {"workload": desc, "queries": len(hs), "vertices": int(sum(ns)),
+                   "edges": int(m_total), "l2": "inputs larger than L2"},
+        "clocks": clk,
+        "tuning": tuning,
+        "cpu_baseline": {
+            "value": len(idx) * cores / busy, "unit": "queries/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"oracle sequential Round R on {len(idx)} seeded queries of the "
+                      f"{len(tasks)}, one query per core on {cores} spawned processes "
+                      f"({busy:.1f} s of oracle time; graph generation excluded)"},
+    }
+    for hh in set(hs):
+        P.sssp_destroy(hh)
+    return out
+
+
+def served_metrics(args):
+    """Continuous batching under Poisson arrivals.  Queries on graphs of the
+    batched distribution plus 10% on R-MAT scale 20 graphs; the server admits
+    them into free slots as memory allows while others run, its own thread
+    runs the device steps, and it records each query's completion time.  For
+    each arrival rate (multiples of the plain loop's measured capacity) it
+    reports queries/s and p50/p99 latency (completion minus scheduled
+    arrival, on the host's monotonic clock) for the server and for the plain
+    FIFO loop of one solve at a time, over the measured queries (after the
+    warm-up queries of the same stream)."""
+    import torch
+    import paper_1812_10499_gb300 as P
+    from graphgen import workloads as wl
+    P.load()
+    torch.cuda.set_device(0)
+    pool = wl.serve_pool(args.serve_pool)
+    hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w) for g in pool]
+    warm, meas = args.serve_warm, args.serve_queries
+    nq = warm + meas
+    which, srcs = wl.serve_queries(pool, nq)
+    nvar = len(pool) - 2
+    st = torch.cuda.Stream()
+    dd = torch.empty(max(g.n for g in pool), dtype=torch.int64, device="cuda")
+    # plain capacity: one solve at a time, the first `warm` queries timed
+    for i in range(min(nq, 20)):
+        P.sssp_solve_device(hs[which[i]], srcs[i], dd, stream=st)
+    st.synchronize()
+    t0 = time.perf_counter()
+    ncap = min(nq, max(200, warm))
+    for i in range(ncap):
+        P.sssp_solve_device(hs[which[i]], srcs[i], dd, stream=st)
+    st.synchronize()
+    service = (time.perf_counter() - t0) / ncap
+    capacity = 1.0 / service
+    # Seeded sample of measured queries checked against the oracle at every rate.
+    sidx = [warm + i for i in sample_indices(meas, 3, 64)]
+    tasks = [("var", pool[which[i]].n, (SEED + 4) * 1000 + which[i], srcs[i])
+             if which[i] < nvar else ("rmat", 20, SEED + 4 + (which[i] - nvar), srcs[i])
+             for i in sidx]
+    res, cores = oracle_sample(tasks)
+    ref = {i: (d, r) for i, (_, d, r) in zip(sidx, res)}
+    busy = sum(t for t, _, _ in res)
+    rates = []
+    clocks = Clocks(0)
+    clocks.start()
+    for mult in args.serve_rates:
+        lam = mult * capacity
+        arrive = wl.arrivals(nq, lam, 4 + int(mult * 100))
+        # plain FIFO loop
+        lat_p = []
+        t_start_p = time.monotonic_ns()
+        for i in range(nq):
+            target = t_start_p + int(arrive[i] * 1e9)
+            while time.monotonic_ns() < target:
+                pass
+            P.sssp_solve_device(hs[which[i]], srcs[i], dd, stream=st)
+            st.synchronize()
+            lat_p.append((time.monotonic_ns() - target) * 1e-9)
+        t_end_p = time.monotonic_ns()
+        # served: submissions at the arrival times, completions recorded by
+        # the server; results collected whenever the submitter is idle
+        server = P.sssp_serve_open(budget_bytes=32 << 30, max_slots=1024,
+                                   rounds_per_step=args.serve_rounds)
+        outs, tickets, infos = {}, {}, {}
+        same = True
+        t_start = time.monotonic_ns()
+
+        def collect(i, timeout_ms):
+            nonlocal same
+            stt, info = P.sssp_serve_wait(server, tickets[i], timeout_ms)
+            if stt != P.SSSP_OK:
+                return False
+            infos[i] = info
+            if i in ref:
+                same = same and np.array_equal(outs[i], ref[i][0]) and info["rounds"] == ref[i][1]
+            del outs[i], tickets[i]
+            return True
+
+        pending = []
+        for i in range(nq):
+            target = t_start + int(arrive[i] * 1e9)
+            while time.monotonic_ns() < target:
+                if pending and collect(pending[0], 0):
+                    pending.pop(0)
+            outs[i] = np.empty(pool[which[i]].n, dtype=np.uint64)
+            tickets[i] = P.sssp_serve_submit(server, hs[which[i]], srcs[i], outs[i])
+            pending.append(i)
+        for i in pending:
+            assert collect(i, 600_000), "served query did not complete"
+        stats = P.sssp_serve_stats_get(server)
+        P.sssp_serve_close(server)
+        lat_s = [(infos[i]["done_ns"] - (t_start + int(arrive[i] * 1e9))) * 1e-9
+                 for i in range(warm, nq)]
+        span_s = (max(infos[i]["done_ns"] for i in range(warm, nq))
+                  - (t_start + int(arrive[warm] * 1e9))) * 1e-9
+        span_p = (t_end_p - (t_start_p + int(arrive[warm] * 1e9))) * 1e-9
+        rates.append({
+            "rate_x_capacity": mult, "arrival_qps": lam,
+            "served_qps": meas / span_s,
+            "served_p50_ms": 1e3 * float(np.percentile(lat_s, 50)),
+            "served_p99_ms": 1e3 * float(np.percentile(lat_s, 99)),
+            "plain_qps": meas / max(span_p, 1e-9),
+            "plain_p50_ms": 1e3 * float(np.percentile(lat_p[warm:], 50)),
+            "plain_p99_ms": 1e3 * float(np.percentile(lat_p[warm:], 99)),
+            "identical_to_oracle_sample": bool(same),
+            "server_steps": stats["steps"], "server_max_inflight": stats["max_inflight"]})
+    clk = clocks.stop()
+    head = min(rates, key=lambda r: abs(r["rate_x_capacity"] - 2.0))
+    out = {
+        "metric": "served SSSP queries/s and p50/p99 latency vs the plain loop",
+        "value": head["served_qps"], "unit": "queries/s",
+        "p50_ms": head["served_p50_ms"], "p99_ms": head["served_p99_ms"],
+        "plain_value": head["plain_qps"], "plain_p50_ms": head["plain_p50_ms"],
+        "plain_p99_ms": head["plain_p99_ms"], "at_rate_x_capacity": head["rate_x_capacity"],
+        "plain_capacity_qps": capacity, "higher_is_better": True, "dtype": "u64",
+        "identical_results": all(r["identical_to_oracle_sample"] for r in rates),
+        "oracle_sample": len(sidx),
+        "data": "synthetic (seeded generator), Poisson arrivals",
+        "config": {"workload": f"{warm} warm-up + {meas} measured queries per rate: 90% on "
+                               f"{nvar} graphs of the batched distribution, 10% on 2 R-MAT "
+                               f"scale 20 graphs; 32 GiB budget, 1024 slots, "
+                               f"{args.serve_rounds} rounds per server step, server thread",
+                   "timing": "latency = completion (recorded by the server, or the plain "
+                             "loop's synchronise) minus the scheduled arrival, host "
+                             "monotonic clock; queries/s = measured queries over the span "
+                             "from the first measured arrival to the last completion"},
+        "rates": rates,
+        "clocks": clk,
+        "cpu_baseline": {
+            "value": len(sidx) * cores / busy, "unit": "queries/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"oracle sequential Round R on {len(sidx)} seeded queries of the served "
+                      f"mix, one query per core on {cores} spawned processes ({busy:.1f} s "
+                      f"of oracle time; graph generation excluded)"},
+    }
+    for h in hs:
+        P.sssp_destroy(h)
+    return out
 
 
 def run_p2p(args):
@@ -531,7 +883,7 @@ def run_p2p(args):
     pairs, ref = [], {}
     for k, s in enumerate(sources):
         d, _ = P.sssp_solve(h, s)
-        reach = np.flatnonzero(d != np.uint64(0xFFFFFFFFFFFFFFFF))
+        reach = np.flatnonzero(d != INF)
         for i in gg.uniform(SEED + 5, k, 8, 0, len(reach) - 1):
             t = int(reach[int(i)])
             pairs.append((s, t))
@@ -590,199 +942,13 @@ def run_p2p(args):
     P.sssp_destroy(h)
 
 
-def run_batch(args):
-    """Queries/s of one lock-step batched launch against the plain loop of
-    one sssp_solve_device per query, same queries, results compared."""
+def run_extra(args):
+    """--config batch | msrc | serve: one sub-object as a line of its own."""
     import torch
-    import graphgen as gg
-    import paper_1812_10499_gb300 as P
-    P.load()
     torch.cuda.set_device(0)
-    t0 = time.time()
-    if args.config == "batch":
-        graphs, srcs = batch_graphs(args.batch_count, SEED + 3)
-        hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w) for g in graphs]
-        ns = [g.n for g in graphs]
-        desc = (f"{len(graphs)} independent graphs, n log-uniform in [1K, 256K], out-degree "
-                f"U{{4..16}}, w U[1,1000], one seeded source each")
-        m_total = sum(g.m for g in graphs)
-    else:
-        g = gg.rmat(18, 16, 1, 255, SEED + 3)
-        cand = np.flatnonzero(g.out_degree() > 0)
-        srcs = [int(cand[int(i)]) for i in gg.uniform(SEED + 3, 9, 64, 0, len(cand) - 1)]
-        h = P.sssp_create(g.n, g.row_ptr, g.col, g.w)
-        hs = [h] * len(srcs)
-        ns = [g.n] * len(srcs)
-        graphs = [g]
-        desc = "64 seeded sources on one R-MAT scale 18 graph (edge factor 16, w U[1,255])"
-        m_total = g.m
-    log(f"batch workload: {len(hs)} queries, {sum(ns)} vertices, setup {time.time() - t0:.1f}s")
-    outs_a = [torch.empty(n, dtype=torch.int64, device="cuda") for n in ns]
-    outs_b = [torch.empty(n, dtype=torch.int64, device="cuda") for n in ns]
-    st = torch.cuda.Stream()
-
-    def plain():
-        for h, s, o in zip(hs, srcs, outs_a):
-            P.sssp_solve_device(h, s, o, stream=st)
-
-    def batched():
-        return P.sssp_solve_batch_device(hs, srcs, outs_b, stream=st)
-
-    for _ in range(args.warmup):
-        plain()
-        batched()
-    st.synchronize()
-    same = all(torch.equal(a, b) for a, b in zip(outs_a, outs_b))
-
-    def timed(fn):
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(args.steps):
-            fn()
-        e1.record(st)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1)
-
-    clocks = Clocks(0)
-    clocks.start()
-    ms_b = timed(batched)
-    ms_p = timed(plain)
-    clk = clocks.stop()
-    q = len(hs) * args.steps
-    line = {
-        "metric": "batched SSSP queries/s vs the plain per-query loop", "value": q / (ms_b * 1e-3),
-        "unit": "queries/s", "plain_value": q / (ms_p * 1e-3), "speedup": ms_p / ms_b,
-        "identical_results": bool(same), "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_b / args.steps,
-        "plain_ms_per_step": ms_p / args.steps, "higher_is_better": True, "dtype": "u64",
-        "data": "synthetic (seeded generator)",
-        "config": {"workload": desc, "queries": len(hs), "vertices": int(sum(ns)),
-                   "edges": int(m_total)},
-        "clocks": clk,
-    }
-    if not args.no_cpu:
-        if args.config == "batch":
-            tasks = [("var", g.n, (SEED + 3) * 1000 + i, s)
-                     for i, (g, s) in enumerate(zip(graphs, srcs))]
-        else:
-            tasks = [("rmat", 18, SEED + 3, s) for s in srcs]
-        qps, done, busy, cores = cpu_queries_per_s(tasks, args.cpu_budget)
-        line["cpu_baseline"] = {
-            "value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
-            "sample": f"oracle sequential Round R, one query per core on {cores} spawned "
-                      f"processes, {done} of the {len(tasks)} queries ({busy:.1f} s of oracle "
-                      f"time; graph generation excluded)"}
-    print(json.dumps(line), flush=True)
-    for h in set(hs):
-        P.sssp_destroy(h)
-
-
-def run_serve(args):
-    """Continuous batching under Poisson arrivals.  Queries on graphs of the
-    batched distribution plus 10% on R-MAT scale 20 graphs; the server admits
-    them into free slots as memory allows while others run.  For each arrival
-    rate (multiples of the plain loop's measured capacity) it reports
-    queries/s and p50/p99 latency (completion minus scheduled arrival) for the
-    server and for the plain FIFO loop of one solve at a time."""
-    import torch
-    import graphgen as gg
-    import paper_1812_10499_gb300 as P
-    P.load()
-    torch.cuda.set_device(0)
-    pool, _ = batch_graphs(args.serve_pool, SEED + 4)
-    pool += [gg.rmat(20, 16, 1, 255, SEED + 4 + i) for i in range(2)]
-    hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w) for g in pool]
-    nq = args.serve_queries
-    pick = gg.unit(SEED + 4, 3, nq)
-    which = [len(pool) - 1 - int(p * 20) % 2 if p < 0.1 else int(p * 1e6) % (len(pool) - 2)
-             for p in pick]
-    srcs = [int(gg.uniform(SEED + 4, 10 + i, 1, 0, pool[w].n - 1)[0]) for i, w in enumerate(which)]
-    outs = [np.empty(pool[w].n, dtype=np.uint64) for w in which]
-    st = torch.cuda.Stream()
-    dd = torch.empty(max(g.n for g in pool), dtype=torch.int64, device="cuda")
-    # plain capacity: one solve at a time
-    for i in range(min(nq, 20)):
-        P.sssp_solve_device(hs[which[i]], srcs[i], dd, stream=st)
-    st.synchronize()
-    t0 = time.perf_counter()
-    for i in range(nq):
-        P.sssp_solve_device(hs[which[i]], srcs[i], dd, stream=st)
-    st.synchronize()
-    service = (time.perf_counter() - t0) / nq
-    capacity = 1.0 / service
-    results = []
-    for mult in args.serve_rates:
-        lam = mult * capacity
-        gaps = -np.log(1.0 - gg.unit(SEED + 4, 4 + int(mult * 100), nq)) / lam
-        arrive = np.cumsum(gaps)
-        # plain FIFO loop
-        lat_p = []
-        t_start = time.perf_counter()
-        for i in range(nq):
-            while time.perf_counter() - t_start < arrive[i]:
-                pass
-            P.sssp_solve_device(hs[which[i]], srcs[i], dd, stream=st)
-            st.synchronize()
-            lat_p.append(time.perf_counter() - t_start - arrive[i])
-        span_p = time.perf_counter() - t_start
-        # served
-        server = P.sssp_serve_open(budget_bytes=32 << 30, max_slots=1024,
-                                   rounds_per_step=args.serve_rounds)
-        lat_s = [None] * nq
-        tickets = {}
-        nxt = 0
-        t_start = time.perf_counter()
-        while nxt < nq or tickets:
-            now = time.perf_counter() - t_start
-            while nxt < nq and arrive[nxt] <= now:
-                tickets[nxt] = P.sssp_serve_submit(server, hs[which[nxt]], srcs[nxt], outs[nxt])
-                nxt += 1
-            if not tickets:
-                continue
-            for i in sorted(tickets):
-                stt, _ = P.sssp_serve_poll(server, tickets[i])
-                if stt == P.SSSP_OK:
-                    lat_s[i] = time.perf_counter() - t_start - arrive[i]
-                    del tickets[i]
-                else:
-                    break
-        span_s = time.perf_counter() - t_start
-        P.sssp_serve_close(server)
-        ok = True
-        for i in range(0, nq, max(1, nq // 16)):
-            ref, _ = P.sssp_solve(hs[which[i]], srcs[i])
-            ok = ok and np.array_equal(ref, outs[i])
-        results.append({
-            "rate_x_capacity": mult, "arrival_qps": lam,
-            "served_qps": nq / span_s, "served_p50_ms": 1e3 * float(np.percentile(lat_s, 50)),
-            "served_p99_ms": 1e3 * float(np.percentile(lat_s, 99)),
-            "plain_qps": nq / span_p, "plain_p50_ms": 1e3 * float(np.percentile(lat_p, 50)),
-            "plain_p99_ms": 1e3 * float(np.percentile(lat_p, 99)), "results_match_alone": ok})
-    best = max(results, key=lambda r: r["served_qps"])
-    line = {
-        "metric": "served SSSP queries/s and p50/p99 latency vs the plain loop",
-        "value": best["served_qps"], "unit": "queries/s", "n_gpus": 1,
-        "plain_capacity_qps": capacity, "higher_is_better": True, "dtype": "u64",
-        "data": "synthetic (seeded generator), Poisson arrivals",
-        "config": {"workload": f"{nq} queries: 90% on {len(pool) - 2} graphs of the batched "
-                               f"distribution, 10% on 2 R-MAT scale 20 graphs; 32 GiB budget, "
-                               f"{args.serve_rounds} rounds per server step"},
-        "rates": results,
-    }
-    if not args.no_cpu:
-        nvar = len(pool) - 2
-        tasks = [("var", pool[w].n, (SEED + 4) * 1000 + w, srcs[i]) if w < nvar
-                 else ("rmat", 20, SEED + 4 + (w - nvar), srcs[i]) for i, w in enumerate(which)]
-        qps, done, busy, cores = cpu_queries_per_s(tasks, args.cpu_budget)
-        line["cpu_baseline"] = {
-            "value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
-            "sample": f"oracle sequential Round R on the served query mix, one query per core on "
-                      f"{cores} spawned processes, {done} of the {nq} queries ({busy:.1f} s of "
-                      f"oracle time; graph generation excluded)"}
-    print(json.dumps(line), flush=True)
-    for h in hs:
-        P.sssp_destroy(h)
+    d = served_metrics(args) if args.config == "serve" else batched_metrics(args, args.config)
+    d.update({"n_gpus": 1, "warmup": args.warmup, "data": "synthetic (seeded generator)"})
+    print(json.dumps(d), flush=True)
 
 
 # ------------------------------------------------------ reference arm
@@ -837,29 +1003,34 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="rmat22")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="default workload: skip the batched / msrc / served sub-objects")
     ap.add_argument("--loop", default="graph", choices=["persistent", "graph", "host"])
     ap.add_argument("--layout", default="auto", choices=list(LAYOUTS))
     ap.add_argument("--rule", default="thr-cheap", choices=list(RULES))
     ap.add_argument("--delta", type=int, default=None,
                     help="window width of the windowed rules (default: max weight / mean degree)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner (the library's default launch shape)")
+    ap.add_argument("--tune-sources", type=int, default=4)
+    ap.add_argument("--tune-reps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=150.0)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--serve-pool", type=int, default=48)
-    ap.add_argument("--serve-queries", type=int, default=400)
+    ap.add_argument("--serve-warm", type=int, default=200)
+    ap.add_argument("--serve-queries", type=int, default=2000)
     ap.add_argument("--serve-rounds", type=int, default=8)
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 1.0, 2.0, 4.0])
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.25, 0.5, 1.0, 2.0, 4.0])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         log("warmup raised to 3 (timing rule)")
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    elif args.config in ("batch", "msrc"):
-        run_batch(args)
-    elif args.config == "serve":
-        run_serve(args)
+    elif args.config in ("batch", "msrc", "serve"):
+        run_extra(args)
     elif args.config == "p2p":
         run_p2p(args)
     else:

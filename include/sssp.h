@@ -143,8 +143,88 @@ typedef struct sssp_options {
                                 (0 = the label-setting round)                              */
 } sssp_options;
 
-/* Fills *opt with the defaults described above. */
+/* Fills *opt with the defaults described above.  hub_degree, chunk_edges
+ * and ctas_per_sm are left 0: the library chooses them (from the tuning
+ * cache when it holds the graph's class, else its defaults). */
 void sssp_options_default(sssp_options* opt);
+
+/* Launch shape of the round kernels for one graph (or one batch).  None of
+ * these changes any result (every output is bit-identical); they change only
+ * how the work is spread over the GPU.  The paper has no counterpart: this
+ * is the GPU's tuning. */
+typedef struct sssp_tuning {
+    uint32_t hub_degree;     /* vertices of degree > hub_degree are split into chunks of
+                                chunk_edges edges, each handled by one warp (1..2^20)     */
+    uint32_t chunk_edges;    /* edges per hub chunk: a multiple of 32, 32..2^20           */
+    uint32_t ctas_per_sm;    /* CTAs of 256 threads per SM of the round kernels
+                                (0 = as many as fit)                                       */
+    uint32_t tail_items;     /* rounds whose frontier and active set each make at most this
+                                many work items (32-vertex tiles and hub chunks) run in the
+                                16-CTA cluster kernel (0 = never)                          */
+} sssp_tuning;
+
+/* The tuning a handle's solves use.  Errors: SSSP_E_INVAL. */
+int sssp_get_tuning(sssp_handle h, sssp_tuning* out);
+
+/* Sets a handle's tuning (recomputes the hub flags, list capacities and
+ * solve contexts; the graph is not copied again).  Errors: SSSP_E_INVAL for
+ * a value out of range, SSSP_E_NOMEM, SSSP_E_CUDA. */
+int sssp_set_tuning(sssp_handle h, const sssp_tuning* t);
+
+/* The key of a graph's class in the tuning cache, from its vertex and edge
+ * counts, largest out- and in-degree, largest weight and state layout
+ * (compact when n * max weight < 2^31), each rounded to a power of two (the
+ * average degree to a half power): graphs of one class share a tuning.
+ * Writes a NUL-terminated string of at most 95 characters.  Host-only.
+ * Errors: SSSP_E_INVAL (cap < 96). */
+int sssp_tune_key(uint32_t n, uint64_t m, uint32_t max_out_degree, uint32_t max_in_degree,
+                  uint32_t max_weight, char* key, size_t cap);
+
+/* The key of a handle's graph (as sssp_tune_key).  Errors: SSSP_E_INVAL. */
+int sssp_graph_key(sssp_handle h, char* key, size_t cap);
+
+/* Process-wide tuning cache, persisted as a JSON object {key: {"hub_degree":
+ * .., "chunk_edges": .., "ctas_per_sm": .., "tail_items": ..}, ...}.  sssp_tune_cache_open loads `path` (a missing file is an empty
+ * cache) and makes later puts write it back (NULL: an in-memory cache only);
+ * without a call, the first use opens the file named by the environment
+ * variable SSSP_TUNE_CACHE, if set.  sssp_create looks up the graph's class
+ * when its options leave hub_degree and chunk_edges 0; sssp_solve_batch
+ * looks up the batch's class.  Host-only; thread-safe.  Errors:
+ * SSSP_E_INVAL (unreadable or malformed file), SSSP_E_NOT_FOUND (get: no
+ * entry), SSSP_E_CUDA never. */
+int sssp_tune_cache_open(const char* path);
+int sssp_tune_cache_get(const char* key, sssp_tuning* out);
+int sssp_tune_cache_put(const char* key, const sssp_tuning* t);
+
+typedef struct sssp_tune_result {
+    sssp_tuning best;        /* the fastest tuning found                                   */
+    double start_ms;         /* device time of one pass over the sources with the tuning
+                                in place before the sweep                                  */
+    double best_ms;          /* the same with `best`                                       */
+    uint32_t evaluated;      /* tunings timed                                              */
+    uint32_t reserved;
+} sssp_tune_result;
+
+/* Autotuner: times single-source solves from `sources` (nsrc >= 1) on the
+ * device for candidate tunings -- hub degree with chunk size, then the
+ * cluster-tail work-item limit, then CTAs per SM, one parameter
+ * group at a time starting from the handle's current tuning -- keeping the
+ * fastest (best of `reps` passes, reps 0 = 3).  The winner is set on the
+ * handle and put in the tuning cache under the graph's key.  Results of
+ * every solve are unchanged.  Errors: as sssp_solve, SSSP_E_INVAL. */
+int sssp_autotune(sssp_handle h, const uint32_t* sources, uint32_t nsrc, uint32_t reps,
+                  sssp_tune_result* out);
+
+/* The same for a batch (as sssp_solve_batch: query i is (g[i], sources[i])):
+ * times whole batched solves and puts the winner in the cache under the
+ * batch's key (its query count, vertex and edge totals and largest graph,
+ * rounded to powers of two), where sssp_solve_batch finds it.  The handles'
+ * own tunings are not changed. */
+int sssp_autotune_batch(const sssp_handle* g, const uint32_t* sources, uint32_t k, uint32_t reps,
+                        sssp_tune_result* out);
+
+/* The key of a batch's class (see sssp_autotune_batch).  Errors: SSSP_E_INVAL. */
+int sssp_batch_key(const sssp_handle* g, uint32_t k, char* key, size_t cap);
 
 /* Builds a device-resident graph (Sec. II: out-edges for relaxation; Sec. IV:
  * in-edges, needed by the lower-bound rule of Lemma 6).
@@ -227,8 +307,10 @@ int sssp_solve_ex(sssp_handle h, uint32_t source, const sssp_solve_args* args,
  * kernels: query i is (g[i], sources[i]); g[i] may repeat (many sources on
  * one graph) or differ (many graphs).  Each query's rounds depend only on its
  * own graph and source, so every result equals the one sssp_solve returns.
- * All handles must live on the same device and be created with the same
- * options.  dist_out[i]: host u64[n_i]; rounds_out: host u32[k] (nullable).
+ * All handles must live on the same device and have the same rule and
+ * window (SSSP_E_INVAL otherwise); their tunings may differ: the batch runs
+ * with the tuning cached for its class (sssp_autotune_batch), else the first
+ * handle's.  dist_out[i]: host u64[n_i]; rounds_out: host u32[k] (nullable).
  * Errors: as sssp_solve, plus SSSP_E_NOMEM for the batch workspace. */
 int sssp_solve_batch(const sssp_handle* g, const uint32_t* sources, uint32_t k,
                      uint64_t* const* dist_out, uint32_t* rounds_out);
@@ -238,68 +320,134 @@ int sssp_solve_batch(const sssp_handle* g, const uint32_t* sources, uint32_t k,
 int sssp_solve_batch_device(const sssp_handle* g, const uint32_t* sources, uint32_t k,
                             uint64_t* const* dist_dev, uint32_t* rounds_out, void* cuda_stream);
 
-/* Continuous-batching query server.  Queries (graph handle, source) are
- * admitted into free slots while earlier queries are in flight, as long as
- * their state fits the device-memory budget; all admitted queries advance
- * together, a few rounds per step, on one stream owned by the server.  A
- * query's result does not depend on which other queries share its rounds. */
+/* Continuous-batching query server (the serving form of Sec. VI's round:
+ * independent queries share its rounds).  Queries (graph handle, source)
+ * are admitted into free slots while earlier queries are in flight, as long
+ * as their state fits the device-memory budget; all admitted queries advance
+ * together, a few rounds per device step, on one stream owned by the
+ * server; between steps finished queries are written out and newly arrived
+ * ones are admitted.  A query's result does not depend on which other
+ * queries share its rounds.  By default a host thread owned by the server
+ * runs the steps whenever a query is queued or in flight, so queries
+ * complete without any call from the client. */
+#define SSSP_SERVE_MANUAL 1u  /* no server thread: sssp_serve_poll, _wait and _drain
+                                 run the steps (the caller drives the server)     */
+#define SSSP_SERVE_WIDE   2u  /* 32-byte records: admits graphs whose
+                                 n * max weight >= 2^31 (default: 16-byte records,
+                                 which such graphs cannot use: SSSP_E_OVERFLOW)   */
+
 typedef struct sssp_serve_cfg {
     uint64_t budget_bytes;   /* device bytes for query state (0 = 32 GiB)                  */
     uint32_t max_slots;      /* queries in flight at once (0 = 1024)                       */
     uint32_t rounds_per_step;/* rounds per device step between admissions (0 = 8)          */
     int32_t device;          /* -1 = current                                               */
-    uint32_t reserved;
-    sssp_alloc_fn alloc;     /* NULL = cudaMalloc (one allocation of budget_bytes)         */
+    uint32_t flags;          /* SSSP_SERVE_* bits                                          */
+    sssp_alloc_fn alloc;     /* NULL = cudaMalloc (one allocation per state array)         */
     sssp_free_fn free;
     void* alloc_ctx;
 } sssp_serve_cfg;
 
-/* Opens a server.  The graphs passed to sssp_serve_submit must stay alive
- * until their queries complete.  Errors: SSSP_E_INVAL, SSSP_E_NOMEM. */
+/* Opens a server (and, unless SSSP_SERVE_MANUAL, starts its thread).  The
+ * graphs passed to sssp_serve_submit must stay alive until their queries
+ * complete; they must have the SSSP_RULE_THRESHOLD rule (any tuning).
+ * Errors: SSSP_E_INVAL, SSSP_E_NOMEM, SSSP_E_CUDA. */
 int sssp_serve_open(const sssp_serve_cfg* cfg, sssp_server** out);
 
 /* Queues a query.  dist_out: host u64[n] written when the query completes
- * (owned by the caller, must stay valid until sssp_serve_poll reports it
- * done).  *ticket identifies the query.  Does not block on the device.
- * Errors: SSSP_E_INVAL, SSSP_E_SOURCE_RANGE, SSSP_E_BUSY (the query alone
- * exceeds the budget). */
+ * (owned by the caller, must stay valid until the query is reported done).
+ * *ticket identifies the query.  Does not block on the device; callable from
+ * any host thread.  Errors: SSSP_E_INVAL (also a graph with other options
+ * than the server's), SSSP_E_SOURCE_RANGE, SSSP_E_OVERFLOW (a graph that
+ * needs 32-byte records on a server without SSSP_SERVE_WIDE), SSSP_E_BUSY
+ * (the query alone exceeds the budget), or the error that stopped the
+ * server. */
 int sssp_serve_submit(sssp_server* s, sssp_handle g, uint32_t source, uint64_t* dist_out,
                       uint64_t* ticket);
 
-/* Advances the server by one step (admission, a few rounds, retirement) and
- * reports on `ticket`: SSSP_OK when its dist_out is written (rounds_out set,
- * nullable), SSSP_PENDING while it is queued or running, SSSP_E_NOT_FOUND
- * for an unknown or already reported ticket. */
+/* Reports on `ticket`: SSSP_OK when its dist_out is written (rounds_out set,
+ * nullable; the ticket is then released), SSSP_PENDING while it is queued or
+ * running, SSSP_E_NOT_FOUND for an unknown or already reported ticket, or
+ * the error that stopped the server.  With SSSP_SERVE_MANUAL it first
+ * advances the server by one step; otherwise it does not block. */
 int sssp_serve_poll(sssp_server* s, uint64_t ticket, uint32_t* rounds_out);
 
-/* Runs the server until every submitted query is complete. */
+/* Timing of one completed query.  Times are nanoseconds of the host's
+ * monotonic clock (std::chrono::steady_clock, CLOCK_MONOTONIC on Linux). */
+typedef struct sssp_query_info {
+    uint32_t rounds;         /* rounds the query ran                                       */
+    uint32_t reserved;
+    uint64_t submit_ns;      /* sssp_serve_submit returned                                 */
+    uint64_t admit_ns;       /* its state was set up on the device                         */
+    uint64_t done_ns;        /* its distances were in dist_out                             */
+    uint64_t first_step;     /* server step in which it was admitted (steps count from 1)  */
+    uint64_t last_step;      /* server step in which it finished                           */
+} sssp_query_info;
+
+/* Waits up to timeout_ms for `ticket` to complete: then as sssp_serve_poll's
+ * SSSP_OK, with info (nullable) filled in; SSSP_PENDING when the time ran
+ * out.  With SSSP_SERVE_MANUAL the calling thread runs the steps meanwhile.
+ * Other results as sssp_serve_poll. */
+int sssp_serve_wait(sssp_server* s, uint64_t ticket, uint32_t timeout_ms, sssp_query_info* info);
+
+/* Blocks until every submitted query is complete.  Errors: SSSP_E_BUSY when
+ * a queued query can never be admitted, or the error that stopped the
+ * server. */
 int sssp_serve_drain(sssp_server* s);
 
-/* Closes the server; queries still in flight are abandoned. */
+typedef struct sssp_serve_stats {
+    uint64_t steps;          /* device steps run                                           */
+    uint64_t rounds;         /* engine rounds run (all queries in flight share a round)    */
+    uint64_t submitted;      /* queries submitted                                          */
+    uint64_t completed;      /* queries whose distances were written out                   */
+    uint32_t queued;         /* waiting for a slot or pages now                            */
+    uint32_t inflight;       /* on the device now                                          */
+    uint32_t max_inflight;   /* most queries on the device together in one step            */
+    uint32_t layout;         /* SSSP_LAYOUT_COMPACT or SSSP_LAYOUT_WIDE                    */
+} sssp_serve_stats;
+
+/* Counters of the server since it was opened.  Errors: SSSP_E_INVAL. */
+int sssp_serve_stats_get(sssp_server* s, sssp_serve_stats* out);
+
+/* Stops the server thread and closes the server; queries still queued or in
+ * flight are abandoned (their dist_out is not written). */
 void sssp_serve_close(sssp_server* s);
 
 /* Per-kernel timing of the round kernels (tracing; the paper has no
  * counterpart).  While enabled on a handle, its single-query solves launch
- * the rounds from the host and bracket every k_relax / k_cupdate launch with
- * CUDA events on the solve stream; launches after the last round are not
- * counted.  Results are bit-identical to the default device loop. */
+ * the round kernels from the host and bracket every launch with CUDA events
+ * on the solve stream.  With the default loop mode (SSSP_LOOP_GRAPH) the
+ * host launches exactly the device loop's iterations -- k_relax, k_cupdate,
+ * then the cluster tail kernel k_tail, which runs the following small rounds
+ * -- so the times describe the schedule of an unprofiled solve; with
+ * SSSP_LOOP_HOST every iteration is one round of k_relax and k_cupdate.
+ * Launches after the last round are not counted.  The work counters of
+ * sssp_solve_info are split by the kernel that did the work.  Results are
+ * bit-identical to an unprofiled solve. */
 typedef struct sssp_kernel_profile {
     uint64_t relax_launches;
     uint64_t cupdate_launches;
     double relax_ms;         /* summed event time of k_relax launches    */
     double cupdate_ms;       /* summed event time of k_cupdate launches  */
+    uint64_t tail_launches;
+    double tail_ms;          /* summed event time of k_tail launches     */
+    uint64_t tail_rounds;    /* rounds finished inside k_tail            */
+    uint64_t grid_counters[4];  /* out_scanned, in_scanned, active_visits, front_visits
+                                   of the work done by k_relax and k_cupdate */
+    uint64_t tail_counters[4];  /* the same for the work done by k_tail   */
 } sssp_kernel_profile;
 
 /* enable: 1 = on, 0 = off.  out (nullable) receives the totals gathered
  * since the last call, which are then reset.  Errors: SSSP_E_INVAL. */
 int sssp_profile(sssp_handle h, int enable, sssp_kernel_profile* out);
 
-/* Per-round event times of the most recent profiled solve: round i's
- * k_relax / k_cupdate milliseconds go to relax_ms[i] / cupdate_ms[i] for
- * i < cap; *count receives the number of rounds recorded.
- * Errors: SSSP_E_INVAL. */
-int sssp_profile_rounds(sssp_handle h, float* relax_ms, float* cupdate_ms, uint32_t cap,
-                        uint32_t* count);
+/* Per-iteration event times of the most recent profiled solve (iterations
+ * of the device loop, or rounds with SSSP_LOOP_HOST): iteration i's
+ * k_relax / k_cupdate / k_tail milliseconds go to relax_ms[i] /
+ * cupdate_ms[i] / tail_ms[i] and the rounds k_tail finished to
+ * tail_rounds[i], for i < cap (tail_ms and tail_rounds nullable); *count
+ * receives the number of iterations recorded.  Errors: SSSP_E_INVAL. */
+int sssp_profile_rounds(sssp_handle h, float* relax_ms, float* cupdate_ms, float* tail_ms,
+                        uint32_t* tail_rounds, uint32_t cap, uint32_t* count);
 
 /* Single-source solve that allocates nothing.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory
@@ -319,11 +467,15 @@ int sssp_profile_rounds(sssp_handle h, float* relax_ms, float* cupdate_ms, uint3
  *   in_off, in_adj: the same edges by target: (source, weight) pairs
  *   The graph must be loop-free with weights > 0 and ids < n (not checked:
  *   it is never copied to the host).
- *   max_weight the largest weight (for the SSSP_E_OVERFLOW check)
+ *   max_weight the largest weight (for the SSSP_E_OVERFLOW check; an edge
+ *              heavier than it is detected on the device during the solve
+ *              and also gives SSSP_E_OVERFLOW)
  *   dist_dev   device u64[n] output, as sssp_solve
  *   rounds_out host u32 (nullable)
  *   cuda_stream the stream for the work (NULL = legacy default stream)
- * The call returns after the stream has finished the solve.  The first call
+ * The call returns after the stream has finished the solve, also when it
+ * fails after enqueuing work (no kernel of a failed call is left running on
+ * the scratch).  The first call
  * on a device sets up that device (looks up the scratch's device address and
  * the kernels' launch limits); make that first call before any stream
  * capture.  Every call shares the scratch and leaves its contents behind

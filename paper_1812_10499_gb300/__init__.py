@@ -43,6 +43,8 @@ SSSP_RULE_WINDOWED = 16
 SSSP_LOOP_GRAPH = 0
 SSSP_LOOP_HOST = 1
 SSSP_LOOP_PERSISTENT = 2
+SSSP_SERVE_MANUAL = 1
+SSSP_SERVE_WIDE = 2
 SSSP_LAYOUT_AUTO = 0
 SSSP_LAYOUT_WIDE = 1
 SSSP_LAYOUT_COMPACT = 2
@@ -81,17 +83,72 @@ class sssp_solve_info(ctypes.Structure):
 
 class sssp_kernel_profile(ctypes.Structure):
     _fields_ = [("relax_launches", ctypes.c_uint64), ("cupdate_launches", ctypes.c_uint64),
-                ("relax_ms", ctypes.c_double), ("cupdate_ms", ctypes.c_double)]
+                ("relax_ms", ctypes.c_double), ("cupdate_ms", ctypes.c_double),
+                ("tail_launches", ctypes.c_uint64), ("tail_ms", ctypes.c_double),
+                ("tail_rounds", ctypes.c_uint64), ("grid_counters", ctypes.c_uint64 * 4),
+                ("tail_counters", ctypes.c_uint64 * 4)]
+
+    COUNTERS = ("out_scanned", "in_scanned", "active_visits", "front_visits")
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if not k.endswith("counters")}
+        d["grid_counters"] = dict(zip(self.COUNTERS, (int(x) for x in self.grid_counters)))
+        d["tail_counters"] = dict(zip(self.COUNTERS, (int(x) for x in self.tail_counters)))
+        return d
 
 
 class sssp_serve_cfg(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_uint32),
                 ("rounds_per_step", ctypes.c_uint32), ("device", ctypes.c_int32),
-                ("reserved", ctypes.c_uint32), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("flags", ctypes.c_uint32), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p)]
+
+
+class sssp_query_info(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("submit_ns", ctypes.c_uint64), ("admit_ns", ctypes.c_uint64),
+                ("done_ns", ctypes.c_uint64), ("first_step", ctypes.c_uint64),
+                ("last_step", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+
+
+class sssp_serve_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint64), ("rounds", ctypes.c_uint64),
+                ("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("queued", ctypes.c_uint32), ("inflight", ctypes.c_uint32),
+                ("max_inflight", ctypes.c_uint32), ("layout", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class sssp_tuning(ctypes.Structure):
+    _fields_ = [("hub_degree", ctypes.c_uint32), ("chunk_edges", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("tail_items", ctypes.c_uint32)]
+
+    FIELDS = ("hub_degree", "chunk_edges", "ctas_per_sm", "tail_items")
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k in self.FIELDS}
+
+    @classmethod
+    def from_dict(cls, d):
+        t = cls()
+        for k in cls.FIELDS:
+            setattr(t, k, int(d[k]))
+        return t
+
+
+class sssp_tune_result(ctypes.Structure):
+    _fields_ = [("best", sssp_tuning), ("start_ms", ctypes.c_double),
+                ("best_ms", ctypes.c_double), ("evaluated", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {"best": self.best.as_dict(), "start_ms": self.start_ms, "best_ms": self.best_ms,
+                "evaluated": int(self.evaluated)}
 
 
 class SsspError(RuntimeError):
@@ -129,12 +186,24 @@ def load(path: str = LIB_PATH):
         "sssp_serve_open": (c_int, [ctypes.POINTER(sssp_serve_cfg), ctypes.POINTER(vp)]),
         "sssp_serve_submit": (c_int, [vp, vp, u32, vp, ctypes.POINTER(u64)]),
         "sssp_serve_poll": (c_int, [vp, u64, ctypes.POINTER(u32)]),
+        "sssp_serve_wait": (c_int, [vp, u64, u32, ctypes.POINTER(sssp_query_info)]),
+        "sssp_serve_stats_get": (c_int, [vp, ctypes.POINTER(sssp_serve_stats)]),
         "sssp_serve_drain": (c_int, [vp]),
         "sssp_serve_close": (None, [vp]),
         "sssp_profile": (c_int, [vp, c_int, ctypes.POINTER(sssp_kernel_profile)]),
-        "sssp_profile_rounds": (c_int, [vp, vp, vp, u32, ctypes.POINTER(u32)]),
+        "sssp_profile_rounds": (c_int, [vp, vp, vp, vp, vp, u32, ctypes.POINTER(u32)]),
         "sssp_solve_noalloc": (c_int, [u32, vp, vp, vp, vp, u32, u32, vp,
                                        ctypes.POINTER(u32), vp]),
+        "sssp_get_tuning": (c_int, [vp, ctypes.POINTER(sssp_tuning)]),
+        "sssp_set_tuning": (c_int, [vp, ctypes.POINTER(sssp_tuning)]),
+        "sssp_tune_key": (c_int, [u32, u64, u32, u32, u32, ctypes.c_char_p, ctypes.c_size_t]),
+        "sssp_graph_key": (c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
+        "sssp_batch_key": (c_int, [vp, u32, ctypes.c_char_p, ctypes.c_size_t]),
+        "sssp_tune_cache_open": (c_int, [ctypes.c_char_p]),
+        "sssp_tune_cache_get": (c_int, [ctypes.c_char_p, ctypes.POINTER(sssp_tuning)]),
+        "sssp_tune_cache_put": (c_int, [ctypes.c_char_p, ctypes.POINTER(sssp_tuning)]),
+        "sssp_autotune": (c_int, [vp, vp, u32, u32, ctypes.POINTER(sssp_tune_result)]),
+        "sssp_autotune_batch": (c_int, [vp, vp, u32, u32, ctypes.POINTER(sssp_tune_result)]),
         "sssp_destroy": (None, [vp]),
         "sssp_host_alloc": (c_int, [ctypes.c_size_t, ctypes.POINTER(vp)]),
         "sssp_host_free": (None, [vp]),
@@ -262,15 +331,20 @@ def sssp_profile(h: int, enable: bool) -> dict:
 
 
 def sssp_profile_rounds(h: int):
-    """Per-round (relax_ms, cupdate_ms) arrays of the last profiled solve."""
+    """Per-iteration (relax_ms, cupdate_ms, tail_ms, tail_rounds) arrays of
+    the last profiled solve."""
     lib = load()
     cnt = ctypes.c_uint32(0)
-    _check(lib.sssp_profile_rounds(h, None, None, 0, ctypes.byref(cnt)), "sssp_profile_rounds")
+    _check(lib.sssp_profile_rounds(h, None, None, None, None, 0, ctypes.byref(cnt)),
+           "sssp_profile_rounds")
     r = np.zeros(cnt.value, dtype=np.float32)
     c = np.zeros(cnt.value, dtype=np.float32)
-    _check(lib.sssp_profile_rounds(h, r.ctypes.data, c.ctypes.data, cnt.value,
-                                   ctypes.byref(cnt)), "sssp_profile_rounds")
-    return r, c
+    t = np.zeros(cnt.value, dtype=np.float32)
+    tr = np.zeros(cnt.value, dtype=np.uint32)
+    _check(lib.sssp_profile_rounds(h, r.ctypes.data, c.ctypes.data, t.ctypes.data,
+                                   tr.ctypes.data, cnt.value, ctypes.byref(cnt)),
+           "sssp_profile_rounds")
+    return r, c, t, tr
 
 
 def sssp_solve_noalloc(n: int, out_off, out_adj, in_off, in_adj, source: int, max_weight: int,
@@ -406,12 +480,15 @@ def sssp_solve_batch_device(handles, sources, dist_devs, stream=None):
 
 
 def sssp_serve_open(budget_bytes: int = 0, max_slots: int = 0, rounds_per_step: int = 0,
-                    device: int = -1) -> int:
+                    device: int = -1, flags: int = 0) -> int:
+    """Opens a server; flags: SSSP_SERVE_MANUAL (no server thread: poll,
+    wait and drain run the steps), SSSP_SERVE_WIDE (32-byte records)."""
     cfg = sssp_serve_cfg()
     cfg.budget_bytes = budget_bytes
     cfg.max_slots = max_slots
     cfg.rounds_per_step = rounds_per_step
     cfg.device = device
+    cfg.flags = flags
     s = ctypes.c_void_p()
     _check(load().sssp_serve_open(ctypes.byref(cfg), ctypes.byref(s)), "sssp_serve_open")
     return s.value
@@ -434,6 +511,23 @@ def sssp_serve_poll(server: int, ticket: int):
     return rc, int(r.value)
 
 
+def sssp_serve_wait(server: int, ticket: int, timeout_ms: int):
+    """Waits up to timeout_ms; returns (status, info dict or None): status
+    SSSP_OK with the query's rounds and monotonic-clock times (ns), or
+    SSSP_PENDING when the time ran out."""
+    info = sssp_query_info()
+    rc = load().sssp_serve_wait(server, ticket, timeout_ms, ctypes.byref(info))
+    if rc not in (SSSP_OK, SSSP_PENDING):
+        raise SsspError(rc, "sssp_serve_wait")
+    return rc, (info.as_dict() if rc == SSSP_OK else None)
+
+
+def sssp_serve_stats_get(server: int) -> dict:
+    st = sssp_serve_stats()
+    _check(load().sssp_serve_stats_get(server, ctypes.byref(st)), "sssp_serve_stats_get")
+    return st.as_dict()
+
+
 def sssp_serve_drain(server: int):
     _check(load().sssp_serve_drain(server), "sssp_serve_drain")
 
@@ -441,3 +535,71 @@ def sssp_serve_drain(server: int):
 def sssp_serve_close(server: int):
     if server:
         load().sssp_serve_close(server)
+
+
+# ----------------------------------------------------------------- tuning
+
+def sssp_get_tuning(h: int) -> dict:
+    t = sssp_tuning()
+    _check(load().sssp_get_tuning(h, ctypes.byref(t)), "sssp_get_tuning")
+    return t.as_dict()
+
+
+def sssp_set_tuning(h: int, tuning: dict):
+    t = sssp_tuning.from_dict(tuning)
+    _check(load().sssp_set_tuning(h, ctypes.byref(t)), "sssp_set_tuning")
+
+
+def sssp_tune_key(n: int, m: int, max_out: int, max_in: int, max_weight: int) -> str:
+    buf = ctypes.create_string_buffer(96)
+    _check(load().sssp_tune_key(n, m, max_out, max_in, max_weight, buf, 96), "sssp_tune_key")
+    return buf.value.decode()
+
+
+def sssp_graph_key(h: int) -> str:
+    buf = ctypes.create_string_buffer(96)
+    _check(load().sssp_graph_key(h, buf, 96), "sssp_graph_key")
+    return buf.value.decode()
+
+
+def sssp_batch_key(handles) -> str:
+    buf = ctypes.create_string_buffer(96)
+    _check(load().sssp_batch_key(_handle_array(handles), len(handles), buf, 96), "sssp_batch_key")
+    return buf.value.decode()
+
+
+def sssp_tune_cache_open(path: str | None):
+    _check(load().sssp_tune_cache_open(None if path is None else path.encode()),
+           "sssp_tune_cache_open")
+
+
+def sssp_tune_cache_get(key: str) -> dict | None:
+    t = sssp_tuning()
+    rc = load().sssp_tune_cache_get(key.encode(), ctypes.byref(t))
+    if rc == SSSP_E_NOT_FOUND:
+        return None
+    _check(rc, "sssp_tune_cache_get")
+    return t.as_dict()
+
+
+def sssp_tune_cache_put(key: str, tuning: dict):
+    t = sssp_tuning.from_dict(tuning)
+    _check(load().sssp_tune_cache_put(key.encode(), ctypes.byref(t)), "sssp_tune_cache_put")
+
+
+def sssp_autotune(h: int, sources, reps: int = 0) -> dict:
+    """Times candidate tunings on the device, sets the fastest on the handle
+    and caches it under the graph's class; returns the sweep's result."""
+    src = np.ascontiguousarray(sources, dtype=np.uint32)
+    r = sssp_tune_result()
+    _check(load().sssp_autotune(h, src.ctypes.data, len(src), reps, ctypes.byref(r)),
+           "sssp_autotune")
+    return r.as_dict()
+
+
+def sssp_autotune_batch(handles, sources, reps: int = 0) -> dict:
+    src = np.ascontiguousarray(sources, dtype=np.uint32)
+    r = sssp_tune_result()
+    _check(load().sssp_autotune_batch(_handle_array(handles), src.ctypes.data, len(handles),
+                                      reps, ctypes.byref(r)), "sssp_autotune_batch")
+    return r.as_dict()

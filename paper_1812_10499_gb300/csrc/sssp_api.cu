@@ -25,7 +25,7 @@ namespace sssp {
 namespace engine {
 
 // Grid of a round kernel: SMs x CTAs per SM (the option, else occupancy).
-int occupancy_grid(int device, const sssp_options& o, bool cupdate = false) {
+int occupancy_grid(int device, const sssp_options& o, bool cupdate) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     int per = (int)o.ctas_per_sm;
@@ -41,6 +41,55 @@ int scan_excl(u64* in, u64 cnt, u64* out, u64* tmp, cudaStream_t st) {
     k_scan_apply<<<tiles, kThreads, 0, st>>>(in, cnt, tmp, out);
     CK(cudaGetLastError());
     return SSSP_OK;
+}
+
+// L2 residency of the per-vertex records, the target of the lower-bound
+// gathers and the relaxation's atomics: when the records fit the device's
+// persisting L2 capacity, an access-policy window over them marks all their
+// lines persisting, so the streamed adjacency and the relaxation filter words
+// do not evict them.  (Measured on R-MAT scale 22: a window larger than the
+// capacity, whose excess lines then stream, is slower than none, and so are
+// the filter words without the window: the relaxation then no longer keeps
+// the records warm for the lower-bound gathers.)  SSSP_L2_PERSIST=0 turns
+// the window, and with it the filter words, off.
+bool records_fit_l2(size_t bytes, int device) {
+    if (const char* v = getenv("SSSP_L2_PERSIST"))
+        if (strtoul(v, nullptr, 10) == 0) return false;
+    int max_win = 0, max_persist = 0;
+    if (cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, device) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, device) !=
+            cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return bytes > 0 && bytes <= (size_t)max_win && bytes <= (size_t)max_persist;
+}
+
+// Sets the window over the context's records when they fit (the context's
+// persisting L2 limit is raised to their size); otherwise clears it.
+void set_l2_window(Context& c, int device) {
+    c.l2win = cudaAccessPolicyWindow{};
+    void* base = c.narrow ? (void*)c.P.recn : (void*)c.P.rec;
+    const size_t bytes = c.nrec * (c.narrow ? sizeof(VRecN) : sizeof(VRec));
+    if (!base || !records_fit_l2(bytes, device)) return;
+    size_t limit = 0;
+    if (cudaDeviceGetLimit(&limit, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    if (limit < bytes &&
+        (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, bytes) != cudaSuccess ||
+         cudaDeviceGetLimit(&limit, cudaLimitPersistingL2CacheSize) != cudaSuccess)) {
+        (void)cudaGetLastError();
+        return;
+    }
+    if (limit < bytes) return;
+    c.l2win.base_ptr = base;
+    c.l2win.num_bytes = bytes;
+    c.l2win.hitRatio = 1.0f;
+    c.l2win.hitProp = cudaAccessPropertyPersisting;
+    c.l2win.missProp = cudaAccessPropertyNormal;
 }
 
 // Builds the device-side while loop: body = relax -> cupdate -> tail (the
@@ -97,6 +146,22 @@ int build_loop(Context& c) {
             e = cudaGraphKernelNodeSetAttribute(n3, cudaLaunchAttributeClusterDimension, &v);
         }
     }
+    // The records' lines persist in L2 (see set_l2_window).
+    if (e == cudaSuccess && c.l2win.num_bytes) {
+        cudaLaunchAttributeValue v{};
+        v.accessPolicyWindow = c.l2win;
+        e = cudaGraphKernelNodeSetAttribute(n1, cudaLaunchAttributeAccessPolicyWindow, &v);
+        if (e == cudaSuccess)
+            e = cudaGraphKernelNodeSetAttribute(n2, cudaLaunchAttributeAccessPolicyWindow, &v);
+        if (e == cudaSuccess && c.tail_ctas) {
+            cudaGraphNode_t nodes[3];
+            size_t cnt = 3;
+            e = cudaGraphGetNodes(body, nodes, &cnt);
+            if (e == cudaSuccess && cnt == 3)
+                e = cudaGraphKernelNodeSetAttribute(nodes[2], cudaLaunchAttributeAccessPolicyWindow,
+                                                    &v);
+        }
+    }
     cudaGraphExec_t x = nullptr;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
     if (e != cudaSuccess) {
@@ -108,6 +173,97 @@ int build_loop(Context& c) {
     return SSSP_OK;
 }
 
+// A profiled solve in the device loop's schedule: each iteration launches
+// k_relax, k_cupdate and the cluster tail kernel from the host, with events
+// around each launch, and snapshots of the control block after k_cupdate and
+// after k_tail that split the work counters by the kernel that did the work.
+int profile_graph_schedule(Context& c, cudaStream_t st) {
+    const void* fr = relax_fn(c.multi, c.narrow);
+    const void* fc = cupdate_fn(c.multi, c.narrow);
+    const void* ft = tail_fn(c.multi, c.narrow);
+    const size_t smr = relax_smem_bytes(c.narrow), smc = cupdate_smem_bytes(c.narrow);
+    RoundParams P = c.P;
+    P.cond = 0;
+    void* args[] = {&P};
+    while (c.ev.size() < 5) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        c.ev.push_back(e);
+    }
+    if (!c.h_snap) CK(cudaHostAlloc((void**)&c.h_snap, 2 * sizeof(Ctl), cudaHostAllocDefault));
+    // Launch attributes as in the device loop: the records' L2 window on
+    // every kernel, the cluster shape on the tail kernel.
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    at[0].val.accessPolicyWindow = c.l2win;
+    at[1].id = cudaLaunchAttributeClusterDimension;
+    at[1].val.clusterDim.x = c.tail_ctas;
+    at[1].val.clusterDim.y = 1;
+    at[1].val.clusterDim.z = 1;
+    const unsigned nwin = c.l2win.num_bytes ? 1u : 0u;
+    cudaLaunchConfig_t rcfg = {}, ccfg = {}, tcfg = {};
+    rcfg.gridDim = dim3(c.grid);
+    rcfg.blockDim = dim3(kThreads);
+    rcfg.dynamicSmemBytes = smr;
+    rcfg.stream = st;
+    rcfg.attrs = at;
+    rcfg.numAttrs = nwin;
+    ccfg = rcfg;
+    ccfg.gridDim = dim3(c.grid_cup);
+    ccfg.dynamicSmemBytes = smc;
+    tcfg.gridDim = dim3(c.tail_ctas);
+    tcfg.blockDim = dim3(kThreads);
+    tcfg.dynamicSmemBytes = solve_smem_bytes(c.narrow);
+    tcfg.stream = st;
+    tcfg.attrs = at + 1 - nwin;
+    tcfg.numAttrs = 1 + nwin;
+    CK(cudaMemcpyAsync(c.h_ctl, c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    Ctl prev = *c.h_ctl;
+    c.prof_round_relax.clear();
+    c.prof_round_cup.clear();
+    c.prof_round_tail.clear();
+    c.prof_round_tail_rounds.clear();
+    while (prev.status == kRunning && prev.round <= prev.stop_round) {
+        CK(cudaEventRecord(c.ev[0], st));
+        CK(cudaLaunchKernelExC(&rcfg, fr, args));
+        CK(cudaEventRecord(c.ev[1], st));
+        CK(cudaLaunchKernelExC(&ccfg, fc, args));
+        CK(cudaEventRecord(c.ev[2], st));
+        CK(cudaMemcpyAsync(&c.h_snap[0], c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(c.ev[3], st));
+        CK(cudaLaunchKernelExC(&tcfg, ft, args));
+        CK(cudaEventRecord(c.ev[4], st));
+        CK(cudaMemcpyAsync(&c.h_snap[1], c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        float a = 0, b = 0, t = 0;
+        CK(cudaEventElapsedTime(&a, c.ev[0], c.ev[1]));
+        CK(cudaEventElapsedTime(&b, c.ev[1], c.ev[2]));
+        CK(cudaEventElapsedTime(&t, c.ev[3], c.ev[4]));
+        const Ctl& A = c.h_snap[0];
+        const Ctl& B = c.h_snap[1];
+        for (int i = 0; i < 4; ++i) {
+            c.prof_grid_ctr[i] += A.stats[i] - prev.stats[i];
+            c.prof_tail_ctr[i] += B.stats[i] - A.stats[i];
+        }
+        const u32 tr = B.round - A.round;
+        c.prof_relax_ms += a;
+        c.prof_cup_ms += b;
+        c.prof_tail_ms += t;
+        c.prof_relax_n++;
+        c.prof_cup_n++;
+        c.prof_tail_n++;
+        c.prof_tail_rounds += tr;
+        c.prof_round_relax.push_back(a);
+        c.prof_round_cup.push_back(b);
+        c.prof_round_tail.push_back(t);
+        c.prof_round_tail_rounds.push_back(tr);
+        prev = B;
+    }
+    *c.h_ctl = prev;
+    return SSSP_OK;
+}
+
 // Runs rounds until the device loop stops (all queries done, stop round hit,
 // or an error).
 int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
@@ -115,7 +271,13 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
     const bool graph = loop_mode == SSSP_LOOP_GRAPH && !c.prof;
     c.last_loop = graph ? SSSP_LOOP_GRAPH : (loop_mode == SSSP_LOOP_PERSISTENT ? loop_mode
                                                                                : SSSP_LOOP_HOST);
-    c.launches_per_iter = c.last_loop == SSSP_LOOP_PERSISTENT ? 0 : (graph && c.tail_ctas ? 3 : 2);
+    // Profiling in the device loop's schedule launches its three kernels.
+    const bool prof_graph = c.prof && loop_mode == SSSP_LOOP_GRAPH && c.tail_ctas;
+    if (prof_graph) c.last_loop = SSSP_LOOP_GRAPH;
+    c.launches_per_iter = c.last_loop == SSSP_LOOP_PERSISTENT
+                              ? 0
+                              : ((graph || prof_graph) && c.tail_ctas ? 3 : 2);
+    if (prof_graph) return profile_graph_schedule(c, st);
     if (loop_mode == SSSP_LOOP_PERSISTENT) {
         RoundParams P = c.P;
         P.cond = 0;
@@ -130,6 +292,7 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
             P.trace = c.trace;
             P.trace_cap = c.trace_cap;
             P.trace_base = c.h_ctl->round;
+            for (int i = 0; i < 4; ++i) c.prof_grid_ctr[i] -= c.h_ctl->stats[i];
         }
         void* args[] = {&P};
         CK(cudaLaunchCooperativeKernel(solve_fn(c.multi, c.narrow), dim3(c.grid_solve),
@@ -137,16 +300,21 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
         if (c.prof) {
             CK(cudaMemcpyAsync(c.h_ctl, c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
+            for (int i = 0; i < 4; ++i) c.prof_grid_ctr[i] += c.h_ctl->stats[i];
             const u32 rounds = std::min<u32>(c.h_ctl->round - P.trace_base, (c.trace_cap - 1) / 2);
             std::vector<u64> t(2 * rounds + 1);
             CK(cudaMemcpy(t.data(), c.trace, sizeof(u64) * t.size(), cudaMemcpyDeviceToHost));
             c.prof_round_relax.clear();
             c.prof_round_cup.clear();
+            c.prof_round_tail.clear();
+            c.prof_round_tail_rounds.clear();
             for (u32 i = 0; i < rounds; ++i) {
                 const float a = (float)((t[2 * i + 1] - t[2 * i]) * 1e-6);
                 const float b = (float)((t[2 * i + 2] - t[2 * i + 1]) * 1e-6);
                 c.prof_round_relax.push_back(a);
                 c.prof_round_cup.push_back(b);
+                c.prof_round_tail.push_back(0.f);
+                c.prof_round_tail_rounds.push_back(0);
                 c.prof_relax_ms += a;
                 c.prof_cup_ms += b;
             }
@@ -180,7 +348,10 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
     if (c.prof) {
         c.prof_round_relax.clear();
         c.prof_round_cup.clear();
+        c.prof_round_tail.clear();
+        c.prof_round_tail_rounds.clear();
     }
+    const Ctl start_ctl = *c.h_ctl;
     for (;;) {
         for (int i = 0; i < kGroup; ++i) {
             if (c.prof) CK(cudaEventRecord(c.ev[3 * i], st));
@@ -201,6 +372,8 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
                 c.prof_cup_ms += b;
                 c.prof_round_relax.push_back(a);
                 c.prof_round_cup.push_back(b);
+                c.prof_round_tail.push_back(0.f);
+                c.prof_round_tail_rounds.push_back(0);
             }
             c.prof_relax_n += ran;
             c.prof_cup_n += ran;
@@ -208,6 +381,8 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
         round_before = c.h_ctl->round;
         if (c.h_ctl->status != kRunning || c.h_ctl->round > c.h_ctl->stop_round) break;
     }
+    if (c.prof)
+        for (int i = 0; i < 4; ++i) c.prof_grid_ctr[i] += c.h_ctl->stats[i] - start_ctl.stats[i];
     return SSSP_OK;
 }
 
@@ -265,8 +440,18 @@ int init_single_context(sssp_graph* h) {
     P.g.n = h->n;
     P.g.source = 0;
     c.narrow = h->narrow;
-    if (c.narrow) RC(c.pool.get(&P.recn, h->n));
-    else RC(c.pool.get(&P.rec, h->n));
+    if (c.narrow) {
+        // Compact records, then (label-setting rounds, records held in L2)
+        // the relaxation filter words right after them.
+        const bool filt = (h->opt.rule & (SSSP_RULE_LABEL_CORRECTING | SSSP_RULE_WINDOWED)) == 0 &&
+                          records_fit_l2((size_t)h->n * sizeof(VRecN), h->device);
+        unsigned char* buf = nullptr;
+        RC(c.pool.get(&buf, (size_t)h->n * (sizeof(VRecN) + (filt ? sizeof(uint2) : 0))));
+        P.recn = reinterpret_cast<VRecN*>(buf);
+        P.gf = filt ? reinterpret_cast<uint2*>(buf + (size_t)h->n * sizeof(VRecN)) : nullptr;
+    } else {
+        RC(c.pool.get(&P.rec, h->n));
+    }
     RC(c.pool.get(&P.fround, h->n));
     RC(c.pool.get(&P.ctl, 1));
     RC(c.pool.get(&P.ivar, 1));
@@ -288,6 +473,7 @@ int init_single_context(sssp_graph* h) {
         RC(c.pool.get(&P.L.FX[1], h->n));
     }
     P.page_shift = kPageShift;
+    set_l2_window(c, h->device);
     RC(alloc_pinned(c, 1));
     CK(cudaMemsetAsync(P.L.hubmin, 0xFF, sizeof(u64) * c.capH, h->stream));
     CK(cudaMemsetAsync(P.L.hubcnt, 0, sizeof(u32) * c.capH, h->stream));
@@ -417,11 +603,7 @@ int create_impl(sssp_graph* h, u32 n, u64 m, const u64* row_ptr, const u32* col,
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
         h->grid_solve = std::max(1, sms) * std::max(1, solve_blocks_per_sm(kThreads));
-        // Small rounds run in one thread-block cluster (SSSP_TAIL_ITEMS: most
-        // work items per phase of such a round; 0 disables it).
         h->tail_items = kDefaultTailItems;
-        if (const char* v = getenv("SSSP_TAIL_ITEMS")) h->tail_items = (u32)strtoul(v, nullptr, 10);
-        h->tail_ctas = h->tail_items ? tail_cluster_ctas() : 0;
     }
     Pool& gp = h->gpool;
     RC(gp.get(&h->out_off, (size_t)n + 1));
@@ -475,31 +657,60 @@ int create_impl(sssp_graph* h, u32 n, u64 m, const u64* row_ptr, const u32* col,
     RC(gp.get(&h->inw, n));   // inWeight: the same reduction over the in-edges
     k_outw<<<h->grid, kThreads, 0, h->stream>>>(h->in_off, h->in_adj, n, h->inw);
     CK(cudaGetLastError());
+    // The graph's degree statistics (its class in the tuning cache), then
+    // the state that depends on the tuning.
+    RC(count_hubs(h, h->opt.hub_degree, &h->hubs_out, &h->hubs_in, &h->max_out, &h->max_in));
+    resolve_tuning(h);
+    RC(apply_tuning(h));
+    return SSSP_OK;
+}
+
+// Hub counts by direction for hub degree `hub` (list capacities), and the
+// largest out- and in-degree (nullable outputs).
+int count_hubs(sssp_graph* h, u32 hub, u32* hubs_out, u32* hubs_in, u32* max_out, u32* max_in) {
+    Pool tmp;
+    tmp.al = h->gpool.al;
+    u32* cnt = nullptr;
+    RC(tmp.get(&cnt, 4));
+    u32 hc[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(hc), h->stream);
+    if (e == cudaSuccess) {
+        k_count_hubs<<<h->grid, kThreads, 0, h->stream>>>(h->out_off, h->in_off, h->n, hub, cnt);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    tmp.release();
+    CK(e);
+    *hubs_out = hc[0];
+    *hubs_in = hc[1];
+    if (max_out) *max_out = hc[2];
+    if (max_in) *max_in = hc[3];
+    return SSSP_OK;
+}
+
+// State that depends on the tuning (hub degree, chunk size, CTAs per SM,
+// cluster-tail thresholds): the round kernels' grids, the compact layout's
+// in-hub flags, the hub counts, and the solve contexts (rebuilt).
+int apply_tuning(sssp_graph* h) {
+    const u32 n = h->n;
+    CK(cudaStreamSynchronize(h->stream));
+    h->grid = occupancy_grid(h->device, h->opt);
+    h->grid_cup = occupancy_grid(h->device, h->opt, true);
+    h->tail_ctas = h->tail_items ? tail_cluster_ctas() : 0;
     if (h->narrow) {
-        RC(gp.get(&h->outw_pack, n));
+        if (!h->outw_pack) RC(h->gpool.get(&h->outw_pack, n));
         k_pack_outw<<<h->grid, kThreads, 0, h->stream>>>(h->outw, h->in_off, n, h->opt.hub_degree,
                                                          h->outw_pack);
         CK(cudaGetLastError());
     }
-    {
-        Pool tmp;
-        tmp.al = gp.al;
-        u32* cnt = nullptr;
-        RC(tmp.get(&cnt, 2));
-        u32 hc[2] = {0, 0};
-        cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(u32) * 2, h->stream);
-        if (e == cudaSuccess) {
-            k_count_hubs<<<h->grid, kThreads, 0, h->stream>>>(h->out_off, h->in_off, n,
-                                                              h->opt.hub_degree, cnt);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        tmp.release();
-        CK(e);
-        h->hubs_out = hc[0];
-        h->hubs_in = hc[1];
+    RC(count_hubs(h, h->opt.hub_degree, &h->hubs_out, &h->hubs_in, nullptr, nullptr));
+    h->single.destroy();
+    h->single = Context();
+    if (h->batch) {
+        h->batch->destroy();
+        delete h->batch;
+        h->batch = nullptr;
     }
     RC(init_single_context(h));
     CK(cudaStreamSynchronize(h->stream));
@@ -544,13 +755,13 @@ int read_status(Context& c, cudaStream_t st, u32 ninst) {
 
 // Enqueues one single-query solve on `st` (no synchronisation).
 int enqueue_single(sssp_graph* h, u32 source, u32 max_rounds, cudaStream_t st, u64* dist_dev,
-                   u32* parent_dev, int* fround_dev, u64* lower_dev, u32 target = kNoTarget) {
+                   u32* parent_dev, int* fround_dev, u64* lower_dev, u32 target) {
     Context& c = h->single;
     RoundParams P = c.P;
     P.g.source = source;
     c.P.g.source = source;
     k_init_records<<<c.grid, kThreads, 0, st>>>(P.rec, P.recn, P.fround, h->outw, h->in_off, h->n,
-                                                P.chg);
+                                                P.chg, P.gf, h->outw_pack);
     k_reset_ctl<<<1, 32, 0, st>>>(P.ctl, 1, h->n + 2);
     CK(launch_start(false, c.narrow, P, 0, 1, max_rounds, st, target));
     RC(run_loop(c, h->opt.loop_mode, st));
@@ -623,25 +834,48 @@ int ensure_batch(sssp_graph* h0, u64 nrec, u32 nslots, u32 npages, u64 capH, u64
 }
 
 int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist, bool dev,
-               u32* rounds_out, cudaStream_t st_user, bool use_user_stream) {
+               u32* rounds_out, cudaStream_t st_user, bool use_user_stream,
+               const sssp_tuning* tune) {
     if (!g || !sources || !dist || k == 0) return SSSP_E_INVAL;
     sssp_graph* h0 = g[0];
     if (!h0) return SSSP_E_INVAL;
+    for (u32 i = 0; i < k; ++i) {
+        if (!g[i] || !dist[i]) return SSSP_E_INVAL;
+        if (g[i]->device != h0->device || g[i]->opt.rule != h0->opt.rule ||
+            g[i]->opt.delta != h0->opt.delta)
+            return SSSP_E_INVAL;
+        if (sources[i] >= g[i]->n) return SSSP_E_SOURCE_RANGE;
+    }
+    // The batch's tuning: the one given (autotuner), else the cache's entry
+    // for the batch's class, else the first graph's.  The graphs' own hub
+    // degrees may differ from it: a graph's in-hub flags (compact layout)
+    // then place some vertices in the other list, which changes no result.
+    sssp_tuning bt{};
+    if (tune) {
+        bt = *tune;
+    } else {
+        char key[96];
+        batch_key(g, k, key, sizeof(key));
+        if (tune_cache_find(key, &bt) != SSSP_OK) {
+            bt.hub_degree = h0->opt.hub_degree;
+            bt.chunk_edges = h0->opt.chunk_edges;
+            bt.ctas_per_sm = h0->opt.ctas_per_sm;
+            bt.tail_items = h0->tail_items;
+        }
+    }
     u32 vbits = 1;
     bool narrow = true;
     u64 npages = 0, capH = 0, capC = 0;
     for (u32 i = 0; i < k; ++i) {
-        if (!g[i] || !dist[i]) return SSSP_E_INVAL;
-        if (g[i]->device != h0->device || g[i]->opt.hub_degree != h0->opt.hub_degree ||
-            g[i]->opt.chunk_edges != h0->opt.chunk_edges || g[i]->opt.rule != h0->opt.rule ||
-            g[i]->opt.delta != h0->opt.delta)
-            return SSSP_E_INVAL;
-        if (sources[i] >= g[i]->n) return SSSP_E_SOURCE_RANGE;
         vbits = std::max(vbits, std::max<u32>(1, bits_for((u64)g[i]->n - 1)));
         narrow = narrow && g[i]->narrow;
         npages += ((u64)g[i]->n + (1u << kPageShift) - 1) >> kPageShift;
-        capH += std::max(g[i]->hubs_in, g[i]->hubs_out);
-        capC += hub_chunks(g[i]);
+        // Hub entries: flagged in-hubs of the graph's own hub degree, and at
+        // most m / (hub + 1) vertices above the batch's hub degree.
+        const u64 above = std::min<u64>(g[i]->n, g[i]->m / ((u64)bt.hub_degree + 1));
+        const u64 hi = std::max<u64>(std::max(g[i]->hubs_in, g[i]->hubs_out), above) + 1;
+        capH += hi;
+        capC += g[i]->m / bt.chunk_edges + hi;
     }
     const u64 nrec = npages << kPageShift;
     if (nrec >= 0xFFFFFFFFull) return SSSP_E_NOMEM;   // list entries are 32-bit record ids
@@ -656,18 +890,38 @@ int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist
     Context& c = *h0->batch;
     cudaStream_t st = use_user_stream ? st_user : h0->stream;
     RoundParams& P = c.P;
+    sssp_options bo = h0->opt;
+    bo.ctas_per_sm = bt.ctas_per_sm;
+    const int grid = occupancy_grid(h0->device, bo), grid_cup = occupancy_grid(h0->device, bo, true);
+    const u32 tail_ctas = bt.tail_items ? tail_cluster_ctas() : 0;
     // The loop graph bakes the params in; rebuild it when they change.
-    if (c.exec && (P.vbits != vbits || c.narrow != narrow)) {
+    if (c.exec && (P.vbits != vbits || c.narrow != narrow || P.hub != bt.hub_degree ||
+                   P.chunk != bt.chunk_edges || P.tail_items != bt.tail_items ||
+                   c.grid != grid || c.grid_cup != grid_cup || c.tail_ctas != tail_ctas)) {
         cudaGraphExecDestroy(c.exec);
         cudaGraphDestroy(c.graph);
         c.exec = nullptr;
         c.graph = nullptr;
     }
+    P.hub = bt.hub_degree;
+    P.chunk = bt.chunk_edges;
+    P.tail_items = bt.tail_items;
+    c.grid = grid;
+    c.grid_cup = grid_cup;
+    c.tail_ctas = tail_ctas;
     P.vbits = vbits;
     P.dinf = dinf;
     c.narrow = narrow;
     P.rec = narrow ? nullptr : c.rec_store;
     P.recn = narrow ? reinterpret_cast<VRecN*>(c.rec_store) : nullptr;
+    // Compact label-setting batches whose records fit the persisting L2 keep
+    // the relaxation filter words in the second half of the 32-byte record
+    // slots (right after the records).
+    P.gf = (narrow && !P.lc && !P.win && records_fit_l2(c.nrec * sizeof(VRecN), h0->device))
+               ? reinterpret_cast<uint2*>(reinterpret_cast<unsigned char*>(c.rec_store) +
+                                          c.nrec * sizeof(VRecN))
+               : nullptr;
+    if (!c.exec) set_l2_window(c, h0->device);   // baked into the loop graph built next
     P.g = InstDesc{g[0]->out_off, g[0]->out_adj, g[0]->in_off, g[0]->in_adj,
                    narrow ? g[0]->outw_pack : g[0]->outw, g[0]->inw, 0, g[0]->n, sources[0]};
     u64 page = 0;
@@ -729,8 +983,8 @@ void sssp_options_default(sssp_options* opt) {
     memset(opt, 0, sizeof(*opt));
     opt->rule = SSSP_RULE_THRESHOLD;
     opt->loop_mode = SSSP_LOOP_GRAPH;
-    opt->hub_degree = kDefaultHub;
-    opt->chunk_edges = kDefaultChunk;
+    opt->hub_degree = 0;      // the library chooses (see sssp_tuning)
+    opt->chunk_edges = 0;
     opt->block_threads = kThreads;
     opt->ctas_per_sm = 0;
     opt->device = -1;
@@ -743,6 +997,8 @@ int sssp_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t*
     sssp_options o;
     sssp_options_default(&o);
     if (opt) o = *opt;
+    // Hub degree and chunk size both left 0: the library chooses the tuning.
+    const bool tune_auto = o.hub_degree == 0 && o.chunk_edges == 0;
     if (o.hub_degree == 0) o.hub_degree = kDefaultHub;
     if (o.chunk_edges == 0) o.chunk_edges = kDefaultChunk;
     if (o.block_threads == 0) o.block_threads = kThreads;
@@ -779,6 +1035,7 @@ int sssp_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t*
     h->device = dev;
     h->opt = o;
     h->opt.device = dev;
+    h->tune_auto = tune_auto;
     h->gpool.al = Allocator{o.alloc, o.free, o.alloc_ctx};
     int rc;
     {
@@ -957,7 +1214,7 @@ int sssp_solve_device(sssp_handle h, uint32_t source, uint64_t* dist_dev, uint32
     std::lock_guard<std::mutex> lk(h->mu);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     RC(enqueue_single(h, source, 0, st, reinterpret_cast<u64*>(dist_dev), nullptr, nullptr,
-                      nullptr));
+                      nullptr, kNoTarget));
     if (rounds_out) {
         RC(read_status(h->single, st, 1));
         if (h->single.h_ivar[0].status != kDone) return SSSP_E_ROUND_LIMIT;
@@ -969,13 +1226,13 @@ int sssp_solve_device(sssp_handle h, uint32_t source, uint64_t* dist_dev, uint32
 int sssp_solve_batch(const sssp_handle* g, const uint32_t* sources, uint32_t k,
                      uint64_t* const* dist_out, uint32_t* rounds_out) {
     return batch_impl(g, sources, k, reinterpret_cast<u64* const*>(dist_out), false, rounds_out,
-                      nullptr, false);
+                      nullptr, false, nullptr);
 }
 
 int sssp_solve_batch_device(const sssp_handle* g, const uint32_t* sources, uint32_t k,
                             uint64_t* const* dist_dev, uint32_t* rounds_out, void* cuda_stream) {
     return batch_impl(g, sources, k, reinterpret_cast<u64* const*>(dist_dev), true, rounds_out,
-                      (cudaStream_t)cuda_stream, true);
+                      (cudaStream_t)cuda_stream, true, nullptr);
 }
 
 int sssp_profile(sssp_handle h, int enable, sssp_kernel_profile* out) {
@@ -987,15 +1244,23 @@ int sssp_profile(sssp_handle h, int enable, sssp_kernel_profile* out) {
         out->cupdate_launches = c.prof_cup_n;
         out->relax_ms = c.prof_relax_ms;
         out->cupdate_ms = c.prof_cup_ms;
+        out->tail_launches = c.prof_tail_n;
+        out->tail_ms = c.prof_tail_ms;
+        out->tail_rounds = c.prof_tail_rounds;
+        for (int i = 0; i < 4; ++i) {
+            out->grid_counters[i] = c.prof_grid_ctr[i];
+            out->tail_counters[i] = c.prof_tail_ctr[i];
+        }
     }
-    c.prof_relax_n = c.prof_cup_n = 0;
-    c.prof_relax_ms = c.prof_cup_ms = 0;
+    c.prof_relax_n = c.prof_cup_n = c.prof_tail_n = c.prof_tail_rounds = 0;
+    c.prof_relax_ms = c.prof_cup_ms = c.prof_tail_ms = 0;
+    for (int i = 0; i < 4; ++i) c.prof_grid_ctr[i] = c.prof_tail_ctr[i] = 0;
     c.prof = enable != 0;
     return SSSP_OK;
 }
 
-int sssp_profile_rounds(sssp_handle h, float* relax_ms, float* cupdate_ms, uint32_t cap,
-                        uint32_t* count) {
+int sssp_profile_rounds(sssp_handle h, float* relax_ms, float* cupdate_ms, float* tail_ms,
+                        uint32_t* tail_rounds, uint32_t cap, uint32_t* count) {
     if (!h || !count || (cap && (!relax_ms || !cupdate_ms))) return SSSP_E_INVAL;
     std::lock_guard<std::mutex> lk(h->mu);
     const Context& c = h->single;
@@ -1003,6 +1268,8 @@ int sssp_profile_rounds(sssp_handle h, float* relax_ms, float* cupdate_ms, uint3
     for (u32 i = 0; i < n && i < cap; ++i) {
         relax_ms[i] = c.prof_round_relax[i];
         cupdate_ms[i] = c.prof_round_cup[i];
+        if (tail_ms) tail_ms[i] = c.prof_round_tail[i];
+        if (tail_rounds) tail_rounds[i] = c.prof_round_tail_rounds[i];
     }
     *count = n;
     return SSSP_OK;

@@ -45,6 +45,7 @@ struct __align__(16) VRecN {
 static_assert(sizeof(VRecN) == 16, "VRecN must be 16 bytes");
 constexpr u32 kFixedN = 1u << 31;
 constexpr u64 kNarrowLimit = kFixedN - 1;   // distances must stay below this
+constexpr u32 kRelaxUnseen = 0x7FFFFFFFu;   // relaxation bound of an undiscovered vertex
 
 // Read-only description of one query's graph.
 struct InstDesc {
@@ -97,6 +98,7 @@ struct __align__(16) Ctl {
                         // full-grid relax launch is skipped
     u32 body_iters;     // launches of the relax kernel (one per loop iteration)
     u32 nFX[2];         // label-correcting: vertices fixed in the round (see Lists::FX)
+
     u64 stats[5];       // out-edges scanned, in-edges scanned, active visits, frontier
                         // visits, vertices fixed (single query)
 };
@@ -129,6 +131,12 @@ struct RoundParams {
     const u32* page_owner;      // record page -> slot (multi-query)
     VRec* rec;                  // wide records (or nullptr)
     VRecN* recn;                // compact records (or nullptr)
+    uint2* gf;                  // compact layout, label-setting rounds (or nullptr): per
+                                // record {relaxation bound, outWeight word}.  The bound is
+                                // 0 once the vertex is fixed, else at least its distance
+                                // (kRelaxUnseen before it is discovered); the second word
+                                // is its graph's outWeight | in-hub flag.  The relaxation
+                                // filters its candidates with it instead of the record.
     int* fround;                // per record: round in which it was fixed, -1 if never
     Ctl* ctl;
     Lists L;

@@ -31,7 +31,8 @@ cudaError_t launch_start(bool multi, bool narrow, const RoundParams& P, u32 firs
 int round_blocks_per_sm(int threads);
 int cupdate_blocks_per_sm(int threads);
 __global__ void k_init_records(VRec* rec, VRecN* recn, int* fround, const u32* outw,
-                               const u64* in_off, u32 n, u32* chg = nullptr);
+                               const u64* in_off, u32 n, u32* chg = nullptr,
+                               uint2* gf = nullptr, const u32* outw_pack = nullptr);
 __global__ void k_init_records_multi(RoundParams P, u64 nrec, u32 first_page, u32 npages);
 __global__ void k_reset_ctl(Ctl* ctl, u32 ninst, u32 round_limit);
 __global__ void k_finalize(const VRec* rec, const VRecN* recn, const int* frec, u64 base, u32 n,
@@ -162,9 +163,15 @@ struct Context {
     // Per-kernel event timing (sssp_profile).
     bool prof = false;
     std::vector<cudaEvent_t> ev;
-    u64 prof_relax_n = 0, prof_cup_n = 0;
-    double prof_relax_ms = 0, prof_cup_ms = 0;
-    std::vector<float> prof_round_relax, prof_round_cup;   // last profiled solve
+    u64 prof_relax_n = 0, prof_cup_n = 0, prof_tail_n = 0, prof_tail_rounds = 0;
+    double prof_relax_ms = 0, prof_cup_ms = 0, prof_tail_ms = 0;
+    u64 prof_grid_ctr[4] = {}, prof_tail_ctr[4] = {};      // counters by kernel (see sssp.h)
+    // Last profiled solve, one entry per loop iteration (host-launched rounds:
+    // one round each).
+    std::vector<float> prof_round_relax, prof_round_cup, prof_round_tail;
+    std::vector<u32> prof_round_tail_rounds;
+    Ctl* h_snap = nullptr;           // pinned control-block snapshots (graph-schedule profile)
+    cudaAccessPolicyWindow l2win{};  // L2 window over the records (num_bytes 0: none)
     u64* trace = nullptr;            // device trace of the persistent kernel
     u32 trace_cap = 0;
 
@@ -178,6 +185,8 @@ struct Context {
         if (h_desc) cudaFreeHost(h_desc);
         if (h_pages) cudaFreeHost(h_pages);
         if (h_stage) cudaFreeHost(h_stage);
+        if (h_snap) cudaFreeHost(h_snap);
+        h_snap = nullptr;
         h_ctl = nullptr;
         h_ivar = nullptr;
         h_desc = nullptr;
@@ -218,6 +227,8 @@ struct sssp_graph {
     int grid_cup = 0;
     u32 tail_ctas = 0;               // see Context::tail_ctas
     u32 tail_items = 0;
+    u32 max_out = 0, max_in = 0;     // largest out- / in-degree (the graph's class)
+    bool tune_auto = false;          // the options left the tuning to the library
     sssp::engine::Context single;    // single-query context
     sssp::engine::Context* batch = nullptr;  // multi-query context (grown on demand)
     std::mutex mu;
@@ -226,9 +237,25 @@ struct sssp_graph {
 
 namespace sssp {
 namespace engine {
+int count_hubs(sssp_graph* h, u32 hub, u32* hubs_out, u32* hubs_in, u32* max_out, u32* max_in);
+int apply_tuning(sssp_graph* h);
+void resolve_tuning(sssp_graph* h);
+int enqueue_single(sssp_graph* h, u32 source, u32 max_rounds, cudaStream_t st, u64* dist_dev,
+                   u32* parent_dev, int* fround_dev, u64* lower_dev, u32 target);
+int batch_impl(const sssp_handle* g, const u32* sources, u32 k, u64* const* dist, bool dev,
+               u32* rounds_out, cudaStream_t st_user, bool use_user_stream,
+               const sssp_tuning* tune);
+int occupancy_grid(int device, const sssp_options& o, bool cupdate = false);
+// Tuning cache (sssp_tune.cu): the class key of a graph / a batch and the
+// process-wide cache of tunings by key.
+void graph_key(const sssp_graph* h, char* buf, size_t cap);
+void batch_key(const sssp_handle* g, u32 k, char* buf, size_t cap);
+int tune_cache_find(const char* key, sssp_tuning* out);
 int build_loop(Context& c);
 int run_loop(Context& c, u32 loop_mode, cudaStream_t st);
 int alloc_lists(Context& c, u64 capS, u64 capH, u64 capC);
 int alloc_pinned(Context& c, u32 slots);
+void set_l2_window(Context& c, int device);
+bool records_fit_l2(size_t bytes, int device);
 }  // namespace engine
 }  // namespace sssp

@@ -536,10 +536,13 @@ __device__ __forceinline__ void issue_range_adj(WarpStage<S>& st, u32 s, const u
 // Starts gathering the neighbour states of the nb edges in adjacency slot
 // as into state slot ds.  `base` is the record base of the edge's graph,
 // taken from the owning lane in multi-query mode.
-template <bool MULTI, class L, class S>
+template <bool MULTI, class L, bool RELAX = false, class S>
 __device__ __forceinline__ void issue_dc(const RoundParams& P, WarpStage<S>& st, u32 as, u32 ds,
                                          u32 nb, u32 cur, u64 base, bool per_owner, u32 lane) {
     typename L::Rec* rec = L::rec(P);
+    // The relaxation of the compact label-setting round stages the 8-byte
+    // filter word (relaxation bound, outWeight) instead of the record.
+    const bool filt = RELAX && L::kNarrow && P.gf != nullptr;
 #pragma unroll
     for (u32 i = 0; i < kBI; ++i) {
         if (32 * i >= nb) break;                   // warp-uniform
@@ -547,7 +550,10 @@ __device__ __forceinline__ void issue_dc(const RoundParams& P, WarpStage<S>& st,
         const bool ev = idx < nb;
         u64 ob = base;
         if (MULTI && per_owner) ob = __shfl_sync(kFull, base, ev ? st.own[as][idx] : 0u);
-        if (ev) st.dc[ds][idx].issue(rec + (u32)(ob + st.adj[as][idx].x), cur);
+        if (!ev) continue;
+        const u32 gy = (u32)(ob + st.adj[as][idx].x);
+        if (filt) cp_async_8(&st.dc[ds][idx], P.gf + gy);
+        else st.dc[ds][idx].issue(rec + gy, cur);
     }
 }
 
@@ -612,6 +618,19 @@ __device__ __forceinline__ void relax_issue(const RoundParams& P,
         pd.yl[i] = e.x;
         pd.gy[i] = (u32)(ob + e.x);
         pd.inst[i] = oi;
+        if (L::kNarrow && P.gf) {
+            // Filter word: bound 0 (fixed) rejects every candidate, a larger
+            // distance cannot lower D; an equal one may (smaller parent).
+            const uint2 fw = *reinterpret_cast<const uint2*>(&v);
+            if (dd <= fw.x) {
+                pd.cand[i] = cand;
+                if (fw.x == kRelaxUnseen) pd.old[i] = atomicMin(&rec[pd.gy[i]].dp, cand);
+                else atomicMin(&rec[pd.gy[i]].dp, cand);
+                pd.ow[i] = fw.y;
+            }
+            a.edges++;
+            continue;
+        }
         if (!v.fixed(cur) && cand < v.d()) {
             pd.cand[i] = cand;
             // Windowed: D[y] changes this round (it ends at most cand, below the
@@ -728,7 +747,8 @@ __device__ void relax_small(const RoundParams& P, WarpStage<typename L::RSlot>& 
         (tl.total + kB - 1) / kB,
         [&](u32 bb, u32 s) { issue_tile_adj(st, tl, s, bb * kB, deg, lane); },
         [&](u32 bb, u32 as, u32 ds) {
-            issue_dc<MULTI, L>(P, st, as, ds, min(kB, tl.total - bb * kB), cur, gbase, true, lane);
+            issue_dc<MULTI, L, true>(P, st, as, ds, min(kB, tl.total - bb * kB), cur, gbase, true,
+                                     lane);
         },
         [&](u32 bb, u32 as, u32 ds) {
             relax_consume<MULTI, L>(P, cur, a, q, qf, pd, lane);
@@ -760,7 +780,7 @@ __device__ void relax_hub(const RoundParams& P, WarpStage<typename L::RSlot>& st
         (n + kB - 1) / kB,
         [&](u32 bb, u32 s) { issue_range_adj(st, s, d.out_adj, cb + bb * kB, ce, lane); },
         [&](u32 bb, u32 as, u32 ds) {
-            issue_dc<MULTI, L>(P, st, as, ds, min(kB, n - bb * kB), cur, d.base, false, lane);
+            issue_dc<MULTI, L, true>(P, st, as, ds, min(kB, n - bb * kB), cur, d.base, false, lane);
         },
         [&](u32 bb, u32 as, u32 ds) {
             relax_consume<MULTI, L>(P, cur, a, q, qf, pd, lane);
@@ -997,6 +1017,8 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
         else cn = decide(P, dy, cy, smin[lane], thr, minD, fix);
         L::set_c(rec + g, nxt, cn | (fix ? kFixed : 0ull));
         if (fix) P.fround[g] = (int)r;
+        // Relaxation bound: D is stable until the next relaxation.
+        if (L::kNarrow && P.gf) P.gf[g].x = fix ? 0u : (u32)dy;
         a.visits++;
     }
     __syncwarp();
@@ -1089,6 +1111,7 @@ __device__ void cup_hub(const RoundParams& P, WarpStage<typename L::CSlot>& st, 
     u64 cn = dy;
     if (!cheap_fix) cn = decide(P, dy, cy, m, thr, minD, fix);
     L::set_c(ry, nxt, cn | (fix ? kFixed : 0ull));
+    if (L::kNarrow && P.gf) P.gf[g].x = fix ? 0u : (u32)dy;
     a.visits++;
     // The next frontier and FX as in cup_small.
     bool front = fix && !P.lc;
@@ -1521,6 +1544,7 @@ __global__ void k_start(RoundParams P, u32 first, u32 count, u32 max_rounds, u32
         rs->dp = s;                   // distance 0, parent = itself
         L::set_c(rs, 0, kFixed);
         L::set_c(rs, 1, kFixed);
+        if (L::kNarrow && P.gf) P.gf[g].x = 0u;   // fixed: no relaxation into it
         P.fround[g] = 0;
         if (P.snap) P.snap[g] = 0;    // label-correcting: relaxed in round 1 with D = 0
         if (target == s) {            // answered: the source is fixed

@@ -14,8 +14,11 @@ __device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
 
 // Every record of a single query: D = inf, C = 0 (Fig. SP_4 declarations).
 // Exactly one of rec (32-byte records) and recn (16-byte records) is set.
+// gf (nullable, compact layout): the relaxation filter words, from the
+// packed outWeight words outw_pack.
 __global__ void k_init_records(VRec* rec, VRecN* recn, int* fround, const u32* outw,
-                               const u64* in_off, u32 n, u32* chg) {
+                               const u64* in_off, u32 n, u32* chg, uint2* gf,
+                               const u32* outw_pack) {
     for (u64 v = blockIdx.x * (u64)blockDim.x + threadIdx.x; v < n;
          v += (u64)gridDim.x * blockDim.x) {
         if (recn) {
@@ -24,6 +27,7 @@ __global__ void k_init_records(VRec* rec, VRecN* recn, int* fround, const u32* o
             r.cf[0] = 0;
             r.cf[1] = 0;
             recn[v] = r;
+            if (gf) gf[v] = make_uint2(kRelaxUnseen, outw_pack[v]);
         } else {
             VRec r;
             r.dp = kInf64;
@@ -55,6 +59,7 @@ __global__ void k_init_records_multi(RoundParams P, u64 nrec, u32 first_page, u3
             r.cf[0] = 0;
             r.cf[1] = 0;
             P.recn[g] = r;
+            if (P.gf) P.gf[g] = make_uint2(kRelaxUnseen, d.outw[v]);
         } else {
             VRec r;
             r.dp = kInf64;
@@ -175,21 +180,32 @@ __global__ void k_pack_outw(const u32* outw, const u64* in_off, u32 n, u32 hub, 
     }
 }
 
-// Vertices above the hub degree, by direction (list capacities).
+// Vertices above the hub degree, by direction (list capacities), and the
+// largest out- and in-degree (cnt[2], cnt[3]; clamped to 2^32 - 1).
 __global__ void k_count_hubs(const u64* out_off, const u64* in_off, u32 n, u32 hub, u32* cnt) {
     u32 a = 0, b = 0;
+    u64 mo = 0, mi = 0;
     for (u64 v = blockIdx.x * (u64)blockDim.x + threadIdx.x; v < n;
          v += (u64)gridDim.x * blockDim.x) {
-        a += (out_off[v + 1] - out_off[v]) > hub;
-        b += (in_off[v + 1] - in_off[v]) > hub;
+        const u64 od = out_off[v + 1] - out_off[v], id = in_off[v + 1] - in_off[v];
+        a += od > hub;
+        b += id > hub;
+        mo = od > mo ? od : mo;
+        mi = id > mi ? id : mi;
     }
+    u32 mo32 = (u32)(mo > 0xFFFFFFFFull ? 0xFFFFFFFFull : mo);
+    u32 mi32 = (u32)(mi > 0xFFFFFFFFull ? 0xFFFFFFFFull : mi);
     for (u32 d = 16; d >= 1; d >>= 1) {
         a += __shfl_xor_sync(kFull, a, d);
         b += __shfl_xor_sync(kFull, b, d);
+        mo32 = max(mo32, __shfl_xor_sync(kFull, mo32, d));
+        mi32 = max(mi32, __shfl_xor_sync(kFull, mi32, d));
     }
     if ((threadIdx.x & 31u) == 0) {
         if (a) atomicAdd(&cnt[0], a);
         if (b) atomicAdd(&cnt[1], b);
+        if (mo32) atomicMax(&cnt[2], mo32);
+        if (mi32) atomicMax(&cnt[3], mi32);
     }
 }
 

@@ -7,6 +7,8 @@ import os
 import subprocess
 import sys
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -35,16 +37,29 @@ def test_traffic_withheld_when_the_kernels_changed(tmp_path, monkeypatch):
     sha = bench.kernel_source_sha256()
     prof = tmp_path / "profiles"
     prof.mkdir()
-    (prof / "k_cupdate_x.md").write_text(
-        f"kernel_source_sha256: {sha}\ntraffic_bytes_per_launch: 123\n")
-    (prof / "k_relax_x.md").write_text(
-        "kernel_source_sha256: 00\ntraffic_bytes_per_launch: 456\n")
+    (prof / "traffic.json").write_text(json.dumps({
+        "k_cupdate/x": {"kernel_source_sha256": sha, "traffic_bytes_per_launch": 123,
+                        "how": "ncu"},
+        "k_relax/x": {"kernel_source_sha256": "00", "traffic_bytes_per_launch": 456}}))
     (tmp_path / "paper_1812_10499_gb300").symlink_to(os.path.join(ROOT, "paper_1812_10499_gb300"))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.measured_traffic("k_cupdate", "x")[0] == 123.0
     t, why = bench.measured_traffic("k_relax", "x")
     assert t is None and "stale" in why
     assert bench.measured_traffic("k_cupdate", "missing") == (None, None)
+
+
+def test_committed_traffic_record_is_machine_readable():
+    """profiles/traffic.json: one entry per kernel/workload, each with the
+    sources' hash, the DRAM bytes per launch and the command that made it."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    entries = json.load(open(path))
+    assert entries
+    for k, e in entries.items():
+        assert "/" in k
+        assert len(e["kernel_source_sha256"]) == 64
+        assert e["traffic_bytes_per_launch"] > 0
+        assert "ncu" in e["command"] and "--clock-control none" in e["command"]
 
 
 def test_algorithmic_bytes_per_unit():
@@ -97,3 +112,9 @@ def test_cpu_baseline_legs():
     tasks += [("rmat", 10, 3, s) for s in (0, 1)]
     qps, done, busy, cores = bench.cpu_queries_per_s(tasks, 120.0, cores=2)
     assert done == 8 and cores == 2 and busy > 0 and qps > 0
+    res, cores = bench.oracle_sample(tasks[:3], cores=2)
+    assert cores == 2 and len(res) == 3
+    import oracle
+    for (secs, d, r), (_, n, gseed, s) in zip(res, tasks[:3]):
+        ref = oracle.round_r(gg.random_var_graph(n, 4, 16, 1, 1000, gseed), s)
+        assert secs > 0 and np.array_equal(d, ref.dist) and r == ref.rounds

@@ -112,14 +112,18 @@ def test_batch_device(sssp_lib):
             P.sssp_destroy(h)
 
 
-def test_serve_alone_and_in_the_mix(sssp_lib):
+@pytest.mark.parametrize("manual", [False, True], ids=["thread", "manual"])
+def test_serve_alone_and_in_the_mix(sssp_lib, manual):
     """Queries submitted while others run are admitted as slots free up; each
-    result equals the oracle's and the query's solve on its own."""
+    result equals the oracle's and the query's solve on its own, and at least
+    two queries shared the device in one server step.  Both with the server
+    thread and with the client driving the steps."""
     P = sssp_lib
     graphs, srcs = batch_graphs(16, 11, nmin=500, nmax=30000)
     hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w) for g in graphs]
     refs = [oracle.round_r(g, s) for g, s in zip(graphs, srcs)]
-    server = P.sssp_serve_open(budget_bytes=64 << 20, max_slots=4, rounds_per_step=3)
+    server = P.sssp_serve_open(budget_bytes=64 << 20, max_slots=4, rounds_per_step=3,
+                               flags=P.SSSP_SERVE_MANUAL if manual else 0)
     try:
         outs, tickets = {}, {}
         order = [int(i) for i in np.argsort(gg.uniform(11, 50, len(hs), 0, 1 << 30))]
@@ -142,6 +146,11 @@ def test_serve_alone_and_in_the_mix(sssp_lib):
                 st, r = P.sssp_serve_poll(server, tickets[j])
                 assert st == P.SSSP_OK
                 done[j] = r
+        stats = P.sssp_serve_stats_get(server)
+        assert stats["submitted"] == stats["completed"] == len(hs)
+        assert stats["queued"] == 0 and stats["inflight"] == 0
+        assert stats["layout"] == P.SSSP_LAYOUT_COMPACT
+        assert stats["max_inflight"] >= 2, stats        # queries overlapped on the device
         for i in range(len(hs)):
             assert np.array_equal(outs[i], refs[i].dist), f"query {i}"
             assert done[i] == refs[i].rounds
@@ -149,6 +158,76 @@ def test_serve_alone_and_in_the_mix(sssp_lib):
             assert np.array_equal(alone, outs[i]) and r_alone == done[i]
     finally:
         P.sssp_serve_close(server)
+        for h in hs:
+            P.sssp_destroy(h)
+
+
+def test_serve_progress_without_the_client(sssp_lib):
+    """The server thread runs the steps: a client that submits and then does
+    nothing finds every query complete, with its timing, and the steps in
+    which queries ran together."""
+    import time
+    P = sssp_lib
+    graphs, srcs = batch_graphs(8, 12, nmin=2000, nmax=20000)
+    hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w) for g in graphs]
+    server = P.sssp_serve_open(budget_bytes=256 << 20, max_slots=8, rounds_per_step=4)
+    try:
+        outs = [np.zeros(g.n, dtype=np.uint64) for g in graphs]
+        tickets = [P.sssp_serve_submit(server, h, s, o) for h, s, o in zip(hs, srcs, outs)]
+        t0 = time.perf_counter()
+        while P.sssp_serve_stats_get(server)["completed"] < len(hs):
+            assert time.perf_counter() - t0 < 60
+            time.sleep(0.05)                            # no poll, no wait, no drain
+        assert P.sssp_serve_stats_get(server)["max_inflight"] >= 2
+        for g, s, h, o, t in zip(graphs, srcs, hs, outs, tickets):
+            ref = oracle.round_r(g, s)
+            assert np.array_equal(o, ref.dist)
+            st, info = P.sssp_serve_wait(server, t, 0)
+            assert st == P.SSSP_OK and info["rounds"] == ref.rounds
+            assert info["submit_ns"] <= info["admit_ns"] <= info["done_ns"]
+            assert 1 <= info["first_step"] <= info["last_step"]
+            with pytest.raises(P.SsspError) as e:      # the ticket was released
+                P.sssp_serve_poll(server, t)
+            assert e.value.code == P.SSSP_E_NOT_FOUND
+        # wait() blocks until a later query completes
+        o = np.zeros(graphs[0].n, dtype=np.uint64)
+        t = P.sssp_serve_submit(server, hs[0], srcs[0], o)
+        st, info = P.sssp_serve_wait(server, t, 30000)
+        assert st == P.SSSP_OK and np.array_equal(o, outs[0])
+    finally:
+        P.sssp_serve_close(server)
+        for h in hs:
+            P.sssp_destroy(h)
+
+
+def test_serve_wide_records(sssp_lib):
+    """A graph whose distances need more than 31 bits is refused by a server
+    on 16-byte records and served, bit-exactly, by one on 32-byte records
+    together with ordinary graphs."""
+    P = sssp_lib
+    big = gg.random_graph(3000, 6, 1 << 19, (1 << 20) - 1, 8)
+    graphs, srcs = batch_graphs(4, 13, nmax=5000)
+    graphs.append(big)
+    srcs.append(0)
+    hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w) for g in graphs]
+    compact = P.sssp_serve_open(budget_bytes=32 << 20, max_slots=4)
+    wide = P.sssp_serve_open(budget_bytes=32 << 20, max_slots=4, flags=P.SSSP_SERVE_WIDE)
+    try:
+        with pytest.raises(P.SsspError) as e:
+            P.sssp_serve_submit(compact, hs[-1], 0, np.zeros(big.n, dtype=np.uint64))
+        assert e.value.code == P.SSSP_E_OVERFLOW
+        outs = [np.zeros(g.n, dtype=np.uint64) for g in graphs]
+        tickets = [P.sssp_serve_submit(wide, h, s, o) for h, s, o in zip(hs, srcs, outs)]
+        P.sssp_serve_drain(wide)
+        assert P.sssp_serve_stats_get(wide)["layout"] == P.SSSP_LAYOUT_WIDE
+        for g, s, o, t in zip(graphs, srcs, outs, tickets):
+            ref = oracle.round_r(g, s)
+            st, r = P.sssp_serve_poll(wide, t)
+            assert st == P.SSSP_OK and r == ref.rounds
+            assert np.array_equal(o, ref.dist)
+    finally:
+        P.sssp_serve_close(compact)
+        P.sssp_serve_close(wide)
         for h in hs:
             P.sssp_destroy(h)
 

@@ -603,3 +603,43 @@ def test_rmat22_full_size(sssp_lib):
     cand = np.flatnonzero(outdeg > 0)
     s = int(cand[int(gg.uniform(1812_10499 + 1, 7, 1, 0, len(cand) - 1)[0])])
     assert_parity(sssp_lib, g, s)
+
+
+@pytest.mark.parametrize("loop", ["graph", "host", "persistent"])
+def test_profiled_solve_splits_the_work_by_kernel(sssp_lib, loop):
+    """A profiled solve launches the round kernels from the host in the loop
+    mode's own schedule (the device loop: k_relax, k_cupdate, then the
+    cluster tail kernel): its results are bit-exact, and the work counters
+    it attributes to the kernels add up to the solve's counters."""
+    P = sssp_lib
+    lm = {"graph": P.SSSP_LOOP_GRAPH, "host": P.SSSP_LOOP_HOST,
+          "persistent": P.SSSP_LOOP_PERSISTENT}[loop]
+    g = gg.rmat(14, 16, 1, 255, 17)
+    s = int(np.argmax(g.out_degree()))
+    ref = oracle.round_r(g, s)
+    h = P.sssp_create(g.n, g.row_ptr, g.col, g.w, options=make_opts(P, loop_mode=lm))
+    try:
+        P.sssp_profile(h, True)
+        out = P.sssp_solve_ex(h, s, parent=True, fixed_round=True, lower=True)
+        prof = P.sssp_profile(h, False)
+        relax, cup, tail, tail_rounds = P.sssp_profile_rounds(h)
+    finally:
+        P.sssp_destroy(h)
+    for k, v in (("dist", ref.dist), ("parent", ref.parent), ("fixed_round", ref.fixed_round),
+                 ("lower", ref.C)):
+        assert np.array_equal(out[k], v), k
+    info = out["info"]
+    assert info["rounds"] == ref.rounds
+    for k in ("out_scanned", "in_scanned", "active_visits", "front_visits"):
+        assert prof["grid_counters"][k] + prof["tail_counters"][k] == info[k] == ref.stats[k], k
+    n_it = len(cup)
+    assert prof["cupdate_launches"] == prof["relax_launches"] == n_it
+    if loop == "graph":
+        # every iteration's k_cupdate closes one round, k_tail the rounds after it
+        assert prof["tail_launches"] == n_it and int(tail_rounds.sum()) == prof["tail_rounds"]
+        assert n_it + prof["tail_rounds"] == ref.rounds
+        assert prof["tail_rounds"] > 0 and prof["tail_counters"]["in_scanned"] > 0
+        assert info["kernel_launches"] == 4 + 3 * n_it
+    else:
+        assert n_it == ref.rounds and prof["tail_launches"] == 0
+        assert prof["tail_counters"] == {k: 0 for k in prof["tail_counters"]}
