@@ -212,12 +212,14 @@ def kernel_source_sha256():
     return h.hexdigest()
 
 
-def measured_traffic(kernel, config):
+def measured_traffic(kernel, config, bytes_per_launch=None):
     """DRAM bytes per launch of `kernel` on workload `config`, from the
     machine-readable record of the committed ncu captures
     (profiles/traffic.json), or None when there is none or the kernel
     sources have changed since it was captured (each entry records the
-    sources' sha256)."""
+    sources' sha256).  An entry holds either the bytes per launch itself or
+    the DRAM bytes per algorithmic byte of a few captured launches, which is
+    then scaled to a launch of this run by its algorithmic bytes."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -225,10 +227,18 @@ def measured_traffic(kernel, config):
     except (OSError, ValueError):
         return None, None
     e = entries.get(f"{kernel}/{config}")
-    if not e or "traffic_bytes_per_launch" not in e:
+    if not e or ("traffic_bytes_per_launch" not in e and "dram_per_algorithmic_byte" not in e):
         return None, None
     if e.get("kernel_source_sha256") != kernel_source_sha256():
         return None, f"profiles/traffic.json {kernel}/{config} is stale (kernel source changed)"
+    if "dram_per_algorithmic_byte" in e:
+        if bytes_per_launch is None:
+            return None, None
+        r = float(e["dram_per_algorithmic_byte"])
+        return r * bytes_per_launch, (
+            f"profiles/traffic.json {kernel}/{config}: {e.get('how', 'ncu dram__bytes')}; "
+            f"DRAM bytes per algorithmic byte {r:.4f} times this run's algorithmic bytes per "
+            f"launch")
     return float(e["traffic_bytes_per_launch"]), (
         f"profiles/traffic.json {kernel}/{config}: {e.get('how', 'ncu dram__bytes')}")
 
@@ -538,7 +548,7 @@ def run_ours(args):
                   "the timed solves run them; algorithmic bytes from the work counters of the "
                   "rounds each kernel ran")
     dom_gbs = bytes_per_launch / (ms_per_launch * 1e-3) / 1e9
-    traffic, traffic_src = measured_traffic(kernel, args.config)
+    traffic, traffic_src = measured_traffic(kernel, args.config, bytes_per_launch)
     # Whole step: all algorithmic bytes of the 8 solves over the timed step.
     step_gbs = step_bytes / (ms_local / args.steps * 1e-3) / 1e9
 
@@ -592,7 +602,11 @@ def run_ours(args):
                          "relax_ms": [round(float(x), 4) for x in per_iter[0]],
                          "cupdate_ms": [round(float(x), 4) for x in per_iter[1]],
                          "tail_ms": [round(float(x), 4) for x in per_iter[2]],
-                         "tail_rounds": [int(x) for x in per_iter[3]]}},
+                         "tail_rounds": [int(x) for x in per_iter[3]],
+                         "relax_bytes": [int(B_OUT_EDGE * c[0] + B_FRONT * c[3])
+                                         for c in per_iter[4]],
+                         "cupdate_bytes": [int(B_IN_EDGE * c[1] + B_ACTIVE * c[2])
+                                           for c in per_iter[4]]}},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(sources),
                 "d2h_bytes_per_step": 8 * g.n * len(sources)},

@@ -443,11 +443,15 @@ int sssp_profile(sssp_handle h, int enable, sssp_kernel_profile* out);
 /* Per-iteration event times of the most recent profiled solve (iterations
  * of the device loop, or rounds with SSSP_LOOP_HOST): iteration i's
  * k_relax / k_cupdate / k_tail milliseconds go to relax_ms[i] /
- * cupdate_ms[i] / tail_ms[i] and the rounds k_tail finished to
- * tail_rounds[i], for i < cap (tail_ms and tail_rounds nullable); *count
- * receives the number of iterations recorded.  Errors: SSSP_E_INVAL. */
+ * cupdate_ms[i] / tail_ms[i], the rounds k_tail finished to tail_rounds[i],
+ * and (device-loop schedule only, else 0) the work counters of its k_relax
+ * and k_cupdate -- out_scanned, in_scanned, active_visits, front_visits --
+ * to grid_counters[4i .. 4i+3], for i < cap (tail_ms, tail_rounds and
+ * grid_counters nullable); *count receives the number of iterations
+ * recorded.  Errors: SSSP_E_INVAL. */
 int sssp_profile_rounds(sssp_handle h, float* relax_ms, float* cupdate_ms, float* tail_ms,
-                        uint32_t* tail_rounds, uint32_t cap, uint32_t* count);
+                        uint32_t* tail_rounds, uint64_t* grid_counters, uint32_t cap,
+                        uint32_t* count);
 
 /* Single-source solve that allocates nothing.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory

@@ -191,7 +191,7 @@ def load(path: str = LIB_PATH):
         "sssp_serve_drain": (c_int, [vp]),
         "sssp_serve_close": (None, [vp]),
         "sssp_profile": (c_int, [vp, c_int, ctypes.POINTER(sssp_kernel_profile)]),
-        "sssp_profile_rounds": (c_int, [vp, vp, vp, vp, vp, u32, ctypes.POINTER(u32)]),
+        "sssp_profile_rounds": (c_int, [vp, vp, vp, vp, vp, vp, u32, ctypes.POINTER(u32)]),
         "sssp_solve_noalloc": (c_int, [u32, vp, vp, vp, vp, u32, u32, vp,
                                        ctypes.POINTER(u32), vp]),
         "sssp_get_tuning": (c_int, [vp, ctypes.POINTER(sssp_tuning)]),
@@ -331,20 +331,24 @@ def sssp_profile(h: int, enable: bool) -> dict:
 
 
 def sssp_profile_rounds(h: int):
-    """Per-iteration (relax_ms, cupdate_ms, tail_ms, tail_rounds) arrays of
-    the last profiled solve."""
+    """Per-iteration (relax_ms, cupdate_ms, tail_ms, tail_rounds, counters)
+    arrays of the last profiled solve; counters is u64[iterations, 4]:
+    out_scanned, in_scanned, active_visits, front_visits of the iteration's
+    k_relax and k_cupdate (device-loop schedule only)."""
     lib = load()
     cnt = ctypes.c_uint32(0)
-    _check(lib.sssp_profile_rounds(h, None, None, None, None, 0, ctypes.byref(cnt)),
+    _check(lib.sssp_profile_rounds(h, None, None, None, None, None, 0, ctypes.byref(cnt)),
            "sssp_profile_rounds")
     r = np.zeros(cnt.value, dtype=np.float32)
     c = np.zeros(cnt.value, dtype=np.float32)
     t = np.zeros(cnt.value, dtype=np.float32)
     tr = np.zeros(cnt.value, dtype=np.uint32)
+    ctr = np.zeros((cnt.value, 4), dtype=np.uint64)
     _check(lib.sssp_profile_rounds(h, r.ctypes.data, c.ctypes.data, t.ctypes.data,
-                                   tr.ctypes.data, cnt.value, ctypes.byref(cnt)),
+                                   tr.ctypes.data, ctr.ctypes.data, cnt.value,
+                                   ctypes.byref(cnt)),
            "sssp_profile_rounds")
-    return r, c, t, tr
+    return r, c, t, tr, ctr
 
 
 def sssp_solve_noalloc(n: int, out_off, out_adj, in_off, in_adj, source: int, max_weight: int,

@@ -224,6 +224,7 @@ int profile_graph_schedule(Context& c, cudaStream_t st) {
     c.prof_round_cup.clear();
     c.prof_round_tail.clear();
     c.prof_round_tail_rounds.clear();
+    c.prof_round_ctr.clear();
     while (prev.status == kRunning && prev.round <= prev.stop_round) {
         CK(cudaEventRecord(c.ev[0], st));
         CK(cudaLaunchKernelExC(&rcfg, fr, args));
@@ -245,6 +246,7 @@ int profile_graph_schedule(Context& c, cudaStream_t st) {
         for (int i = 0; i < 4; ++i) {
             c.prof_grid_ctr[i] += A.stats[i] - prev.stats[i];
             c.prof_tail_ctr[i] += B.stats[i] - A.stats[i];
+            c.prof_round_ctr.push_back(A.stats[i] - prev.stats[i]);
         }
         const u32 tr = B.round - A.round;
         c.prof_relax_ms += a;
@@ -308,6 +310,7 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
             c.prof_round_cup.clear();
             c.prof_round_tail.clear();
             c.prof_round_tail_rounds.clear();
+            c.prof_round_ctr.clear();
             for (u32 i = 0; i < rounds; ++i) {
                 const float a = (float)((t[2 * i + 1] - t[2 * i]) * 1e-6);
                 const float b = (float)((t[2 * i + 2] - t[2 * i + 1]) * 1e-6);
@@ -315,6 +318,7 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
                 c.prof_round_cup.push_back(b);
                 c.prof_round_tail.push_back(0.f);
                 c.prof_round_tail_rounds.push_back(0);
+                c.prof_round_ctr.insert(c.prof_round_ctr.end(), 4, 0ull);
                 c.prof_relax_ms += a;
                 c.prof_cup_ms += b;
             }
@@ -350,6 +354,7 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
         c.prof_round_cup.clear();
         c.prof_round_tail.clear();
         c.prof_round_tail_rounds.clear();
+        c.prof_round_ctr.clear();
     }
     const Ctl start_ctl = *c.h_ctl;
     for (;;) {
@@ -374,6 +379,7 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
                 c.prof_round_cup.push_back(b);
                 c.prof_round_tail.push_back(0.f);
                 c.prof_round_tail_rounds.push_back(0);
+                c.prof_round_ctr.insert(c.prof_round_ctr.end(), 4, 0ull);
             }
             c.prof_relax_n += ran;
             c.prof_cup_n += ran;
@@ -1260,7 +1266,8 @@ int sssp_profile(sssp_handle h, int enable, sssp_kernel_profile* out) {
 }
 
 int sssp_profile_rounds(sssp_handle h, float* relax_ms, float* cupdate_ms, float* tail_ms,
-                        uint32_t* tail_rounds, uint32_t cap, uint32_t* count) {
+                        uint32_t* tail_rounds, uint64_t* grid_counters, uint32_t cap,
+                        uint32_t* count) {
     if (!h || !count || (cap && (!relax_ms || !cupdate_ms))) return SSSP_E_INVAL;
     std::lock_guard<std::mutex> lk(h->mu);
     const Context& c = h->single;
@@ -1270,6 +1277,8 @@ int sssp_profile_rounds(sssp_handle h, float* relax_ms, float* cupdate_ms, float
         cupdate_ms[i] = c.prof_round_cup[i];
         if (tail_ms) tail_ms[i] = c.prof_round_tail[i];
         if (tail_rounds) tail_rounds[i] = c.prof_round_tail_rounds[i];
+        if (grid_counters)
+            for (u32 k = 0; k < 4; ++k) grid_counters[4 * i + k] = c.prof_round_ctr[4 * i + k];
     }
     *count = n;
     return SSSP_OK;

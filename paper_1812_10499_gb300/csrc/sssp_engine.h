@@ -170,6 +170,8 @@ struct Context {
     // one round each).
     std::vector<float> prof_round_relax, prof_round_cup, prof_round_tail;
     std::vector<u32> prof_round_tail_rounds;
+    std::vector<u64> prof_round_ctr;   // per iteration: the 4 work counters of k_relax +
+                                       // k_cupdate (device-loop schedule; 0 otherwise)
     Ctl* h_snap = nullptr;           // pinned control-block snapshots (graph-schedule profile)
     cudaAccessPolicyWindow l2win{};  // L2 window over the records (num_bytes 0: none)
     u64* trace = nullptr;            // device trace of the persistent kernel

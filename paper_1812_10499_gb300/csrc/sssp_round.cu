@@ -1096,10 +1096,16 @@ __device__ void cup_hub(const RoundParams& P, WarpStage<typename L::CSlot>& st, 
     if (lane != 0) return;
     a.edges += n;
     atomicMin(&P.L.hubmin[lo], val);
-    __threadfence();
-    if (atomicAdd(&P.L.hubcnt[lo], 1u) != nch - 1) return;
+    // The arrival count is an acquire-release atomic: it publishes this
+    // chunk's minimum and, for the last arrival, makes every other chunk's
+    // minimum visible before the vertex is finished.
+    u32 arrived;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;\n"
+                 : "=r"(arrived)
+                 : "l"(&P.L.hubcnt[lo])
+                 : "memory");
+    if (arrived != nch - 1) return;
     // Last chunk of this hub: finish the vertex.
-    __threadfence();
     const u64 m = atomicExch(&P.L.hubmin[lo], kInf64);
     P.L.hubcnt[lo] = 0;
     typename L::Rec* ry = L::rec(P) + g;

@@ -40,13 +40,17 @@ def test_traffic_withheld_when_the_kernels_changed(tmp_path, monkeypatch):
     (prof / "traffic.json").write_text(json.dumps({
         "k_cupdate/x": {"kernel_source_sha256": sha, "traffic_bytes_per_launch": 123,
                         "how": "ncu"},
-        "k_relax/x": {"kernel_source_sha256": "00", "traffic_bytes_per_launch": 456}}))
+        "k_relax/x": {"kernel_source_sha256": "00", "traffic_bytes_per_launch": 456},
+        "k_tail/x": {"kernel_source_sha256": sha, "dram_per_algorithmic_byte": 1.25}}))
     (tmp_path / "paper_1812_10499_gb300").symlink_to(os.path.join(ROOT, "paper_1812_10499_gb300"))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.measured_traffic("k_cupdate", "x")[0] == 123.0
     t, why = bench.measured_traffic("k_relax", "x")
     assert t is None and "stale" in why
     assert bench.measured_traffic("k_cupdate", "missing") == (None, None)
+    # a ratio of captured launches is scaled by this run's bytes per launch
+    assert bench.measured_traffic("k_tail", "x", 1000.0)[0] == 1250.0
+    assert bench.measured_traffic("k_tail", "x")[0] is None
 
 
 def test_committed_traffic_record_is_machine_readable():
@@ -58,7 +62,7 @@ def test_committed_traffic_record_is_machine_readable():
     for k, e in entries.items():
         assert "/" in k
         assert len(e["kernel_source_sha256"]) == 64
-        assert e["traffic_bytes_per_launch"] > 0
+        assert e.get("traffic_bytes_per_launch", 0) > 0 or e["dram_per_algorithmic_byte"] > 0
         assert "ncu" in e["command"] and "--clock-control none" in e["command"]
 
 

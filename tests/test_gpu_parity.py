@@ -622,7 +622,7 @@ def test_profiled_solve_splits_the_work_by_kernel(sssp_lib, loop):
         P.sssp_profile(h, True)
         out = P.sssp_solve_ex(h, s, parent=True, fixed_round=True, lower=True)
         prof = P.sssp_profile(h, False)
-        relax, cup, tail, tail_rounds = P.sssp_profile_rounds(h)
+        relax, cup, tail, tail_rounds, ctr = P.sssp_profile_rounds(h)
     finally:
         P.sssp_destroy(h)
     for k, v in (("dist", ref.dist), ("parent", ref.parent), ("fixed_round", ref.fixed_round),
@@ -640,6 +640,9 @@ def test_profiled_solve_splits_the_work_by_kernel(sssp_lib, loop):
         assert n_it + prof["tail_rounds"] == ref.rounds
         assert prof["tail_rounds"] > 0 and prof["tail_counters"]["in_scanned"] > 0
         assert info["kernel_launches"] == 4 + 3 * n_it
+        # per-iteration counters add up to the grid kernels' totals
+        for j, k in enumerate(("out_scanned", "in_scanned", "active_visits", "front_visits")):
+            assert int(ctr[:, j].sum()) == prof["grid_counters"][k]
     else:
         assert n_it == ref.rounds and prof["tail_launches"] == 0
         assert prof["tail_counters"] == {k: 0 for k in prof["tail_counters"]}
