@@ -122,6 +122,19 @@ def dag(layers: int, width: int, deg: int, maxskip: int, wlo: int, whi: int, see
     return _take(_load().gg_dag(layers, width, deg, maxskip, wlo, whi, seed))
 
 
+def out_tree(n: int, wlo: int, whi: int, seed: int) -> Graph:
+    """Random out-tree rooted at 0: vertex v > 0 has one in-edge, from a
+    uniform vertex with a smaller id; w ~ U[wlo, whi]."""
+    v = np.arange(1, n, dtype=np.uint64)
+    par = uniform(seed, 0, n, 0, 1 << 30)[1:] % v
+    w = uniform(seed, 1, n, wlo, whi)[1:]
+    order = np.argsort(par, kind="stable")
+    row_ptr = np.zeros(n + 1, dtype=np.uint64)
+    np.add.at(row_ptr, par.astype(np.int64) + 1, 1)
+    return Graph(n, np.cumsum(row_ptr, dtype=np.uint64), v[order].astype(np.uint32),
+                 w[order].astype(np.uint32))
+
+
 def uniform(seed: int, stream: int, count: int, lo: int, hi: int) -> np.ndarray:
     out = np.empty(count, dtype=np.uint64)
     if count:

@@ -30,6 +30,7 @@ LABEL_CORRECT = 2
 CHEAP_FIRST = 4
 ALL_UNFIXED = 8
 DELTA = 16
+PRED_COUNT = 32
 
 _STATS = ("out_scanned", "in_scanned", "active_visits", "front_visits", "reached", "max_active")
 

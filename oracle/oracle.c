@@ -301,7 +301,9 @@ int orc_round_delta(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, co
     const int cheap_first = (mode & ORC_CHEAP_FIRST) != 0;
     const int all_unfixed = (mode & ORC_ALL_UNFIXED) != 0;
     const int windowed = (mode & ORC_DELTA) != 0;
+    const int pred_count = (mode & ORC_PRED_COUNT) != 0;
     if (windowed && label_correct) return ORC_EINVAL;
+    if (pred_count && (windowed || label_correct)) return ORC_EINVAL;
     uint64_t m = row_ptr[n];
 
     uint64_t* col_ptr = (uint64_t*)malloc(sizeof(uint64_t) * ((size_t)n + 1));
@@ -321,15 +323,18 @@ int orc_round_delta(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, co
     uint64_t* Cn = (uint64_t*)malloc(sizeof(uint64_t) * n);
     uint64_t* Cu = (uint64_t*)malloc(sizeof(uint64_t) * n);   /* undiscovered (ablation) */
     uint8_t* changed = (uint8_t*)calloc(n, 1);
+    uint64_t* pcnt = (uint64_t*)malloc(sizeof(uint64_t) * n);   /* SP_1 predecessor counts */
     uint32_t* list_mem[4] = {front, front2, act, act2};   /* freed at the end */
     if (!col_ptr || !row || !w_in || !outW || !inW || !par || !C || !fr || !front || !front2 ||
-        !front_d || !act || !act2 || !Cn || !Cu || !changed) {
+        !front_d || !act || !act2 || !Cn || !Cu || !changed || !pcnt) {
         free(col_ptr); free(row); free(w_in); free(outW); free(inW); free(par); free(C); free(fr);
         free(front); free(front2); free(front_d); free(act); free(act2); free(Cn); free(Cu);
-        free(changed);
+        free(changed); free(pcnt);
         return ORC_ENOMEM;
     }
     orc_transpose(n, row_ptr, col, w, col_ptr, row, w_in);
+    /* Every in-edge of y still has to be relaxed by its source. */
+    for (uint32_t y = 0; y < n; ++y) pcnt[y] = col_ptr[y + 1] - col_ptr[y];
 
     /* outWeight[x] = min out-edge weight (Fig. SP_3 / SP_4 declarations);
      * a vertex without out-edges contributes nothing to the threshold. */
@@ -370,6 +375,7 @@ int orc_round_delta(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, co
             st[ORC_ST_OUT_SCANNED] += row_ptr[x + 1] - row_ptr[x];
             for (uint64_t k = row_ptr[x]; k < row_ptr[x + 1]; ++k) {
                 uint32_t y = col[k];
+                pcnt[y]--;                                /* (x, y) is relaxed now */
                 if (fr[y] >= 0) continue;                 /* only unfixed targets */
                 uint64_t nd = dx + w[k];
                 if (nd < D[y] || (nd == D[y] && x < par[y])) {
@@ -397,7 +403,8 @@ int orc_round_delta(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, co
             uint32_t y = act[i];
             uint64_t self = rule_mind ? minD : min_u64(D[y], thr);
             uint64_t best = ORC_INF;
-            if (cheap_first && (D[y] <= sat_add(minD, inW[y]) || D[y] <= thr)) {
+            if ((cheap_first && (D[y] <= sat_add(minD, inW[y]) || D[y] <= thr)) ||
+                (pred_count && pcnt[y] == 0)) {
                 Cn[i] = D[y];            /* fixed without reading the in-edges */
                 continue;
             }
@@ -456,7 +463,7 @@ int orc_round_delta(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, co
 
     free(col_ptr); free(row); free(w_in); free(outW); free(inW); free(par); free(C); free(fr);
     free(list_mem[0]); free(list_mem[1]); free(front_d); free(list_mem[2]); free(list_mem[3]);
-    free(Cn); free(Cu); free(changed);
+    free(Cn); free(Cu); free(changed); free(pcnt);
     return ORC_OK;
 }
 

@@ -50,6 +50,12 @@
                                  Cn[y] = D[y], so only in_scanned changes */
 
 #define ORC_DELTA        16u  /* windowed relaxation (orc_round_delta only): see oracle.c */
+#define ORC_PRED_COUNT   32u  /* SP_1's predecessor counts (Sec. III): count, per vertex, the
+                                 in-edges whose source has not yet relaxed them; an active y
+                                 whose count is 0 (every in-neighbour fixed and relaxed, so
+                                 D[y] is final) is fixed without reading its in-edges.  Eq. (1)
+                                 fixes such a y in the same round, so only in_scanned changes.
+                                 Label-setting only (not with ORC_LABEL_CORRECT or ORC_DELTA) */
 
 /* Per-round statistics written by orc_round (array of ORC_NSTATS u64). */
 #define ORC_ST_OUT_SCANNED   0  /* out-edges scanned in relax steps          */

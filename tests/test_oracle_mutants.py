@@ -56,6 +56,11 @@ MUTANTS = {
                                                 "if (windowed) changed[y] = 0;"),
     "windowed frontier drops fixed vertices": ("if (windowed ? changed[y] : !label_correct)",
                                                "if (windowed ? 0 : !label_correct)"),
+    "pred counts fix one relaxation early": ("(pred_count && pcnt[y] == 0)",
+                                             "(pred_count && pcnt[y] <= 1)"),
+    "pred counts start at the out-degree": (
+        "for (uint32_t y = 0; y < n; ++y) pcnt[y] = col_ptr[y + 1] - col_ptr[y];",
+        "for (uint32_t y = 0; y < n; ++y) pcnt[y] = row_ptr[y + 1] - row_ptr[y];"),
     "heap compares wrong way": ("if (h->key[a] != h->key[b]) return h->key[a] < h->key[b];",
                                 "if (h->key[a] != h->key[b]) return h->key[a] > h->key[b];"),
 }
@@ -97,6 +102,15 @@ def battery(lib):
     reach = depth >= 0
     assert np.array_equal(r.fixed_round[reach], depth[reach])
     assert r.rounds == int(depth.max()) + 1
+    # SP_1's predecessor counts: only the scan count changes; none on a tree.
+    g = gg.rmat(10, 8, 1, 255, 6)
+    s = int(np.argmax(g.out_degree()))
+    a = oracle.round_r(g, s, lib=lib)
+    b = oracle.round_r(g, s, mode=oracle.PRED_COUNT, lib=lib)
+    assert np.array_equal(a.dist, b.dist) and np.array_equal(a.C, b.C)
+    assert np.array_equal(a.fixed_round, b.fixed_round) and a.rounds == b.rounds
+    t = gg.out_tree(300, 1, 50, 3)
+    assert oracle.round_r(t, 0, mode=oracle.PRED_COUNT, lib=lib).stats["in_scanned"] == 0
     g = gg.random_var_graph(200, 1, 6, 1, 30, 3)
     col_ptr, row, w_in = oracle.transpose(g, lib=lib)
     fwd = sorted(pins.edges_of(g))

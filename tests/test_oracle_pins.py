@@ -402,6 +402,50 @@ def test_cheap_rules_first_change_only_the_scan_count(base):
         assert b.stats["in_scanned"] < a.stats["in_scanned"]
 
 
+@pytest.mark.parametrize("base", [oracle.RULE_THR, oracle.RULE_MIND, oracle.CHEAP_FIRST],
+                         ids=["thr", "mind", "cheap"])
+def test_pred_counts_change_only_the_scan_count(base):
+    """SP_1's predecessor counts (Sec. III): a vertex all of whose in-edges
+    have been relaxed by fixed sources has its final D, and Eq. (1) fixes it
+    in that same round; fixing it without reading its in-edges leaves every
+    state, round count and counter but in_scanned unchanged."""
+    for g, s in ((gg.rmat(12, 8, 1, 255, 4), None), (gg.random_var_graph(3000, 1, 9, 1, 60, 8), 2),
+                 (gg.grid(40, 30, 1, 50, 1), 0), (gg.dag(20, 64, 5, 3, 1, 100, 7), 0)):
+        if s is None or g.out_degree()[s] == 0:
+            s = int(np.argmax(g.out_degree()))
+        a = oracle.round_r(g, s, mode=base)
+        b = oracle.round_r(g, s, mode=base | oracle.PRED_COUNT)
+        assert np.array_equal(a.dist, b.dist) and np.array_equal(a.parent, b.parent)
+        assert np.array_equal(a.C, b.C) and np.array_equal(a.fixed_round, b.fixed_round)
+        assert a.rounds == b.rounds
+        for k in ("out_scanned", "active_visits", "front_visits", "reached"):
+            assert a.stats[k] == b.stats[k]
+        assert b.stats["in_scanned"] <= a.stats["in_scanned"]
+
+
+def test_pred_counts_on_an_out_tree():
+    """On an out-tree every discovered vertex's only in-neighbour has been
+    fixed and has relaxed it: with the counts no in-edge is read, without
+    them each reached vertex but the root reads its one in-edge once."""
+    for n, seed in ((50, 1), (2000, 2)):
+        g = gg.out_tree(n, 1, 50, seed)
+        a = oracle.round_r(g, 0)
+        b = oracle.round_r(g, 0, mode=oracle.PRED_COUNT)
+        assert a.stats["reached"] == n
+        assert a.stats["in_scanned"] == n - 1
+        assert b.stats["in_scanned"] == 0
+        assert np.array_equal(a.dist, b.dist) and a.rounds == b.rounds
+        assert np.array_equal(b.dist, oracle.dijkstra(g, 0)[0])
+
+
+def test_pred_counts_refused_with_label_correcting_or_window():
+    g = gg.random_graph(50, 3, 1, 9, 1)
+    for kw in (dict(mode=oracle.PRED_COUNT | oracle.LABEL_CORRECT),
+               dict(mode=oracle.PRED_COUNT, delta=5)):
+        with pytest.raises(Exception):
+            oracle.round_r(g, 0, **kw)
+
+
 # ------------------------------------------- ablation: C for all unfixed vertices
 
 def test_all_unfixed_ablation_is_sound_and_never_slower_in_rounds():
