@@ -47,9 +47,11 @@ INF = np.uint64(0xFFFFFFFFFFFFFFFF)
 # Per-vertex state layout of the round kernels (SSSP_LAYOUT_*).
 LAYOUTS = {"auto": 0, "wide": 1, "compact": 2}
 # Round rule (SSSP_RULE_* bits): threshold clamp, minD clamp, label-correcting,
-# cheaper rules first, windowed relaxation (window width --delta).
+# cheaper rules first, windowed relaxation (window width --delta), SP_1's
+# predecessor counts.
 RULES = {"thr": 0, "mind": 1, "lc": 2, "lc-mind": 3, "thr-cheap": 4, "mind-cheap": 5,
-         "lc-cheap": 6, "thr-win": 16, "mind-win": 17, "thr-cheap-win": 20}
+         "lc-cheap": 6, "thr-win": 16, "mind-win": 17, "thr-cheap-win": 20, "thr-pred": 32,
+         "mind-pred": 33, "thr-cheap-pred": 36}
 
 
 def window_delta(g, delta):
@@ -206,7 +208,7 @@ def kernel_source_sha256():
     sources and launch defaults: layout header, kernels, engine header with the
     default hub and chunk sizes."""
     h = hashlib.sha256()
-    for f in ("sssp_dev.cuh", "sssp_round.cu", "sssp_engine.h"):
+    for f in ("sssp_dev.cuh", "sssp_round.cuh", "sssp_engine.h"):
         text = open(os.path.join(ROOT, "paper_1812_10499_gb300", "csrc", f)).read()
         h.update(_code_only(text).encode())
     return h.hexdigest()

@@ -92,6 +92,18 @@ extern "C" {
  * rounds depend on delta.  Not combinable with SSSP_RULE_LABEL_CORRECTING;
  * not available for the server. */
 #define SSSP_RULE_WINDOWED 16u
+/* Flag OR-ed into the rule: SP_1's predecessor counts (Sec. III).  Each
+ * vertex counts its in-edges that have not yet been relaxed; the relaxation
+ * of an edge into an unfixed vertex decrements the count (one atomic per such
+ * edge).  An active y whose count is 0 -- every in-neighbour is fixed and
+ * has relaxed into y, so D[y] is final -- is fixed without reading its
+ * in-edges.  Eq. (1) fixes such a y in the same round (every term is
+ * D[x] + w >= D[y]), so every output is unchanged; only in_scanned drops.
+ * Combinable with SSSP_RULE_MIND and SSSP_RULE_CHEAP_FIRST; not with
+ * SSSP_RULE_LABEL_CORRECTING or SSSP_RULE_WINDOWED (sssp_create returns
+ * SSSP_E_INVAL); not available for the server.  Costs 4 bytes of device
+ * memory per vertex (per record in a batch). */
+#define SSSP_RULE_PRED_COUNT 32u
 
 /* How the rounds are sequenced.  All modes give identical results. */
 #define SSSP_LOOP_GRAPH      0u  /* two kernels per round in a CUDA graph with a device-side

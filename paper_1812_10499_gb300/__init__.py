@@ -40,6 +40,7 @@ SSSP_RULE_MIND = 1
 SSSP_RULE_LABEL_CORRECTING = 2
 SSSP_RULE_CHEAP_FIRST = 4
 SSSP_RULE_WINDOWED = 16
+SSSP_RULE_PRED_COUNT = 32
 SSSP_LOOP_GRAPH = 0
 SSSP_LOOP_HOST = 1
 SSSP_LOOP_PERSISTENT = 2

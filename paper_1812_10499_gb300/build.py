@@ -15,8 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsssp.so")
-SOURCES = ["sssp_round.cu", "sssp_setup.cu", "sssp_api.cu", "sssp_serve.cu", "sssp_noalloc.cu",
-           "sssp_tune.cu"]
+SOURCES = ["sssp_round.cu", "sssp_round_pred.cu", "sssp_setup.cu", "sssp_api.cu", "sssp_serve.cu",
+           "sssp_noalloc.cu", "sssp_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

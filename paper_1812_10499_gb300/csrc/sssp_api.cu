@@ -119,7 +119,7 @@ int build_loop(Context& c) {
     P.cond = h;
     void* args[] = {&P};
     cudaKernelNodeParams kp{};
-    kp.func = const_cast<void*>(relax_fn(c.multi, c.narrow));
+    kp.func = const_cast<void*>(relax_fn(c.multi, c.narrow, c.P.pcnt != nullptr));
     kp.gridDim = dim3(c.grid);
     kp.blockDim = dim3(kThreads);
     kp.sharedMemBytes = (unsigned)relax_smem_bytes(c.narrow);
@@ -127,14 +127,14 @@ int build_loop(Context& c) {
     cudaGraphNode_t n1, n2;
     e = cudaGraphAddKernelNode(&n1, body, nullptr, 0, &kp);
     if (e == cudaSuccess) {
-        kp.func = const_cast<void*>(cupdate_fn(c.multi, c.narrow));
+        kp.func = const_cast<void*>(cupdate_fn(c.multi, c.narrow, c.P.pcnt != nullptr));
         kp.gridDim = dim3(c.grid_cup);
         kp.sharedMemBytes = (unsigned)cupdate_smem_bytes(c.narrow);
         e = cudaGraphAddKernelNode(&n2, body, &n1, 1, &kp);
     }
     if (e == cudaSuccess && c.tail_ctas) {
         cudaGraphNode_t n3;
-        kp.func = const_cast<void*>(tail_fn(c.multi, c.narrow));
+        kp.func = const_cast<void*>(tail_fn(c.multi, c.narrow, c.P.pcnt != nullptr));
         kp.gridDim = dim3(c.tail_ctas);
         kp.sharedMemBytes = (unsigned)solve_smem_bytes(c.narrow);
         e = cudaGraphAddKernelNode(&n3, body, &n2, 1, &kp);
@@ -178,9 +178,9 @@ int build_loop(Context& c) {
 // around each launch, and snapshots of the control block after k_cupdate and
 // after k_tail that split the work counters by the kernel that did the work.
 int profile_graph_schedule(Context& c, cudaStream_t st) {
-    const void* fr = relax_fn(c.multi, c.narrow);
-    const void* fc = cupdate_fn(c.multi, c.narrow);
-    const void* ft = tail_fn(c.multi, c.narrow);
+    const void* fr = relax_fn(c.multi, c.narrow, c.P.pcnt != nullptr);
+    const void* fc = cupdate_fn(c.multi, c.narrow, c.P.pcnt != nullptr);
+    const void* ft = tail_fn(c.multi, c.narrow, c.P.pcnt != nullptr);
     const size_t smr = relax_smem_bytes(c.narrow), smc = cupdate_smem_bytes(c.narrow);
     RoundParams P = c.P;
     P.cond = 0;
@@ -297,8 +297,9 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
             for (int i = 0; i < 4; ++i) c.prof_grid_ctr[i] -= c.h_ctl->stats[i];
         }
         void* args[] = {&P};
-        CK(cudaLaunchCooperativeKernel(solve_fn(c.multi, c.narrow), dim3(c.grid_solve),
-                                       dim3(kThreads), args, solve_smem_bytes(c.narrow), st));
+        const void* fs = solve_fn(c.multi, c.narrow, c.P.pcnt != nullptr);
+        CK(cudaLaunchCooperativeKernel(fs, dim3(c.grid_solve), dim3(kThreads), args,
+                                       solve_smem_bytes(c.narrow), st));
         if (c.prof) {
             CK(cudaMemcpyAsync(c.h_ctl, c.P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
@@ -336,8 +337,8 @@ int run_loop(Context& c, u32 loop_mode, cudaStream_t st) {
     // profiling, events bracket every launch: ev[3i] | relax | ev[3i+1] |
     // cupdate | ev[3i+2].
     constexpr int kGroup = 16;
-    const void* fr = relax_fn(c.multi, c.narrow);
-    const void* fc = cupdate_fn(c.multi, c.narrow);
+    const void* fr = relax_fn(c.multi, c.narrow, c.P.pcnt != nullptr);
+    const void* fc = cupdate_fn(c.multi, c.narrow, c.P.pcnt != nullptr);
     const size_t smr = relax_smem_bytes(c.narrow), smc = cupdate_smem_bytes(c.narrow);
     RoundParams P = c.P;
     P.cond = 0;
@@ -472,6 +473,10 @@ int init_single_context(sssp_graph* h) {
     P.cheap = (h->opt.rule & SSSP_RULE_CHEAP_FIRST) ? 1u : 0u;
     P.win = (h->opt.rule & SSSP_RULE_WINDOWED) ? 1u : 0u;
     P.delta = h->opt.delta;
+    if (h->opt.rule & SSSP_RULE_PRED_COUNT) {
+        CK(pred_kernels_init());
+        RC(c.pool.get(&P.pcnt, h->n));
+    }
     if (P.lc || P.win) {
         RC(c.pool.get(&P.snap, h->n));
         RC(c.pool.get(&P.chg, h->n));
@@ -767,7 +772,7 @@ int enqueue_single(sssp_graph* h, u32 source, u32 max_rounds, cudaStream_t st, u
     P.g.source = source;
     c.P.g.source = source;
     k_init_records<<<c.grid, kThreads, 0, st>>>(P.rec, P.recn, P.fround, h->outw, h->in_off, h->n,
-                                                P.chg, P.gf, h->outw_pack);
+                                                P.chg, P.gf, h->outw_pack, P.pcnt);
     k_reset_ctl<<<1, 32, 0, st>>>(P.ctl, 1, h->n + 2);
     CK(launch_start(false, c.narrow, P, 0, 1, max_rounds, st, target));
     RC(run_loop(c, h->opt.loop_mode, st));
@@ -824,6 +829,10 @@ int ensure_batch(sssp_graph* h0, u64 nrec, u32 nslots, u32 npages, u64 capH, u64
     P.cheap = (h0->opt.rule & SSSP_RULE_CHEAP_FIRST) ? 1u : 0u;
     P.win = (h0->opt.rule & SSSP_RULE_WINDOWED) ? 1u : 0u;
     P.delta = h0->opt.delta;
+    if (h0->opt.rule & SSSP_RULE_PRED_COUNT) {
+        CK(pred_kernels_init());
+        RC(c->pool.get(&P.pcnt, nrec));
+    }
     if (P.lc || P.win) {
         RC(c->pool.get(&P.snap, nrec));
         RC(c->pool.get(&P.chg, nrec));
@@ -1009,8 +1018,10 @@ int sssp_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t*
     if (o.chunk_edges == 0) o.chunk_edges = kDefaultChunk;
     if (o.block_threads == 0) o.block_threads = kThreads;
     if ((o.rule & ~(SSSP_RULE_MIND | SSSP_RULE_LABEL_CORRECTING | SSSP_RULE_CHEAP_FIRST |
-                    SSSP_RULE_WINDOWED)) != 0 ||
+                    SSSP_RULE_WINDOWED | SSSP_RULE_PRED_COUNT)) != 0 ||
         ((o.rule & SSSP_RULE_LABEL_CORRECTING) && (o.rule & SSSP_RULE_WINDOWED)) ||
+        ((o.rule & SSSP_RULE_PRED_COUNT) &&
+         (o.rule & (SSSP_RULE_LABEL_CORRECTING | SSSP_RULE_WINDOWED))) ||
         o.loop_mode > SSSP_LOOP_PERSISTENT || o.chunk_edges % 32 != 0 ||
         o.layout > SSSP_LAYOUT_COMPACT ||
         o.hub_degree > (1u << 20) || o.chunk_edges > (1u << 20) ||

@@ -154,6 +154,9 @@ struct RoundParams {
                                 // previous round's relaxation
     u32 cheap;                  // 1: fix y without scanning its in-edges when
                                 // D[y] <= minD + inWeight[y] or D[y] <= threshold
+    u32* pcnt;                  // SP_1's predecessor counts (nullable): per record, the
+                                // in-edges not yet relaxed; an active y at 0 is fixed
+                                // without scanning its in-edges
     u32 win;                    // 1: windowed relaxation (Delta-stepping's bucket as a
                                 // window over D): an active vertex whose D changed since
                                 // it last relaxed relaxes while D < minD + delta

@@ -14,11 +14,12 @@
 #include "sssp_dev.cuh"
 
 namespace sssp {
-// narrow: 16-byte records (RoundParams::recn) instead of 32-byte ones (rec).
-const void* relax_fn(bool multi, bool narrow);
-const void* cupdate_fn(bool multi, bool narrow);
-const void* solve_fn(bool multi, bool narrow);
-const void* tail_fn(bool multi, bool narrow);
+// narrow: 16-byte records (RoundParams::recn) instead of 32-byte ones (rec);
+// pred: the kernels with SP_1's predecessor counts (RoundParams::pcnt set).
+const void* relax_fn(bool multi, bool narrow, bool pred);
+const void* cupdate_fn(bool multi, bool narrow, bool pred);
+const void* solve_fn(bool multi, bool narrow, bool pred);
+const void* tail_fn(bool multi, bool narrow, bool pred);
 const void* barrier_selftest_fn();
 u32 tail_cluster_ctas();
 size_t solve_smem_bytes(bool narrow);
@@ -26,13 +27,15 @@ int solve_blocks_per_sm(int threads);
 size_t relax_smem_bytes(bool narrow);
 size_t cupdate_smem_bytes(bool narrow);
 cudaError_t round_kernels_init();
+cudaError_t pred_kernels_init();   // before the first graph with SSSP_RULE_PRED_COUNT
 cudaError_t launch_start(bool multi, bool narrow, const RoundParams& P, u32 first, u32 count,
                          u32 max_rounds, cudaStream_t st, u32 target = kNoTarget);
 int round_blocks_per_sm(int threads);
 int cupdate_blocks_per_sm(int threads);
 __global__ void k_init_records(VRec* rec, VRecN* recn, int* fround, const u32* outw,
                                const u64* in_off, u32 n, u32* chg = nullptr,
-                               uint2* gf = nullptr, const u32* outw_pack = nullptr);
+                               uint2* gf = nullptr, const u32* outw_pack = nullptr,
+                               u32* pcnt = nullptr);
 __global__ void k_init_records_multi(RoundParams P, u64 nrec, u32 first_page, u32 npages);
 __global__ void k_reset_ctl(Ctl* ctl, u32 ninst, u32 round_limit);
 __global__ void k_finalize(const VRec* rec, const VRecN* recn, const int* frec, u64 base, u32 n,

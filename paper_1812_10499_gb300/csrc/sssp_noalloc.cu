@@ -134,7 +134,7 @@ extern "C" int sssp_solve_noalloc(uint32_t n, const uint64_t* out_off, const uin
     if (e == cudaSuccess) e = launch_start(false, narrow, P, 0, 1, 0, st);
     if (e == cudaSuccess) {
         void* args[] = {&P};
-        e = cudaLaunchCooperativeKernel(solve_fn(false, narrow), dim3(grid), dim3(kThreads), args,
+        e = cudaLaunchCooperativeKernel(solve_fn(false, narrow, false), dim3(grid), dim3(kThreads), args,
                                         solve_smem_bytes(narrow), st);
     }
     if (e == cudaSuccess) {

@@ -1,5 +1,7 @@
-// sssp_round.cu -- sm_103a kernels of the SP_3/SP_4 round (Garg, arXiv
-// 1812.10499, Sec. V-VI).
+// sssp_round.cuh -- sm_103a kernels of the SP_3/SP_4 round (Garg, arXiv
+// 1812.10499, Sec. V-VI), as templates.  sssp_round.cu instantiates them for
+// the two state layouts, sssp_round_pred.cu for the same layouts with SP_1's
+// predecessor counts; the two compile in parallel.
 //
 // One round r is two phases:
 //   relax   : SP_4 step 3, label-setting (as SP_3 explores only fixed
@@ -25,7 +27,9 @@
 // adjacency two batches ahead, neighbour states one batch ahead, compute on
 // the current batch.  List appends go through warp-private buffers flushed
 // 32 entries per atomic.  Every kernel is templated on the state layout:
-// 32-byte records (WideL) or 16-byte records (NarrowL).
+// 32-byte records (WideL) or 16-byte records (NarrowL), either of them
+// with predecessor counts (PredL).
+#pragma once
 #include "sssp_dev.cuh"
 
 namespace sssp {
@@ -166,6 +170,7 @@ struct WideL {
     typedef RecSlot RSlot;
     typedef DcSlot CSlot;
     static constexpr bool kNarrow = false;
+    static constexpr bool kPred = false;
     // Eq. (1) term lb(x) + w of one in-edge, clamped to the distance infinity.
     typedef u64 Term;
     typedef Bounds64 Bounds;
@@ -187,6 +192,7 @@ struct NarrowL {
     typedef NSlot RSlot;
     typedef NSlot CSlot;
     static constexpr bool kNarrow = true;
+    static constexpr bool kPred = false;
     // The same term in 32-bit arithmetic.  Here the packed D word holds the
     // distance in its upper half (32 parent bits) and every finite value is
     // below 2^31 - 1, so lb(x) <= kInf31 and lb(x) + w cannot wrap.  Terms are
@@ -215,6 +221,16 @@ struct NarrowL {
         return make_ulonglong2(v.x, widen_c((u32)(v.y >> (32 * cur))));
     }
     __device__ static void set_c(Rec* p, u32 slot, u64 c) { p->cf[slot] = narrow_c(c); }
+};
+
+// A layout with SP_1's predecessor counts (Sec. III): the relaxation
+// decrements the count of every unfixed target, and the lower-bound phase
+// fixes an active vertex whose count is 0 without reading its in-edges.
+// The counting kernels are separate instantiations (compiled in their own
+// translation unit), so the default kernels carry none of it.
+template <class Base>
+struct PredL : Base {
+    static constexpr bool kPred = true;
 };
 
 // Shared-memory pipeline of one warp: adjacency of three batches and
@@ -417,16 +433,14 @@ __device__ __forceinline__ const InstDesc& desc_of(const RoundParams& P, u32 g, 
 }
 
 // outWeight of local vertex v: from the record (wide) or the graph (compact).
-template <class L>
-__device__ __forceinline__ u32 outw_of(const InstDesc& d, const typename L::Rec* r, u32 v);
-template <>
-__device__ __forceinline__ u32 outw_of<WideL>(const InstDesc&, const VRec* r, u32) {
-    return r->outw;
-}
-template <>
-__device__ __forceinline__ u32 outw_of<NarrowL>(const InstDesc& d, const VRecN*, u32 v) {
+__device__ __forceinline__ u32 outw_rec(const InstDesc&, const VRec* r, u32) { return r->outw; }
+__device__ __forceinline__ u32 outw_rec(const InstDesc& d, const VRecN*, u32 v) {
     const u32 ow = d.outw[v] & kInf31;            // bit 31: in-hub flag
     return ow == kInf31 ? kNoOutW : ow;
+}
+template <class L>
+__device__ __forceinline__ u32 outw_of(const InstDesc& d, const typename L::Rec* r, u32 v) {
+    return outw_rec(d, r, v);
 }
 
 // ------------------------------------------------------------- pipeline
@@ -622,6 +636,8 @@ __device__ __forceinline__ void relax_issue(const RoundParams& P,
             // Filter word: bound 0 (fixed) rejects every candidate, a larger
             // distance cannot lower D; an equal one may (smaller parent).
             const uint2 fw = *reinterpret_cast<const uint2*>(&v);
+            // SP_1's predecessor count: this edge into an unfixed y is relaxed.
+            if (L::kPred && fw.x != 0u) atomicSub(&P.pcnt[pd.gy[i]], 1u);
             if (dd <= fw.x) {
                 pd.cand[i] = cand;
                 if (fw.x == kRelaxUnseen) pd.old[i] = atomicMin(&rec[pd.gy[i]].dp, cand);
@@ -631,6 +647,7 @@ __device__ __forceinline__ void relax_issue(const RoundParams& P,
             a.edges++;
             continue;
         }
+        if (L::kPred && !v.fixed(cur)) atomicSub(&P.pcnt[pd.gy[i]], 1u);
         if (!v.fixed(cur) && cand < v.d()) {
             pd.cand[i] = cand;
             // Windowed: D[y] changes this round (it ends at most cand, below the
@@ -947,7 +964,7 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
     const bool valid = idx < nas;
     u32 g = 0, yloc = 0, inst = 0, deg = 0, outw = kNoOutW;
     u64 gbase = 0, ib = 0, dy = 0, cy = 0, thr = thr0, minD = minD0, odeg = 0;
-    bool cheap_fix = false;
+    bool fix_now = false;
     const uint2* in_adj = P.g.in_adj;
     typename L::Rec* rec = L::rec(P);
     if (valid) {
@@ -968,10 +985,10 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
         dy = v.x >> P.vbits;
         cy = v.y & kCMask;
         outw = outw_of<L>(d, rec + g, yloc);
-        if (P.cheap) {
-            cheap_fix = cheap_rules_fix(dy, d.inw[yloc], thr, minD);
-            if (cheap_fix) deg = 0;                 // its in-edges are not read
-        }
+        if (P.cheap) fix_now = cheap_rules_fix(dy, d.inw[yloc], thr, minD);
+        // SP_1: every in-edge relaxed by a fixed source, so D[y] is final.
+        if (L::kPred && !fix_now) fix_now = P.pcnt[g] == 0u;
+        if (fix_now) deg = 0;                     // its in-edges are not read
     }
     smin[lane] = kInf64;
     const typename L::Bounds bd = L::bounds(thr, minD);
@@ -1013,7 +1030,7 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
     bool fix = false;
     if (valid) {
         u64 cn = dy;
-        if (cheap_fix) fix = true;
+        if (fix_now) fix = true;
         else cn = decide(P, dy, cy, smin[lane], thr, minD, fix);
         L::set_c(rec + g, nxt, cn | (fix ? kFixed : 0ull));
         if (fix) P.fround[g] = (int)r;
@@ -1072,12 +1089,14 @@ __device__ void cup_hub(const RoundParams& P, WarpStage<typename L::CSlot>& st, 
     const u64 ce = umin64(cb + P.chunk, ie);
     const typename L::Bounds bd = L::bounds(thr, minD);
     typename L::Term tv = L::kTermInf;
-    // Cheaper rules first: every chunk of y takes the same decision.
-    bool cheap_fix = false;
+    // Cheaper rules first: every chunk of y takes the same decision (the
+    // predecessor counts do not change during this phase).
+    bool fix_now = false;
     if (P.cheap)
-        cheap_fix = cheap_rules_fix(L::ld_dc(L::rec(P) + g, cur).x >> P.vbits, d.inw[yloc], thr,
-                                    minD);
-    const u32 n = (ce > cb && !cheap_fix) ? (u32)(ce - cb) : 0u;
+        fix_now = cheap_rules_fix(L::ld_dc(L::rec(P) + g, cur).x >> P.vbits, d.inw[yloc], thr,
+                                  minD);
+    if (L::kPred && !fix_now) fix_now = P.pcnt[g] == 0u;
+    const u32 n = (ce > cb && !fix_now) ? (u32)(ce - cb) : 0u;
     run_pipeline(
         (n + kB - 1) / kB,
         [&](u32 b, u32 s) { issue_range_adj(st, s, d.in_adj, cb + b * kB, ce, lane); },
@@ -1115,7 +1134,7 @@ __device__ void cup_hub(const RoundParams& P, WarpStage<typename L::CSlot>& st, 
     const u32 outw = outw_of<L>(d, ry, yloc);
     bool fix = true;
     u64 cn = dy;
-    if (!cheap_fix) cn = decide(P, dy, cy, m, thr, minD, fix);
+    if (!fix_now) cn = decide(P, dy, cy, m, thr, minD, fix);
     L::set_c(ry, nxt, cn | (fix ? kFixed : 0ull));
     if (L::kNarrow && P.gf) P.gf[g].x = fix ? 0u : (u32)dy;
     a.visits++;
@@ -1154,7 +1173,7 @@ __device__ __forceinline__ bool has_next(const RoundParams& P, const InstVar* v,
 
 // End of round r, run by the last CTA: retire finished queries, advance the
 // round counter and set the device loop's condition.
-__device__ void round_epilogue(const RoundParams& P, u32 r) {
+__device__ inline void round_epilogue(const RoundParams& P, u32 r) {
     __shared__ u32 s_running;
     Ctl* ctl = P.ctl;
     const u32 nxt = (r & 1u) ^ 1u;
@@ -1335,7 +1354,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-__device__ bool grid_barrier(const RoundParams& P, bool epilogue, u32 r) {
+__device__ inline bool grid_barrier(const RoundParams& P, bool epilogue, u32 r) {
     __shared__ u32 s_last, s_gen;
     Ctl* ctl = P.ctl;
     const unsigned long long lim = P.barrier_ns ? P.barrier_ns : kBarrierTimeoutNs;
@@ -1369,13 +1388,6 @@ __device__ bool grid_barrier(const RoundParams& P, bool epilogue, u32 r) {
     }
     __syncthreads();
     return (ld_volatile(&ctl->error) & 4u) == 0;
-}
-
-// Self-test of the barrier's wait limit: CTA `absent` never arrives, so the
-// others must give up after P.barrier_ns, set ctl->error bit 4 and return.
-__global__ void k_barrier_selftest(RoundParams P, u32 absent) {
-    if (blockIdx.x == absent) return;
-    grid_barrier(P, false, 0);
 }
 
 // All rounds of the running queries in one launch: relax phase, barrier,
@@ -1577,143 +1589,32 @@ __global__ void k_start(RoundParams P, u32 first, u32 count, u32 max_rounds, u32
 
 // ----------------------------------------------- host access for the engine
 
-const void* relax_fn(bool multi, bool narrow) {
-    if (multi) return narrow ? (const void*)k_relax<true, NarrowL> : (const void*)k_relax<true, WideL>;
-    return narrow ? (const void*)k_relax<false, NarrowL> : (const void*)k_relax<false, WideL>;
-}
-const void* cupdate_fn(bool multi, bool narrow) {
-    if (multi)
-        return narrow ? (const void*)k_cupdate<true, NarrowL> : (const void*)k_cupdate<true, WideL>;
-    return narrow ? (const void*)k_cupdate<false, NarrowL> : (const void*)k_cupdate<false, WideL>;
-}
-const void* solve_fn(bool multi, bool narrow) {
-    if (multi) return narrow ? (const void*)k_solve<true, NarrowL> : (const void*)k_solve<true, WideL>;
-    return narrow ? (const void*)k_solve<false, NarrowL> : (const void*)k_solve<false, WideL>;
-}
-const void* barrier_selftest_fn() { return (const void*)k_barrier_selftest; }
+enum class RoundKernel { kRelax, kCupdate, kSolve, kTail };
 
-const void* tail_fn(bool multi, bool narrow) {
-    if (multi) return narrow ? (const void*)k_tail<true, NarrowL> : (const void*)k_tail<true, WideL>;
-    return narrow ? (const void*)k_tail<false, NarrowL> : (const void*)k_tail<false, WideL>;
-}
-size_t relax_smem_bytes(bool narrow) {
-    return narrow ? relax_smem<NarrowL>() : relax_smem<WideL>();
-}
-size_t cupdate_smem_bytes(bool narrow) {
-    return narrow ? cupdate_smem<NarrowL>() : cupdate_smem<WideL>();
-}
-size_t solve_smem_bytes(bool narrow) {
-    const size_t a = relax_smem_bytes(narrow), b = cupdate_smem_bytes(narrow);
-    return a > b ? a : b;
-}
-
-cudaError_t launch_start(bool multi, bool narrow, const RoundParams& P, u32 first, u32 count,
-                         u32 max_rounds, cudaStream_t st, u32 target) {
-    if (multi) {
-        if (narrow) k_start<true, NarrowL><<<1, 256, 0, st>>>(P, first, count, max_rounds, target);
-        else k_start<true, WideL><<<1, 256, 0, st>>>(P, first, count, max_rounds, target);
-    } else {
-        if (narrow) k_start<false, NarrowL><<<1, 32, 0, st>>>(P, first, count, max_rounds, target);
-        else k_start<false, WideL><<<1, 32, 0, st>>>(P, first, count, max_rounds, target);
+// Address of one round kernel for the layouts W (32-byte records) and N
+// (16-byte records); instantiating this instantiates the kernels, so each
+// translation unit that includes this header does it for its own layouts.
+template <class W, class N>
+const void* round_kernel(RoundKernel k, bool multi, bool narrow) {
+    switch (k) {
+        case RoundKernel::kRelax:
+            if (multi) return narrow ? (const void*)k_relax<true, N> : (const void*)k_relax<true, W>;
+            return narrow ? (const void*)k_relax<false, N> : (const void*)k_relax<false, W>;
+        case RoundKernel::kCupdate:
+            if (multi)
+                return narrow ? (const void*)k_cupdate<true, N> : (const void*)k_cupdate<true, W>;
+            return narrow ? (const void*)k_cupdate<false, N> : (const void*)k_cupdate<false, W>;
+        case RoundKernel::kSolve:
+            if (multi) return narrow ? (const void*)k_solve<true, N> : (const void*)k_solve<true, W>;
+            return narrow ? (const void*)k_solve<false, N> : (const void*)k_solve<false, W>;
+        case RoundKernel::kTail:
+            if (multi) return narrow ? (const void*)k_tail<true, N> : (const void*)k_tail<true, W>;
+            return narrow ? (const void*)k_tail<false, N> : (const void*)k_tail<false, W>;
     }
-    return cudaGetLastError();
+    return nullptr;
 }
 
-// Raises the dynamic shared-memory limit of the round kernels (once per
-// process and device).
-cudaError_t round_kernels_init() {
-    cudaError_t e = cudaSuccess;
-    for (int m = 0; m < 2 && e == cudaSuccess; ++m)
-        for (int nw = 0; nw < 2 && e == cudaSuccess; ++nw) {
-            const bool multi = m, narrow = nw;
-            e = cudaFuncSetAttribute(relax_fn(multi, narrow),
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)relax_smem_bytes(narrow));
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(cupdate_fn(multi, narrow),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)cupdate_smem_bytes(narrow));
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(solve_fn(multi, narrow),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)solve_smem_bytes(narrow));
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(tail_fn(multi, narrow),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)solve_smem_bytes(narrow));
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(tail_fn(multi, narrow),
-                                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        }
-    return e;
-}
-
-// CTAs of the tail kernel's cluster, or 0 when such a cluster cannot be
-// scheduled on the current device (the device loop then runs without it).
-u32 tail_cluster_ctas() {
-    if (round_kernels_init() != cudaSuccess) return 0;
-    for (int m = 0; m < 2; ++m)
-        for (int nw = 0; nw < 2; ++nw) {
-            cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = kTailCTAs;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
-            cfg.gridDim = dim3(kTailCTAs);
-            cfg.blockDim = dim3(256);
-            cfg.dynamicSmemBytes = solve_smem_bytes(nw);
-            cfg.attrs = at;
-            cfg.numAttrs = 1;
-            int nclusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&nclusters, tail_fn(m, nw), &cfg) != cudaSuccess) {
-                (void)cudaGetLastError();
-                return 0;
-            }
-            if (nclusters < 1) return 0;
-        }
-    return kTailCTAs;
-}
-
-// CTAs per SM of the relax kernel (every variant fits), and of the
-// lower-bound kernel, which is compiled for more CTAs per SM.
-int round_blocks_per_sm(int threads) {
-    if (round_kernels_init() != cudaSuccess) return 1;
-    int best = 1 << 30;
-    for (int m = 0; m < 2; ++m)
-        for (int nw = 0; nw < 2; ++nw) {
-            int a = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, relax_fn(m, nw), threads,
-                                                          relax_smem_bytes(nw));
-            best = a < best ? a : best;
-        }
-    return best;
-}
-int cupdate_blocks_per_sm(int threads) {
-    if (round_kernels_init() != cudaSuccess) return 1;
-    int best = 1 << 30;
-    for (int m = 0; m < 2; ++m)
-        for (int nw = 0; nw < 2; ++nw) {
-            int b = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cupdate_fn(m, nw), threads,
-                                                          cupdate_smem_bytes(nw));
-            best = b < best ? b : best;
-        }
-    return best;
-}
-
-// Co-resident CTAs per SM of the persistent kernel (its grid must fit).
-int solve_blocks_per_sm(int threads) {
-    if (round_kernels_init() != cudaSuccess) return 1;
-    int best = 1 << 30;
-    for (int m = 0; m < 2; ++m)
-        for (int nw = 0; nw < 2; ++nw) {
-            int a = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, solve_fn(m, nw), threads,
-                                                          solve_smem_bytes(nw));
-            best = a < best ? a : best;
-        }
-    return best;
-}
+// The kernels of the layouts with predecessor counts (sssp_round_pred.cu).
+const void* pred_round_kernel(RoundKernel k, bool multi, bool narrow);
 
 }  // namespace sssp

@@ -15,10 +15,11 @@ __device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
 // Every record of a single query: D = inf, C = 0 (Fig. SP_4 declarations).
 // Exactly one of rec (32-byte records) and recn (16-byte records) is set.
 // gf (nullable, compact layout): the relaxation filter words, from the
-// packed outWeight words outw_pack.
+// packed outWeight words outw_pack.  pcnt (nullable): SP_1's predecessor
+// counts, each vertex's in-degree (Fig. SP_1 declarations).
 __global__ void k_init_records(VRec* rec, VRecN* recn, int* fround, const u32* outw,
                                const u64* in_off, u32 n, u32* chg, uint2* gf,
-                               const u32* outw_pack) {
+                               const u32* outw_pack, u32* pcnt) {
     for (u64 v = blockIdx.x * (u64)blockDim.x + threadIdx.x; v < n;
          v += (u64)gridDim.x * blockDim.x) {
         if (recn) {
@@ -39,6 +40,7 @@ __global__ void k_init_records(VRec* rec, VRecN* recn, int* fround, const u32* o
         }
         fround[v] = -1;
         if (chg) chg[v] = 0;     // label-correcting change marks (rounds start at 1)
+        if (pcnt) pcnt[v] = (u32)(in_off[v + 1] - in_off[v]);
     }
 }
 
@@ -71,6 +73,7 @@ __global__ void k_init_records_multi(RoundParams P, u64 nrec, u32 first_page, u3
         }
         P.fround[g] = -1;
         if (P.chg) P.chg[g] = 0;
+        if (P.pcnt) P.pcnt[g] = (u32)(d.in_off[v + 1] - d.in_off[v]);
     }
 }
 

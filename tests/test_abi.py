@@ -123,6 +123,10 @@ def test_rule_bits_checked_on_the_host(lib):
     # An unknown bit, and windowed with label-correcting relaxation.
     assert create(8) == -1
     assert create(P.SSSP_RULE_WINDOWED | P.SSSP_RULE_LABEL_CORRECTING, 5) == -1
+    # Predecessor counts are label-setting only.
+    assert create(P.SSSP_RULE_PRED_COUNT | P.SSSP_RULE_LABEL_CORRECTING) == -1
+    assert create(P.SSSP_RULE_PRED_COUNT | P.SSSP_RULE_WINDOWED, 5) == -1
+    assert create(64) == -1
     # The options structure carries the window width after alloc_ctx.
     assert P.sssp_options.delta.offset == P.sssp_options.alloc_ctx.offset + 8
 
@@ -167,6 +171,7 @@ def test_binding_constants_match_the_header():
     for name, val in defs:
         if hasattr(P, name):
             assert getattr(P, name) == int(val), name
-    for name in ("SSSP_E_INVAL", "SSSP_E_SOURCE_RANGE", "SSSP_RULE_WINDOWED", "SSSP_LAYOUT_COMPACT",
+    for name in ("SSSP_E_INVAL", "SSSP_E_SOURCE_RANGE", "SSSP_RULE_WINDOWED", "SSSP_RULE_PRED_COUNT",
+                 "SSSP_LAYOUT_COMPACT",
                  "SSSP_LOOP_PERSISTENT", "SSSP_PENDING"):
         assert hasattr(P, name), name

@@ -442,6 +442,76 @@ def test_cheap_rules_first(sssp_lib, layout, base):
                   loop_mode=P.SSSP_LOOP_PERSISTENT)
 
 
+@LAYOUTS
+@pytest.mark.parametrize("base", [oracle.RULE_THR, oracle.RULE_MIND, oracle.CHEAP_FIRST],
+                         ids=["thr", "mind", "cheap"])
+def test_pred_counts(sssp_lib, layout, base):
+    """SP_1's predecessor counts: bit-exact with the oracle in the same mode,
+    counters included (fewer in-edges read), through the hub paths and every
+    loop mode."""
+    P = sssp_lib
+    mode = base | oracle.PRED_COUNT
+    assert_parity(P, gg.random_graph(4096, 8, 1, 100, 1812_10499), 0, mode=mode, layout=layout)
+    g = gg.rmat(13, 8, 1, 255, 6)
+    s = int(np.argmax(g.out_degree()))
+    assert_parity(P, g, s, mode=mode, layout=layout)
+    assert_parity(P, g, s, mode=mode, layout=layout, hub_degree=8, chunk_edges=32)
+    assert_parity(P, g, s, mode=mode, layout=layout, loop_mode=P.SSSP_LOOP_HOST)
+    assert_parity(P, gg.grid(50, 40, 1, 100, 2), 0, mode=mode, layout=layout,
+                  loop_mode=P.SSSP_LOOP_PERSISTENT)
+    assert_parity(P, gg.dag(20, 64, 5, 3, 1, 100, 7), 0, mode=mode, layout=layout)
+
+
+@pytest.mark.parametrize("tail", ["cluster", "grid"])
+def test_pred_counts_per_round_state(sssp_lib, tail, monkeypatch):
+    """The state after every round equals the oracle's (solves stopped with
+    max_rounds), with every round in the cluster tail kernel or none."""
+    monkeypatch.setenv("SSSP_TAIL_ITEMS", "1000000" if tail == "cluster" else "0")
+    g = gg.random_var_graph(700, 1, 6, 1, 50, 12)
+    mode = oracle.CHEAP_FIRST | oracle.PRED_COUNT
+    snaps = []
+    ref = oracle.round_r(g, 0, mode=mode, on_round=lambda r, thr, mD, D, C, F: snaps.append(
+        (D.copy(), C.copy(), F.copy())))
+    assert ref.rounds == len(snaps)
+    for r, (D, C, F) in enumerate(snaps, start=1):
+        out = gpu_solve(sssp_lib, g, 0, max_rounds=r, rule=mode)
+        assert out["info"]["rounds"] == r
+        assert np.array_equal(out["dist"], D), f"D after round {r}"
+        assert np.array_equal(out["lower"], C), f"C after round {r}"
+        assert np.array_equal(out["fixed_round"], F), f"fixed after round {r}"
+
+
+@LAYOUTS
+def test_pred_counts_on_an_out_tree(sssp_lib, layout):
+    """On an out-tree every discovered vertex's one in-neighbour is fixed and
+    has relaxed it: no in-edge is read, and the distances are Dijkstra's."""
+    P = sssp_lib
+    g = gg.out_tree(20000, 1, 50, 5)
+    out, ref = assert_parity(P, g, 0, mode=oracle.PRED_COUNT, layout=layout)
+    assert out["info"]["in_scanned"] == 0
+    assert out["info"]["reached"] == g.n
+
+
+def test_pred_counts_batch(sssp_lib):
+    """Several graphs in one batched launch with predecessor counts: each
+    equals its own oracle run (distances and round count)."""
+    P = sssp_lib
+    o = P.sssp_options_default()
+    o.rule = P.SSSP_RULE_PRED_COUNT | P.SSSP_RULE_CHEAP_FIRST
+    graphs = [gg.random_var_graph(n, 2, 10, 1, 500, 80 + i) for i, n in enumerate((300, 5000, 1200, 64))]
+    graphs += [gg.grid(40, 30, 1, 1000, 85), gg.out_tree(3000, 1, 500, 86)]
+    hs = [P.sssp_create(g.n, g.row_ptr, g.col, g.w, options=o) for g in graphs]
+    try:
+        srcs = [0, 7, 100, 5, 0, 0]
+        dists, rounds = P.sssp_solve_batch(hs, srcs)
+        for g, s, d, r in zip(graphs, srcs, dists, rounds):
+            ref = oracle.round_r(g, s, mode=oracle.PRED_COUNT | oracle.CHEAP_FIRST)
+            assert np.array_equal(d, ref.dist) and int(r) == ref.rounds
+    finally:
+        for h in hs:
+            P.sssp_destroy(h)
+
+
 def test_kernel_launch_count(sssp_lib, monkeypatch):
     """The solve reports the kernels it launched: four start/output kernels
     plus the round kernels of its loop mode."""
