@@ -687,21 +687,32 @@ def batched_metrics(args, kind):
     st.synchronize()
     tuning = None
     if not args.no_tune:
-        # The batch with the first graph's tuning, then the autotuner's pick
-        # (cached under the batch's class, where the batched call finds it).
+        # The autotuner's pick is cached under the batch's class, where the
+        # batched call finds it.  Then the batch with the first graph's
+        # tuning and with the pick, alternately (three times each, the best
+        # of each kept), so that neither side gets the other's warm-up.
         steps_t = max(1, min(args.steps, 5))
-        ms0 = timed(batched, steps_t)
+        key = P.sssp_batch_key(hs)
         t0 = time.perf_counter()
         res = P.sssp_autotune_batch(hs, srcs, reps=2)
         tune_s = time.perf_counter() - t0
+        first = P.sssp_get_tuning(hs[0])
+        ms0s, ms1s = [], []
+        for _ in range(3):
+            for t, acc in ((first, ms0s), (res["best"], ms1s)):
+                P.sssp_tune_cache_put(key, t)
+                batched()
+                acc.append(timed(batched, steps_t))
+        ms0, ms1 = min(ms0s), min(ms1s)
         for _ in range(args.warmup):
             rounds_b = batched()
-        ms1 = timed(batched, steps_t)
-        tuning = {"class_key": P.sssp_batch_key(hs), "chosen": res["best"],
+        tuning = {"class_key": key, "chosen": res["best"],
                   "sweep": {"evaluated": res["evaluated"], "start_ms": res["start_ms"],
                             "best_ms": res["best_ms"], "seconds": tune_s},
                   "batch_ms_default": ms0, "batch_ms_tuned": ms1, "gain": ms0 / ms1,
-                  "what": "sssp_autotune_batch on the whole batch (the timed queries)"}
+                  "what": "sssp_autotune_batch on the whole batch (the timed queries); "
+                          "batch_ms_*: best of three alternating timings of steps_t batches "
+                          "with the first graph's tuning and with the chosen one"}
     same_plain = all(torch.equal(a, b) for a, b in zip(outs_a, outs_b))
 
     steps = max(1, min(args.steps, 10))

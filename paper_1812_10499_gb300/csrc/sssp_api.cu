@@ -413,6 +413,43 @@ int alloc_lists(Context& c, u64 capS, u64 capH, u64 capC) {
     return SSSP_OK;
 }
 
+// The control block and, when they fit beside it, the per-query scalars go in
+// one of kHotSlots candidate slots, kHotStride bytes apart, of one allocation:
+// the slot that the tail kernel's cluster reaches with the shortest chain of
+// atomics (k_place_probe).  Which slot that is depends on where the
+// allocation lands in physical memory, and the latency-bound rounds -- each
+// a chain of waits on these words -- differ by up to 14% between a good slot
+// and a bad one.  SSSP_HOT_SLOT=<i> forces slot i (for measurements).
+int alloc_hot(Context& c, u32 nivar, cudaStream_t st) {
+    constexpr u32 kHotSlots = 16, kHotStride = 4096;
+    const size_t bytes = (size_t)kHotSlots * kHotStride;
+    unsigned char* hot = nullptr;
+    RC(c.pool.get(&hot, bytes + 256));
+    auto* cyc = reinterpret_cast<unsigned long long*>(hot + bytes);
+    CK(launch_place_probe(reinterpret_cast<u32*>(hot), kHotSlots, kHotStride / 4, cyc,
+                          c.tail_ctas, solve_smem_bytes(c.narrow), st));
+    unsigned long long h[kHotSlots];
+    CK(cudaMemcpyAsync(h, cyc, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemsetAsync(hot, 0, bytes + 256, st));
+    CK(cudaStreamSynchronize(st));
+    int best = 0;
+    for (u32 i = 1; i < kHotSlots; ++i)
+        if (h[i] < h[best]) best = (int)i;
+    if (const char* e = getenv("SSSP_HOT_SLOT")) {
+        const int f = atoi(e);
+        if (f >= 0 && f < (int)kHotSlots) best = f;
+    }
+    c.hot_slot = best;
+    unsigned char* slot = hot + (size_t)best * kHotStride;
+    c.P.ctl = reinterpret_cast<Ctl*>(slot);
+    const size_t ivoff = (sizeof(Ctl) + 255) & ~(size_t)255;
+    if (ivoff + (size_t)nivar * sizeof(InstVar) <= kHotStride)
+        c.P.ivar = reinterpret_cast<InstVar*>(slot + ivoff);
+    else
+        RC(c.pool.get(&c.P.ivar, nivar));
+    return SSSP_OK;
+}
+
 int alloc_pinned(Context& c, u32 slots) {
     CK(cudaHostAlloc((void**)&c.h_ctl, sizeof(Ctl), cudaHostAllocDefault));
     CK(cudaHostAlloc((void**)&c.h_ivar, sizeof(InstVar) * slots, cudaHostAllocDefault));
@@ -460,8 +497,7 @@ int init_single_context(sssp_graph* h) {
         RC(c.pool.get(&P.rec, h->n));
     }
     RC(c.pool.get(&P.fround, h->n));
-    RC(c.pool.get(&P.ctl, 1));
-    RC(c.pool.get(&P.ivar, 1));
+    RC(alloc_hot(c, 1, h->stream));
     RC(c.pool.get(&c.stage, h->n));
     RC(alloc_lists(c, h->n, std::max(h->hubs_in, h->hubs_out), hub_chunks(h)));
     P.dinf = h->dinf;
@@ -811,8 +847,7 @@ int ensure_batch(sssp_graph* h0, u64 nrec, u32 nslots, u32 npages, u64 capH, u64
     P.tail_items = h0->tail_items;
     RC(c->pool.get(&c->rec_store, nrec));   // 32-byte slots; the compact layout uses half
     RC(c->pool.get(&P.fround, nrec));
-    RC(c->pool.get(&P.ctl, 1));
-    RC(c->pool.get(&P.ivar, nslots));
+    RC(alloc_hot(*c, nslots, h0->stream));
     InstDesc* idesc = nullptr;
     u32* pages = nullptr;
     RC(c->pool.get(&idesc, nslots));

@@ -53,6 +53,8 @@ __global__ void k_scan_tiles(const u64* in, u64 cnt, u64* tile_sums);
 __global__ void k_scan_sums(u64* tile_sums, u32 ntiles);
 __global__ void k_scan_apply(const u64* in, u64 cnt, const u64* tile_sums, u64* out);
 constexpr u32 kScanTile = 2048;
+cudaError_t launch_place_probe(u32* base, u32 nslots, u32 stride_words, unsigned long long* cycles,
+                               u32 cluster_ctas, size_t smem, cudaStream_t st);
 }  // namespace sssp
 
 namespace sssp {
@@ -179,6 +181,7 @@ struct Context {
     cudaAccessPolicyWindow l2win{};  // L2 window over the records (num_bytes 0: none)
     u64* trace = nullptr;            // device trace of the persistent kernel
     u32 trace_cap = 0;
+    int hot_slot = -1;               // slot of the control block in its probed region
 
     void destroy() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -259,6 +262,7 @@ int tune_cache_find(const char* key, sssp_tuning* out);
 int build_loop(Context& c);
 int run_loop(Context& c, u32 loop_mode, cudaStream_t st);
 int alloc_lists(Context& c, u64 capS, u64 capH, u64 capC);
+int alloc_hot(Context& c, u32 nivar, cudaStream_t st);
 int alloc_pinned(Context& c, u32 slots);
 void set_l2_window(Context& c, int device);
 bool records_fit_l2(size_t bytes, int device);

@@ -130,8 +130,7 @@ int open_impl(sssp_server* s) {
     }
     RC(c.pool.get(&P.fround, nrec));
     set_l2_window(c, s->device);
-    RC(c.pool.get(&P.ctl, 1));
-    RC(c.pool.get(&P.ivar, c.nslots));
+    RC(alloc_hot(c, c.nslots, s->stream));
     InstDesc* idesc = nullptr;
     u32* pages = nullptr;
     RC(c.pool.get(&idesc, c.nslots));

@@ -282,4 +282,57 @@ __global__ void k_scan_apply(const u64* in, u64 cnt, const u64* tile_sums, u64* 
     }
 }
 
+// ------------------------------------------------- control-block placement
+
+// Round-trip time, in SM cycles, of a chain of 16 dependent atomics on each
+// of nslots candidate words (stride_words apart), the least of three passes
+// after one warming pass, from one thread of CTA 0.  Launched like the tail
+// kernel (one cluster of its CTAs), so the thread runs where the tail
+// kernel's CTA 0 will: the words the tail kernel's rounds wait on (list
+// counters, round minima) go in the fastest slot.  Writes cycles[0, nslots);
+// the candidate words are left changed (they are reset before any solve).
+__global__ void k_place_probe(u32* base, u32 nslots, u32 stride_words,
+                              unsigned long long* cycles) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    u32 x = 0;
+    for (u32 s = 0; s < nslots; ++s) x = atomicAdd(base + (size_t)s * stride_words, x >> 31);
+    for (u32 s = 0; s < nslots; ++s) cycles[s] = ~0ull;
+    for (u32 pass = 0; pass < 3; ++pass)
+        for (u32 s = 0; s < nslots; ++s) {
+            u32* p = base + (size_t)s * stride_words;
+            const long long t0 = clock64();
+            // Each atomic's operand depends on the previous one's result.
+            for (int i = 0; i < 16; ++i) x = atomicAdd(p, x >> 31);
+            const unsigned long long dt = (unsigned long long)(clock64() - t0) + (x >> 31);
+            if (dt < cycles[s]) cycles[s] = dt;
+        }
+}
+
+cudaError_t launch_place_probe(u32* base, u32 nslots, u32 stride_words, unsigned long long* cycles,
+                               u32 cluster_ctas, size_t smem, cudaStream_t st) {
+    if (cluster_ctas == 0) {
+        k_place_probe<<<1, 32, 0, st>>>(base, nslots, stride_words, cycles);
+        return cudaGetLastError();
+    }
+    cudaError_t e =
+        cudaFuncSetAttribute(k_place_probe, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_place_probe, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster_ctas;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cluster_ctas);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_place_probe, base, nslots, stride_words, cycles);
+}
+
 }  // namespace sssp

@@ -512,6 +512,28 @@ def test_pred_counts_batch(sssp_lib):
             P.sssp_destroy(h)
 
 
+@pytest.mark.parametrize("slot", [0, 7, 15])
+def test_control_block_slot(sssp_lib, slot, monkeypatch):
+    """The control block's placement (chosen by a latency probe among 16
+    slots, here forced) changes no result: single queries in every loop mode
+    and a batch whose per-query scalars do not fit beside it."""
+    monkeypatch.setenv("SSSP_HOT_SLOT", str(slot))
+    P = sssp_lib
+    g = gg.random_var_graph(3000, 1, 8, 1, 200, 41)
+    for lm in (P.SSSP_LOOP_GRAPH, P.SSSP_LOOP_HOST, P.SSSP_LOOP_PERSISTENT):
+        assert_parity(P, g, 0, loop_mode=lm)
+    graphs = [gg.random_var_graph(200 + 7 * i, 1, 6, 1, 50, 90 + i) for i in range(64)]
+    hs = [P.sssp_create(x.n, x.row_ptr, x.col, x.w) for x in graphs]
+    try:
+        dists, rounds = P.sssp_solve_batch(hs, [0] * len(graphs))
+        for x, d, r in zip(graphs, dists, rounds):
+            ref = oracle.round_r(x, 0)
+            assert np.array_equal(d, ref.dist) and int(r) == ref.rounds
+    finally:
+        for h in hs:
+            P.sssp_destroy(h)
+
+
 def test_kernel_launch_count(sssp_lib, monkeypatch):
     """The solve reports the kernels it launched: four start/output kernels
     plus the round kernels of its loop mode."""
