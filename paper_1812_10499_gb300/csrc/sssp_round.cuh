@@ -910,23 +910,16 @@ __global__ void __launch_bounds__(256, SSSP_MIN_CTAS) k_relax(RoundParams P) {
 // ---------------------------------------------------------------- cupdate
 
 // Segment minimum: brk has a bit at the first lane of every segment of
-// contiguous lanes.  The 32-bit form gives every lane its segment's minimum
-// (one warp reduction over the segment's lanes); the 64-bit form is an
-// inclusive segmented scan, exact at the segment's last lane.
-__device__ __forceinline__ u32 seg_min(u32 v, u32 brk, u32 lane) {
-    const u32 le = lanemask_le(lane);
-    const u32 first = 31 - __clz(brk & le);
-    const u32 above = brk & ~le;
-    const u32 last = above ? (u32)(__ffs(above) - 2) : 31u;
-    const u32 mask = (kFull >> (31 - last)) & (kFull << first);
-    return __reduce_min_sync(mask, v);
-}
-__device__ __forceinline__ u64 seg_min(u64 v, u32 brk, u32 lane) {
+// contiguous lanes.  An inclusive segmented scan, exact at the segment's last
+// lane.  (A warp reduction with each segment's lane mask gives every lane the
+// minimum too, but it made the latency-bound rounds 9-13% slower.)
+template <class T>
+__device__ __forceinline__ T seg_min(T v, u32 brk, u32 lane) {
     const u32 span = lane - (31 - __clz(brk & lanemask_le(lane)));
 #pragma unroll
     for (u32 dd = 1; dd < 32; dd <<= 1) {
-        const u64 ov = __shfl_up_sync(kFull, v, dd);
-        if (dd <= span) v = umin64(v, ov);
+        const T ov = __shfl_up_sync(kFull, v, dd);
+        if (dd <= span) v = ov < v ? ov : v;
     }
     return v;
 }
@@ -955,7 +948,14 @@ __device__ __forceinline__ u64 decide(const RoundParams& P, u64 dy, u64 cy, u64 
     return fix ? dy : cn;
 }
 
-template <bool MULTI, class L>
+// SHATOM (the cluster tail kernel): with the compact layout each edge's
+// 32-bit term goes into its owner's slot by a shared-memory atomicMin
+// instead of the segmented scan -- fewer dependent instructions per batch,
+// which is what the small rounds wait on (random n = 4096 -15%, R-MAT 22
+// +3%).  In large rounds, where many lanes share an owner, the scan is
+// faster, and with the wide layout's 64-bit terms the atomics cost 1.4% on
+// the 4096^2 grid, so both keep the scan.
+template <bool MULTI, class L, bool SHATOM = false>
 __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st, u32 t, u32 nas,
                           u32 r, u32 cur, u32 lane, u64* smin, u64 thr0, u64 minD0, Acc& a,
                           Acc& an, WarpQueue& qf, WarpQueue& qa, bool has_pre, u32 gpre) {
@@ -990,7 +990,12 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
         if (L::kPred && !fix_now) fix_now = P.pcnt[g] == 0u;
         if (fix_now) deg = 0;                     // its in-edges are not read
     }
-    smin[lane] = kInf64;
+    // The owners' minima: 64-bit slots, or (compact layout, SHATOM) 32-bit
+    // slots in their place.
+    constexpr bool kAtom = SHATOM && L::kNarrow;
+    u32* smin32 = reinterpret_cast<u32*>(smin);
+    if (kAtom) smin32[lane] = kInf31;
+    else smin[lane] = kInf64;
     const typename L::Bounds bd = L::bounds(thr, minD);
     Tile tl = make_tile(st, deg, (u64)(in_adj + ib), lane);
     run_pipeline(
@@ -1014,6 +1019,10 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
                 }
                 typename L::Term val = L::kTermInf;
                 if (ev) val = L::term(P, st.dc[ds][sidx], cur, st.adj[as][sidx].y, ob);
+                if (kAtom) {
+                    if (ev) atomicMin(smin32 + own, (u32)val);
+                    continue;
+                }
                 // Min over the lanes sharing an owner (contiguous lanes; a
                 // segment starts at every owner change).
                 const u32 prev = __shfl_up_sync(kFull, own, 1);
@@ -1031,7 +1040,7 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
     if (valid) {
         u64 cn = dy;
         if (fix_now) fix = true;
-        else cn = decide(P, dy, cy, smin[lane], thr, minD, fix);
+        else cn = decide(P, dy, cy, kAtom ? (u64)smin32[lane] : smin[lane], thr, minD, fix);
         L::set_c(rec + g, nxt, cn | (fix ? kFixed : 0ull));
         if (fix) P.fround[g] = (int)r;
         // Relaxation bound: D is stable until the next relaxation.
@@ -1241,8 +1250,9 @@ __device__ __forceinline__ void snap_frontier(const RoundParams& P, u32 k, u32 n
     if (ok) P.snap[g] = L::rec(P)[g].dp >> P.vbits;
 }
 
-// Steps (b) and (c) of round r over the whole active set (all CTAs).
-template <bool MULTI, class L>
+// Steps (b) and (c) of round r over the whole active set (all CTAs); TAIL:
+// inside the cluster tail kernel.
+template <bool MULTI, class L, bool TAIL = false>
 __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
     typedef WarpStage<typename L::CSlot> Stage;
     Stage* s_st = reinterpret_cast<Stage*>(s_dyn);
@@ -1294,8 +1304,8 @@ __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r)
     const u32 nwarps = gridDim.x * kWarps;
     for (u32 item = item0; item < total;) {
         if (item < tiles)
-            cup_small<MULTI, L>(P, s_st[wib], item, nas, r, cur, lane, s_min + wib * 32, thr,
-                                minD, a, an, qf, qa, item == item0, gpre);
+            cup_small<MULTI, L, TAIL>(P, s_st[wib], item, nas, r, cur, lane, s_min + wib * 32,
+                                      thr, minD, a, an, qf, qa, item == item0, gpre);
         else if (item < tiles + ah_chunks)
             cup_hub<MULTI, L>(P, s_st[wib], item - tiles, nah, r, cur, lane, thr, minD, a, an);
         else
@@ -1505,7 +1515,7 @@ __global__ void __launch_bounds__(256, 1) k_tail(RoundParams P) {
             if (lead && threadIdx.x == 0) ctl->cup_only = 1;
             break;
         }
-        cupdate_phase<MULTI, L>(P, s_dyn, r);
+        cupdate_phase<MULTI, L, true>(P, s_dyn, r);
         cluster_sync_all();
         if (!MULTI) {
             go = tail_next_single(P, r);
