@@ -1027,9 +1027,15 @@ __device__ void cup_small(const RoundParams& P, WarpStage<typename L::CSlot>& st
                 // segment starts at every owner change).
                 const u32 prev = __shfl_up_sync(kFull, own, 1);
                 const u32 brk = __ballot_sync(kFull, lane == 0 || !ev || prev != own);
-                val = seg_min(val, brk, lane);
-                const bool tail = ev && (lane == 31 || ((brk >> (lane + 1)) & 1u));
-                if (tail) smin[own] = umin64(smin[own], (u64)val);
+                if (L::kNarrow && brk == 1u) {
+                    // The whole row is one owner's: one warp reduction.
+                    val = __reduce_min_sync(kFull, (u32)val);
+                    if (lane == 0) smin[own] = umin64(smin[own], (u64)val);
+                } else {
+                    val = seg_min(val, brk, lane);
+                    const bool tail = ev && (lane == 31 || ((brk >> (lane + 1)) & 1u));
+                    if (tail) smin[own] = umin64(smin[own], (u64)val);
+                }
                 __syncwarp();
             }
         });
