@@ -31,6 +31,7 @@ CHEAP_FIRST = 4
 ALL_UNFIXED = 8
 DELTA = 16
 PRED_COUNT = 32
+WITNESS = 64
 
 _STATS = ("out_scanned", "in_scanned", "active_visits", "front_visits", "reached", "max_active")
 
@@ -68,6 +69,9 @@ def _bind(lib):
     lib.orc_round_delta.restype = c_int
     lib.orc_round_delta.argtypes = [u32, vp, vp, vp, u32, u32, ctypes.c_int64, u64, vp, vp, vp,
                                     vp, vp, vp, ROUND_CB, vp]
+    lib.orc_round_ex.restype = c_int
+    lib.orc_round_ex.argtypes = [u32, vp, vp, vp, u32, u32, ctypes.c_int64, u64, u32, vp, vp, vp,
+                                 vp, vp, vp, ROUND_CB, vp]
     lib.orc_prune.restype = c_int
     lib.orc_prune.argtypes = [u32, vp, vp, u32, vp]
     for f in (lib.orc_sp1, lib.orc_sp2):
@@ -156,13 +160,16 @@ class RoundResult:
 
 
 def round_r(g, s: int, mode: int = RULE_THR, on_round=None, lib=None,
-            target: int | None = None, delta: int | None = None) -> RoundResult:
+            target: int | None = None, delta: int | None = None,
+            witness_deg: int | None = None) -> RoundResult:
     """Sequential Round R (the SP_3/SP_4 round; see oracle.c).
 
     on_round(round, thr, minD, D, C, fixed_round) is called after every round
     with numpy views of the state (valid only during the call).  target: stop
     after the round that fixes this vertex (single-target query).  delta:
-    windowed relaxation (ORC_DELTA) with this window width; None = off."""
+    windowed relaxation (ORC_DELTA) with this window width; None = off.
+    witness_deg: stored minimum witnesses (ORC_WITNESS) for vertices of
+    in-degree <= witness_deg; None = off."""
     lib = lib or load()
     rp, col, w = _csr(g)
     n = g.n
@@ -181,7 +188,14 @@ def round_r(g, s: int, mode: int = RULE_THR, on_round=None, lib=None,
         cb = ROUND_CB(_cb)
     else:
         cb = ROUND_CB()
-    if delta is None:
+    if witness_deg is not None:
+        rc = lib.orc_round_ex(n, rp.ctypes.data, col.ctypes.data, w.ctypes.data, s,
+                              mode | WITNESS | (DELTA if delta is not None else 0),
+                              -1 if target is None else int(target),
+                              0 if delta is None else int(delta), int(witness_deg),
+                              dist.ctypes.data, parent.ctypes.data, C.ctypes.data,
+                              fr.ctypes.data, ctypes.byref(rounds), stats.ctypes.data, cb, None)
+    elif delta is None:
         rc = lib.orc_round(n, rp.ctypes.data, col.ctypes.data, w.ctypes.data, s, mode,
                            -1 if target is None else int(target), dist.ctypes.data,
                            parent.ctypes.data, C.ctypes.data, fr.ctypes.data,

@@ -230,19 +230,48 @@ int orc_floyd_warshall(uint32_t n, const uint64_t* row_ptr, const uint32_t* col,
  * reading the C of the previous round:
  *   lb(x) = max(C[x], min(D[x], threshold))          (Lemmas 7 and 8)
  *   lb(x) = C[x] if x is fixed, else max(C[x], minD)  (minD rule, SP_4 step 4). */
+/* One Eq. (1) term lb(x) + w of in-edge k = (x, y). */
+static uint64_t eq1_term(uint64_t k, const uint32_t* row, const uint32_t* w_in, const uint64_t* C,
+                         const uint64_t* D, const int32_t* fr, uint64_t thr, uint64_t minD,
+                         int rule_mind) {
+    uint32_t x = row[k];
+    uint64_t lb;
+    if (rule_mind)
+        lb = (fr[x] >= 0) ? C[x] : max_u64(C[x], minD);
+    else
+        lb = max_u64(C[x], min_u64(D[x], thr));
+    return sat_add(lb, w_in[k]);
+}
+
 static uint64_t eq1_min(uint32_t y, const uint64_t* col_ptr, const uint32_t* row,
                         const uint32_t* w_in, const uint64_t* C, const uint64_t* D,
                         const int32_t* fr, uint64_t thr, uint64_t minD, int rule_mind) {
     uint64_t best = ORC_INF;
+    for (uint64_t k = col_ptr[y]; k < col_ptr[y + 1]; ++k)
+        best = min_u64(best, eq1_term(k, row, w_in, C, D, fr, thr, minD, rule_mind));
+    return best;
+}
+
+/* eq1_min that also records the witness (ORC_WITNESS): *kw = the first
+ * in-edge with the least term, *m2 = the least term of the other in-edges
+ * (equal to the minimum when two in-edges share it). */
+static uint64_t eq1_min_witness(uint32_t y, const uint64_t* col_ptr, const uint32_t* row,
+                                const uint32_t* w_in, const uint64_t* C, const uint64_t* D,
+                                const int32_t* fr, uint64_t thr, uint64_t minD, int rule_mind,
+                                uint64_t* kw, uint64_t* m2) {
+    uint64_t best = ORC_INF, second = ORC_INF, kb = col_ptr[y];
     for (uint64_t k = col_ptr[y]; k < col_ptr[y + 1]; ++k) {
-        uint32_t x = row[k];
-        uint64_t lb;
-        if (rule_mind)
-            lb = (fr[x] >= 0) ? C[x] : max_u64(C[x], minD);
-        else
-            lb = max_u64(C[x], min_u64(D[x], thr));
-        best = min_u64(best, sat_add(lb, w_in[k]));
+        const uint64_t t = eq1_term(k, row, w_in, C, D, fr, thr, minD, rule_mind);
+        if (t < best) {
+            second = min_u64(second, best);
+            best = t;
+            kb = k;
+        } else {
+            second = min_u64(second, t);
+        }
     }
+    *kw = kb;
+    *m2 = second;
     return best;
 }
 
@@ -259,6 +288,15 @@ int orc_round_delta(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, co
                     uint32_t s, uint32_t mode, int64_t target, uint64_t delta,
                     uint64_t* dist, uint32_t* parent, uint64_t* C_out, int32_t* fixed_round,
                     uint32_t* rounds_out, uint64_t* stats, orc_round_cb cb, void* ctx) {
+    if (mode & ORC_WITNESS) return ORC_EINVAL;   /* needs a degree limit: orc_round_ex */
+    return orc_round_ex(n, row_ptr, col, w, s, mode, target, delta, 0, dist, parent, C_out,
+                        fixed_round, rounds_out, stats, cb, ctx);
+}
+
+int orc_round_ex(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* w,
+                 uint32_t s, uint32_t mode, int64_t target, uint64_t delta, uint32_t witness_deg,
+                 uint64_t* dist, uint32_t* parent, uint64_t* C_out, int32_t* fixed_round,
+                 uint32_t* rounds_out, uint64_t* stats, orc_round_cb cb, void* ctx) {
     /*
      * One round of the parallel SP_3/SP_4 scheme, done one vertex at a time
      * on a snapshot (Sec. VI, SP_4 steps 1-5, label-setting as in SP_3):
@@ -302,8 +340,10 @@ int orc_round_delta(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, co
     const int all_unfixed = (mode & ORC_ALL_UNFIXED) != 0;
     const int windowed = (mode & ORC_DELTA) != 0;
     const int pred_count = (mode & ORC_PRED_COUNT) != 0;
+    const int witness = (mode & ORC_WITNESS) != 0;
     if (windowed && label_correct) return ORC_EINVAL;
     if (pred_count && (windowed || label_correct)) return ORC_EINVAL;
+    if (witness && (windowed || label_correct || all_unfixed)) return ORC_EINVAL;
     uint64_t m = row_ptr[n];
 
     uint64_t* col_ptr = (uint64_t*)malloc(sizeof(uint64_t) * ((size_t)n + 1));
@@ -324,12 +364,14 @@ int orc_round_delta(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, co
     uint64_t* Cu = (uint64_t*)malloc(sizeof(uint64_t) * n);   /* undiscovered (ablation) */
     uint8_t* changed = (uint8_t*)calloc(n, 1);
     uint64_t* pcnt = (uint64_t*)malloc(sizeof(uint64_t) * n);   /* SP_1 predecessor counts */
+    uint64_t* wk = (uint64_t*)malloc(sizeof(uint64_t) * n);     /* witness in-edge */
+    uint64_t* wm2 = (uint64_t*)malloc(sizeof(uint64_t) * n);    /* witness bound m2 */
     uint32_t* list_mem[4] = {front, front2, act, act2};   /* freed at the end */
     if (!col_ptr || !row || !w_in || !outW || !inW || !par || !C || !fr || !front || !front2 ||
-        !front_d || !act || !act2 || !Cn || !Cu || !changed || !pcnt) {
+        !front_d || !act || !act2 || !Cn || !Cu || !changed || !pcnt || !wk || !wm2) {
         free(col_ptr); free(row); free(w_in); free(outW); free(inW); free(par); free(C); free(fr);
         free(front); free(front2); free(front_d); free(act); free(act2); free(Cn); free(Cu);
-        free(changed); free(pcnt);
+        free(changed); free(pcnt); free(wk); free(wm2);
         return ORC_ENOMEM;
     }
     orc_transpose(n, row_ptr, col, w, col_ptr, row, w_in);
@@ -408,8 +450,23 @@ int orc_round_delta(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, co
                 Cn[i] = D[y];            /* fixed without reading the in-edges */
                 continue;
             }
+            const int witnessed = witness && col_ptr[y + 1] - col_ptr[y] <= witness_deg;
+            if (witnessed && C[y] != 0) {
+                /* Visited before (every visit leaves C >= 1), so the witness
+                 * is set: if its term is still <= m2 it is the minimum. */
+                st[ORC_ST_IN_SCANNED] += 1;
+                const uint64_t t = eq1_term(wk[y], row, w_in, C, D, fr, thr, minD, rule_mind);
+                if (t <= wm2[y]) {
+                    Cn[i] = max_u64(C[y], max_u64(self, t));
+                    continue;
+                }
+            }
             st[ORC_ST_IN_SCANNED] += col_ptr[y + 1] - col_ptr[y];
-            best = eq1_min(y, col_ptr, row, w_in, C, D, fr, thr, minD, rule_mind);
+            if (witnessed)
+                best = eq1_min_witness(y, col_ptr, row, w_in, C, D, fr, thr, minD, rule_mind,
+                                       &wk[y], &wm2[y]);
+            else
+                best = eq1_min(y, col_ptr, row, w_in, C, D, fr, thr, minD, rule_mind);
             Cn[i] = max_u64(C[y], max_u64(self, best));
         }
         /* Ablation: the same bound for every undiscovered vertex (D = infinity,
@@ -463,7 +520,7 @@ int orc_round_delta(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, co
 
     free(col_ptr); free(row); free(w_in); free(outW); free(inW); free(par); free(C); free(fr);
     free(list_mem[0]); free(list_mem[1]); free(front_d); free(list_mem[2]); free(list_mem[3]);
-    free(Cn); free(Cu); free(changed); free(pcnt);
+    free(Cn); free(Cu); free(changed); free(pcnt); free(wk); free(wm2);
     return ORC_OK;
 }
 

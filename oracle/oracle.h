@@ -56,6 +56,19 @@
                                  D[y] is final) is fixed without reading its in-edges.  Eq. (1)
                                  fixes such a y in the same round, so only in_scanned changes.
                                  Label-setting only (not with ORC_LABEL_CORRECT or ORC_DELTA) */
+#define ORC_WITNESS      64u  /* (orc_round_ex only) a stored minimum witness per vertex: after a
+                                 full in-edge scan of y, its argmin in-edge k* (the first one in
+                                 CSC order with the least term) and m2, the least term of its
+                                 other in-edges.  Every Eq. (1) term only grows from round to
+                                 round (C grows, D falls but stays >= the distance >= the last
+                                 bound, the threshold and minD grow), so at y's next visit, if
+                                 the term of k* is still <= m2, it is the exact minimum: the
+                                 visit reads one in-edge instead of all of them.  Otherwise y
+                                 is scanned in full and gets a new witness.  Applies to vertices
+                                 with in-degree <= witness_deg; a visit counts 1 in-edge read for
+                                 the check plus the in-degree if the check fails.  Only
+                                 in_scanned changes.  Label-setting only, not with
+                                 ORC_ALL_UNFIXED */
 
 /* Per-round statistics written by orc_round (array of ORC_NSTATS u64). */
 #define ORC_ST_OUT_SCANNED   0  /* out-edges scanned in relax steps          */
@@ -113,6 +126,13 @@ int orc_round_delta(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, co
                     uint32_t s, uint32_t mode, int64_t target, uint64_t delta,
                     uint64_t* dist, uint32_t* parent, uint64_t* C_out, int32_t* fixed_round,
                     uint32_t* rounds_out, uint64_t* stats, orc_round_cb cb, void* ctx);
+
+/* orc_round_delta with ORC_WITNESS allowed in mode, for vertices of
+ * in-degree <= witness_deg. */
+int orc_round_ex(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* w,
+                 uint32_t s, uint32_t mode, int64_t target, uint64_t delta, uint32_t witness_deg,
+                 uint64_t* dist, uint32_t* parent, uint64_t* C_out, int32_t* fixed_round,
+                 uint32_t* rounds_out, uint64_t* stats, orc_round_cb cb, void* ctx);
 
 /* Sec. III pre-processing: iteratively delete non-source vertices with no
  * in-edges.  removed[v] = 1 for deleted vertices. */

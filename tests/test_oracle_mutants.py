@@ -33,8 +33,8 @@ MUTANTS = {
         "Cn[i] = max_u64(C[y], max_u64(self, best)); C[y] = Cn[i];"),
     "self clamp ignores D": ("uint64_t self = rule_mind ? minD : min_u64(D[y], thr);",
                              "uint64_t self = rule_mind ? minD : thr;"),
-    "in-edge weight of the wrong edge": ("best = min_u64(best, sat_add(lb, w_in[k]));",
-                                         "best = min_u64(best, sat_add(lb, w_in[col_ptr[y]]));"),
+    "in-edge weight of the wrong edge": ("return sat_add(lb, w_in[k]);",
+                                         "return sat_add(lb, w_in[k > 0 ? k - 1 : k]);"),
     "outWeight is a max": ("mw = min_u64(mw, w[k]);", "mw = max_u64(mw, w[k]);"),
     "fix on C >= D - 1": ("int fix = (Cn[i] == D[y])", "int fix = (Cn[i] + 1 >= D[y])"),
     "dijkstra relaxes from target": ("uint64_t nd = dist[j] + w[k];",
@@ -61,6 +61,11 @@ MUTANTS = {
     "pred counts start at the out-degree": (
         "for (uint32_t y = 0; y < n; ++y) pcnt[y] = col_ptr[y + 1] - col_ptr[y];",
         "for (uint32_t y = 0; y < n; ++y) pcnt[y] = row_ptr[y + 1] - row_ptr[y];"),
+    "witness check strict": ("if (t <= wm2[y]) {", "if (t < wm2[y]) {"),
+    "witness keeps the last minimal edge": (
+        "        if (t < best) {\n            second = min_u64(second, best);",
+        "        if (t <= best) {\n            second = min_u64(second, best);"),
+    "witness bound includes the minimum": ("    *m2 = second;", "    *m2 = best;"),
     "heap compares wrong way": ("if (h->key[a] != h->key[b]) return h->key[a] < h->key[b];",
                                 "if (h->key[a] != h->key[b]) return h->key[a] > h->key[b];"),
 }
@@ -111,6 +116,14 @@ def battery(lib):
     assert np.array_equal(a.fixed_round, b.fixed_round) and a.rounds == b.rounds
     t = gg.out_tree(300, 1, 50, 3)
     assert oracle.round_r(t, 0, mode=oracle.PRED_COUNT, lib=lib).stats["in_scanned"] == 0
+    # Stored minimum witnesses: the same state, and the scan count of an
+    # independent Python count (small weights: many ties).
+    for mode, (g, s) in ((oracle.RULE_THR, (gg.random_var_graph(300, 1, 12, 1, 4, 21), 0)),
+                         (oracle.CHEAP_FIRST, (gg.random_var_graph(300, 1, 12, 1, 40, 22), 0))):
+        a = oracle.round_r(g, s, mode=mode, lib=lib)
+        b = oracle.round_r(g, s, mode=mode, witness_deg=2**32 - 1, lib=lib)
+        assert np.array_equal(a.dist, b.dist) and np.array_equal(a.C, b.C)
+        assert b.stats["in_scanned"] == pins.witness_scan_count(g, s, mode, 2**32 - 1)
     g = gg.random_var_graph(200, 1, 6, 1, 30, 3)
     col_ptr, row, w_in = oracle.transpose(g, lib=lib)
     fwd = sorted(pins.edges_of(g))

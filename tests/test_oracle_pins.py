@@ -446,6 +446,104 @@ def test_pred_counts_refused_with_label_correcting_or_window():
             oracle.round_r(g, 0, **kw)
 
 
+# --------------------------------------------- stored minimum witnesses (R22)
+
+def witness_scan_count(g, s, mode, wdeg):
+    """in_scanned of the witness mode, recomputed in plain Python from the
+    per-round state of the run without witnesses (which the witness mode must
+    reproduce exactly): the terms of round r come from the C of round r - 1,
+    the D and threshold / minD of round r and the fixing rounds before r."""
+    snaps = []
+    oracle.round_r(g, s, mode=mode, on_round=lambda r, thr, mD, D, C, F: snaps.append(
+        (thr, mD, D.copy(), C.copy(), F.copy())))
+    n = g.n
+    ins = [[] for _ in range(n)]
+    for u, v, w in edges_of(g):
+        ins[v].append((u, w))                 # CSC order: by source, then CSR order
+    inw = [min((w for _, w in e), default=None) for e in ins]
+    Cpre = [0] * n
+    Fpre = [-1] * n
+    Fpre[s] = 0
+    witness = {}
+    count = 0
+    for r, (thr, mD, D, C, F) in enumerate(snaps, start=1):
+        def term(u, w):
+            if mode & oracle.RULE_MIND:
+                lb = Cpre[u] if Fpre[u] >= 0 else max(Cpre[u], mD)
+            else:
+                lb = max(Cpre[u], min(int(D[u]), thr))
+            return lb + w
+        for y in range(n):
+            if y == s or int(D[y]) == INF or not (F[y] == -1 or F[y] == r):
+                continue
+            dy = int(D[y])
+            if mode & oracle.CHEAP_FIRST and ((inw[y] is not None and dy <= mD + inw[y])
+                                              or dy <= thr):
+                continue
+            if mode & oracle.PRED_COUNT and all(0 <= Fpre[u] for u, _ in ins[y]):
+                continue
+            if len(ins[y]) <= wdeg and Cpre[y] != 0:
+                count += 1
+                k, m2 = witness[y]
+                if term(*ins[y][k]) <= m2:
+                    continue
+            count += len(ins[y])
+            if len(ins[y]) <= wdeg:
+                terms = [term(u, w) for u, w in ins[y]]
+                k = min(range(len(terms)), key=lambda i: (terms[i], i))
+                others = terms[:k] + terms[k + 1:]
+                witness[y] = (k, min(others) if others else INF)
+        Cpre = [int(c) for c in C]
+        Fpre = [int(f) for f in F]
+    return count
+
+
+@pytest.mark.parametrize("base", [oracle.RULE_THR, oracle.RULE_MIND, oracle.CHEAP_FIRST,
+                                  oracle.CHEAP_FIRST | oracle.PRED_COUNT],
+                         ids=["thr", "mind", "cheap", "cheap-pred"])
+def test_witness_changes_only_the_scan_count(base):
+    """Every Eq. (1) term is non-decreasing across rounds, so a stored argmin
+    whose term is still <= the other terms' old minimum is the exact minimum:
+    every state, round count and counter but in_scanned is unchanged."""
+    for g, s in ((gg.rmat(12, 8, 1, 255, 4), None), (gg.random_var_graph(3000, 1, 9, 1, 60, 8), 2),
+                 (gg.grid(40, 30, 1, 50, 1), 0), (gg.dag(20, 64, 5, 3, 1, 100, 7), 0),
+                 (gg.random_var_graph(2000, 1, 30, 1, 3, 9), 0)):
+        if s is None or g.out_degree()[s] == 0:
+            s = int(np.argmax(g.out_degree()))
+        a = oracle.round_r(g, s, mode=base)
+        for wdeg in (4, 256, 2**32 - 1):
+            b = oracle.round_r(g, s, mode=base, witness_deg=wdeg)
+            assert np.array_equal(a.dist, b.dist) and np.array_equal(a.parent, b.parent)
+            assert np.array_equal(a.C, b.C) and np.array_equal(a.fixed_round, b.fixed_round)
+            assert a.rounds == b.rounds
+            for k in ("out_scanned", "active_visits", "front_visits", "reached"):
+                assert a.stats[k] == b.stats[k]
+        assert oracle.round_r(g, s, mode=base, witness_deg=0).stats == a.stats
+
+
+@pytest.mark.parametrize("base", [oracle.RULE_THR, oracle.RULE_MIND, oracle.CHEAP_FIRST,
+                                  oracle.CHEAP_FIRST | oracle.PRED_COUNT],
+                         ids=["thr", "mind", "cheap", "cheap-pred"])
+def test_witness_scan_count_matches_a_python_count(base):
+    """The in-edges the witness mode reads, counted independently in Python
+    (small weights, so that equal terms and ties for the minimum are common)."""
+    for g, s, wdeg in ((gg.random_var_graph(300, 1, 12, 1, 4, 21), 0, 2**32 - 1),
+                       (gg.random_var_graph(300, 1, 12, 1, 40, 22), 0, 6),
+                       (gg.rmat(8, 8, 1, 3, 23), None, 2**32 - 1)):
+        if s is None:
+            s = int(np.argmax(g.out_degree()))
+        got = oracle.round_r(g, s, mode=base, witness_deg=wdeg).stats["in_scanned"]
+        assert got == witness_scan_count(g, s, base, wdeg)
+
+
+def test_witness_refused_with_other_rounds():
+    g = gg.random_graph(50, 3, 1, 9, 1)
+    for kw in (dict(mode=oracle.LABEL_CORRECT), dict(mode=oracle.RULE_THR, delta=5),
+               dict(mode=oracle.ALL_UNFIXED)):
+        with pytest.raises(Exception):
+            oracle.round_r(g, 0, witness_deg=8, **kw)
+
+
 # ------------------------------------------- ablation: C for all unfixed vertices
 
 def test_all_unfixed_ablation_is_sound_and_never_slower_in_rounds():
