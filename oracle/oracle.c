@@ -252,9 +252,10 @@ static uint64_t eq1_min(uint32_t y, const uint64_t* col_ptr, const uint32_t* row
     return best;
 }
 
-/* eq1_min that also records the witness (ORC_WITNESS): *kw = the first
- * in-edge with the least term, *m2 = the least term of the other in-edges
- * (equal to the minimum when two in-edges share it). */
+/* eq1_min that also records the witness (ORC_WITNESS): *kw = the in-edge
+ * with the least (term, source, weight) -- a choice that does not depend on
+ * the order of the in-edges -- and *m2 = the least term of the other
+ * in-edges (equal to the minimum when two in-edges share it). */
 static uint64_t eq1_min_witness(uint32_t y, const uint64_t* col_ptr, const uint32_t* row,
                                 const uint32_t* w_in, const uint64_t* C, const uint64_t* D,
                                 const int32_t* fr, uint64_t thr, uint64_t minD, int rule_mind,
@@ -268,6 +269,9 @@ static uint64_t eq1_min_witness(uint32_t y, const uint64_t* col_ptr, const uint3
             kb = k;
         } else {
             second = min_u64(second, t);
+            if (t == best && k != kb &&
+                (row[k] < row[kb] || (row[k] == row[kb] && w_in[k] < w_in[kb])))
+                kb = k;
         }
     }
     *kw = kb;

@@ -57,8 +57,8 @@
                                  fixes such a y in the same round, so only in_scanned changes.
                                  Label-setting only (not with ORC_LABEL_CORRECT or ORC_DELTA) */
 #define ORC_WITNESS      64u  /* (orc_round_ex only) a stored minimum witness per vertex: after a
-                                 full in-edge scan of y, its argmin in-edge k* (the first one in
-                                 CSC order with the least term) and m2, the least term of its
+                                 full in-edge scan of y, its argmin in-edge k* (least term, then
+                                 least source, then least weight) and m2, the least term of its
                                  other in-edges.  Every Eq. (1) term only grows from round to
                                  round (C grows, D falls but stays >= the distance >= the last
                                  bound, the threshold and minD grow), so at y's next visit, if

@@ -62,9 +62,8 @@ MUTANTS = {
         "for (uint32_t y = 0; y < n; ++y) pcnt[y] = col_ptr[y + 1] - col_ptr[y];",
         "for (uint32_t y = 0; y < n; ++y) pcnt[y] = row_ptr[y + 1] - row_ptr[y];"),
     "witness check strict": ("if (t <= wm2[y]) {", "if (t < wm2[y]) {"),
-    "witness keeps the last minimal edge": (
-        "        if (t < best) {\n            second = min_u64(second, best);",
-        "        if (t <= best) {\n            second = min_u64(second, best);"),
+    "witness ties keep the first edge": ("(row[k] < row[kb] || (row[k] == row[kb] && w_in[k] < w_in[kb]))",
+                                         "(row[k] > row[kb] || (row[k] == row[kb] && w_in[k] > w_in[kb]))"),
     "witness bound includes the minimum": ("    *m2 = second;", "    *m2 = best;"),
     "heap compares wrong way": ("if (h->key[a] != h->key[b]) return h->key[a] < h->key[b];",
                                 "if (h->key[a] != h->key[b]) return h->key[a] > h->key[b];"),

@@ -490,7 +490,7 @@ def witness_scan_count(g, s, mode, wdeg):
             count += len(ins[y])
             if len(ins[y]) <= wdeg:
                 terms = [term(u, w) for u, w in ins[y]]
-                k = min(range(len(terms)), key=lambda i: (terms[i], i))
+                k = min(range(len(terms)), key=lambda i: (terms[i], ins[y][i][0], ins[y][i][1]))
                 others = terms[:k] + terms[k + 1:]
                 witness[y] = (k, min(others) if others else INF)
         Cpre = [int(c) for c in C]
