@@ -19,6 +19,7 @@
 // state (slots, pages, the context) is touched only by the step that holds
 // `step_mu`.
 #include <chrono>
+#include <cstring>
 #include <condition_variable>
 #include <deque>
 #include <thread>
@@ -75,6 +76,11 @@ struct sssp_server {
     std::vector<u32> free_slots;
     std::vector<Query*> slot_query;
     u32 inflight = 0;
+    // Finished queries whose distances wait in the page-locked staging h_out
+    // (at the given offsets) to be copied into their output arrays.
+    u64* h_out = nullptr;
+    u64 h_out_n = 0;
+    std::vector<std::pair<Query*, u64>> deliver;
     // Host-side bookkeeping, guarded by mu.
     std::mutex mu;
     std::condition_variable cv_work;    // a query was queued, or the server closes
@@ -150,6 +156,8 @@ int open_impl(sssp_server* s) {
     CK(cudaHostAlloc((void**)&c.h_desc, sizeof(InstDesc) * c.nslots, cudaHostAllocDefault));
     CK(cudaHostAlloc((void**)&c.h_pages, sizeof(u32) * c.npages, cudaHostAllocDefault));
     CK(cudaHostAlloc((void**)&s->h_stop, sizeof(u32), cudaHostAllocDefault));
+    s->h_out_n = 1u << 23;
+    CK(cudaHostAlloc((void**)&s->h_out, sizeof(u64) * s->h_out_n, cudaHostAllocDefault));
     CK(cudaMemsetAsync(P.L.hubmin, 0xFF, sizeof(u64) * c.capH, s->stream));
     CK(cudaMemsetAsync(P.L.hubcnt, 0, sizeof(u32) * c.capH, s->stream));
     CK(cudaMemsetAsync(P.ivar, 0, sizeof(InstVar) * c.nslots, s->stream));
@@ -247,35 +255,64 @@ int retire(sssp_server* s, u64 step, u32* rounds_run) {
     *rounds_run = c.h_ctl->round - s->round_host;
     s->round_host = c.h_ctl->round;
     std::vector<Query*> done;
+    u64 total = 0;
     for (u32 slot = 0; slot < c.nslots; ++slot) {
         Query* q = s->slot_query[slot];
         if (!q || c.h_ivar[slot].status != kDone) continue;
+        done.push_back(q);
+        total += q->g->n;
+    }
+    // The staging is free here: the previous step's results were delivered
+    // before this step's status read.
+    if (total > s->h_out_n) {
+        cudaFreeHost(s->h_out);
+        s->h_out = nullptr;
+        s->h_out_n = 0;
+        const u64 n = std::max<u64>(total, 2 * (u64)(1u << 23));
+        CK(cudaHostAlloc((void**)&s->h_out, sizeof(u64) * n, cudaHostAllocDefault));
+        s->h_out_n = n;
+    }
+    u64 off = 0;
+    for (Query* q : done) {
+        const u32 slot = q->slot;
         const u64 base = (u64)q->first_page << kPageShift;
         k_finalize<<<c.grid, kThreads, 0, s->stream>>>(c.P.rec, c.P.recn, c.P.fround, base,
                                                        q->g->n, c.P.vbits, c.P.ivar + slot,
                                                        c.stage + base, nullptr, nullptr, nullptr);
         CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(q->out, c.stage + base, sizeof(u64) * q->g->n, cudaMemcpyDeviceToHost,
-                           s->stream));
+        CK(cudaMemcpyAsync(s->h_out + off, c.stage + base, sizeof(u64) * q->g->n,
+                           cudaMemcpyDeviceToHost, s->stream));
         q->rounds = c.h_ivar[slot].rounds;
-        done.push_back(q);
+        q->last_step = step;
+        s->deliver.emplace_back(q, off);
+        off += q->g->n;
     }
     if (!done.empty()) CK(cudaStreamSynchronize(s->stream));
+    // The distances are on the host: the slots and pages take new queries.
     for (Query* q : done) {
         for (u32 p = 0; p < q->npages; ++p) s->page_used[q->first_page + p] = 0;
         s->slot_query[q->slot] = nullptr;
         s->free_slots.push_back(q->slot);
         s->inflight--;
     }
+    return SSSP_OK;
+}
+
+// Copies the finished queries' distances from the staging into their output
+// arrays and completes them.  A step does this after it has launched its
+// rounds, so the copies overlap the device's work.  Caller holds step_mu.
+void deliver(sssp_server* s) {
+    if (s->deliver.empty()) return;
+    for (const auto& d : s->deliver)
+        memcpy(d.first->out, s->h_out + d.second, sizeof(u64) * d.first->g->n);
     const u64 t = now_ns();
     std::lock_guard<std::mutex> lk(s->mu);
-    for (Query* q : done) {
-        q->state = kComplete;
-        q->done_ns = t;
-        q->last_step = step;
+    for (const auto& d : s->deliver) {
+        d.first->state = kComplete;
+        d.first->done_ns = t;
     }
-    s->completed += done.size();
-    return SSSP_OK;
+    s->completed += s->deliver.size();
+    s->deliver.clear();
 }
 
 // One server step: admission, a few rounds of every query in flight,
@@ -300,11 +337,14 @@ int step(sssp_server* s) {
             rc = SSSP_E_CUDA;
         }
         if (rc == SSSP_OK) rc = run_loop(c, SSSP_LOOP_GRAPH, s->stream);
+        deliver(s);    // the previous step's results, while the rounds run
         if (rc == SSSP_OK) rc = retire(s, step_no, &ran);
     } else if (rc == SSSP_OK) {
         std::lock_guard<std::mutex> lk(s->mu);
         stuck = !s->pending.empty();   // nothing on the device and nothing admissible
     }
+    // With nothing left on the device no step may follow soon: deliver now.
+    if (s->inflight == 0) deliver(s);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (inflight > 0) {
@@ -312,7 +352,7 @@ int step(sssp_server* s) {
             s->rounds += ran;
             s->max_inflight = std::max(s->max_inflight, inflight);
         }
-        s->inflight_seen = s->inflight;
+        s->inflight_seen = s->inflight + (u32)s->deliver.size();
         s->stuck = stuck;
         if (rc != SSSP_OK && s->error == SSSP_OK) s->error = rc;
     }
@@ -395,6 +435,7 @@ int sssp_serve_open(const sssp_serve_cfg* cfg, sssp_server** out) {
         if (rc != SSSP_OK) {
             s->ctx.destroy();
             if (s->h_stop) cudaFreeHost(s->h_stop);
+            if (s->h_out) cudaFreeHost(s->h_out);
             if (s->stream) cudaStreamDestroy(s->stream);
         }
     }
@@ -409,6 +450,7 @@ int sssp_serve_open(const sssp_serve_cfg* cfg, sssp_server** out) {
             DeviceGuard dg(dev);
             s->ctx.destroy();
             cudaFreeHost(s->h_stop);
+            if (s->h_out) cudaFreeHost(s->h_out);
             cudaStreamDestroy(s->stream);
             delete s;
             return SSSP_E_NOMEM;
@@ -554,6 +596,7 @@ void sssp_serve_close(sssp_server* s) {
         if (s->stream) cudaStreamSynchronize(s->stream);
         s->ctx.destroy();
         if (s->h_stop) cudaFreeHost(s->h_stop);
+        if (s->h_out) cudaFreeHost(s->h_out);
         if (s->stream) cudaStreamDestroy(s->stream);
     }
     for (auto& kv : s->tickets) delete kv.second;
