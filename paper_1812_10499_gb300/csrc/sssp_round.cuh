@@ -394,9 +394,31 @@ __device__ __forceinline__ void fold(const RoundParams& P, u32 inst, u32 slot, u
 }
 
 // Flush register folds and counters at the end of a phase (all lanes).
-template <bool MULTI>
+template <bool MULTI, bool NARROW = false>
 __device__ __forceinline__ void flush(const RoundParams& P, u32 slot, u32 nfix_slot, Acc& a,
                                       u32 lane, int stat_edges, int stat_visits) {
+    if (NARROW && gridDim.x <= kSmallGrid) {
+        // Cluster-sized grid, compact layout: every sum and minimum fits 32
+        // bits (distances below 2^31, D + outWeight below 2^32 - 2), so one
+        // warp reduction each instead of shuffle trees.
+        const u32 e32 = __reduce_add_sync(kFull, (u32)a.edges);
+        const u32 v32 = __reduce_add_sync(kFull, (u32)a.visits);
+        const u32 nf32 = __reduce_add_sync(kFull, (u32)a.nfix);
+        if (!MULTI) {
+            const u32 d32 = __reduce_min_sync(kFull, a.fmin_d == kInf64 ? kFull : (u32)a.fmin_d);
+            const u32 t32 = __reduce_min_sync(kFull, a.fmin_t == kInf64 ? kFull : (u32)a.fmin_t);
+            if (lane == 0) {
+                if (d32 != kFull) atomicMin(&P.ivar[0].minD[slot], (u64)d32);
+                if (t32 != kFull) atomicMin(&P.ivar[0].thr[slot], (u64)t32);
+                if (nf32) atomicAdd(&P.ivar[0].nfix[nfix_slot], nf32);
+            }
+        }
+        if (lane == 0) {
+            if (e32) atomicAdd(&P.ctl->stats[stat_edges], (u64)e32);
+            if (v32) atomicAdd(&P.ctl->stats[stat_visits], (u64)v32);
+        }
+        return;
+    }
     const u64 e = warp_sum64(a.edges), v = warp_sum64(a.visits);
     const u64 nf = warp_sum64(a.nfix);
     if (!MULTI) {
@@ -895,7 +917,7 @@ __device__ void relax_phase(const RoundParams& P, unsigned char* s_dyn, u32 r) {
     }
     relax_consume<MULTI, L>(P, cur, a, q, qf, pd, lane);
     wq_flush2(P, q, &ctl->nAS[cur], P.L.AS[cur], qf, &ctl->nFS[nxt], P.L.FS[nxt], lane);
-    flush<MULTI>(P, cur, nxt, a, lane, 0, 3);
+    flush<MULTI, L::kNarrow>(P, cur, nxt, a, lane, 0, 3);
 }
 
 template <bool MULTI, class L>
@@ -1328,7 +1350,7 @@ __device__ void cupdate_phase(const RoundParams& P, unsigned char* s_dyn, u32 r)
     a.fmin_d = an.fmin_d;
     a.fmin_t = an.fmin_t;
     a.nfix = an.nfix;
-    flush<MULTI>(P, nxt, nxt, a, lane, 1, 2);
+    flush<MULTI, L::kNarrow>(P, nxt, nxt, a, lane, 1, 2);
 }
 
 template <bool MULTI, class L>
